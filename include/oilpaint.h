@@ -1,0 +1,239 @@
+/*
+ * oilpaint.h -- C ABI of the GB300 (sm_103a) histogram oil-paint filter.
+ *
+ * The filter is the one of section 4 of S. Mukherjee, "Study on performance
+ * improvement of oil paint image filter algorithm using Parallel Pattern
+ * Library" (arXiv 1405.1020), whose interface there is
+ * ApplyOilPaintOnBuffer(in, width, height, intensity_level, radius, out).
+ * For every output pixel (x, y):
+ *   - each neighbour in the (2r+1) x (2r+1) window centred on (x, y) gets the
+ *     intensity level floor((R+G+B) * L / 765), clamped to L-1 (section 4's
+ *     ((r+g+b)*intensity_level/3.0)/255 is the same integer for every sum and
+ *     every L in 1..256; pure white, the one sum that reaches L, joins the top
+ *     level).  OP_LEVEL_INTDIV3 selects floor(floor((R+G+B)/3) * L / 255)
+ *     instead, also clamped;
+ *   - neighbours outside the image are skipped (the window shrinks at the
+ *     border; every pixel of the image is written);
+ *   - the level with the largest count wins, the lowest level on a tie;
+ *   - each output channel is the truncated mean of that level's pixels.
+ * With 4 bytes per pixel the 4th byte is copied from the input pixel.  Bytes
+ * between width*bpp and stride in a row are never written.
+ *
+ * Conventions for every call:
+ *   - "device pointer" means memory the CUDA device can address (cudaMalloc,
+ *     a torch CUDA tensor's data_ptr(), ...); "host pointer" means ordinary or
+ *     pinned host memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); every *_run call is asynchronous on it and never synchronises;
+ *   - calls return OP_OK (0) or a negative OP_E_* status; nothing aborts;
+ *   - errors found on the device while a kernel runs (a bounded wait that ran
+ *     out) set a sticky per-object error word that op_sync_status /
+ *     op_batch_sync_status report and clear;
+ *   - an op_t or op_batch_t is not thread safe: one host thread at a time.
+ *   - the device used is the one current (cudaSetDevice) when the object is
+ *     created; calls must be made with that device current.
+ */
+#ifndef OILPAINT_H
+#define OILPAINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define OP_OK 0
+#define OP_E_INVALID (-1)     /* bad argument (NULL, size out of range, aliasing, ...) */
+#define OP_E_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define OP_E_NOMEM (-3)       /* host or device allocation failed */
+#define OP_E_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define OP_E_UNSUPPORTED (-5) /* valid request this build cannot run (e.g. shared memory) */
+
+/* ---- flags for op_create_ex / op_image_t.flags -------------------------- */
+#define OP_LEVEL_PAPER 0u   /* level = min(floor((R+G+B)*L/765), L-1)        (section 4) */
+#define OP_LEVEL_INTDIV3 1u /* level = min(floor(floor((R+G+B)/3)*L/255), L-1)          */
+
+/* ---- limits ------------------------------------------------------------- */
+#define OP_MAX_RADIUS 44   /* 255*(2r+1)^2 must fit the 21-bit per-level channel sums */
+#define OP_MAX_LEVELS 256  /* levels are stored in 8 bits */
+#define OP_MAX_DIM 65535u  /* width and height */
+
+typedef struct op_s op_t;
+
+/*
+ * Launch configuration of the filter kernel.  op_create picks it from the
+ * tuning table (see op_tune_table_set); the autotuner overrides it.
+ *   tile_w     output columns per CTA = threads per CTA: 32, 64, 128 or 256;
+ *   tile_h     output rows per CTA (0 = chosen from the image size and the
+ *              number of resident CTAs);
+ *   chunk_rows input rows per TMA halo copy, 1..32;
+ *   prefetch   halo copies in flight ahead of the one being consumed, 1..4.
+ */
+typedef struct {
+  uint32_t tile_w;
+  uint32_t tile_h;
+  uint32_t chunk_rows;
+  uint32_t prefetch;
+} op_config_t;
+
+/*
+ * op_create -- the 5-argument form (section 4's interface plus the row
+ * pitch).  width, height in pixels (1..OP_MAX_DIM); stride = bytes between
+ * rows; bytes per pixel are 4 if stride >= 4*width and stride % 4 == 0, else
+ * 3; 0 <= radius <= OP_MAX_RADIUS; 1 <= levels <= OP_MAX_LEVELS.  Level mode
+ * OP_LEVEL_PAPER.  Returns a handle owned by the caller (free with
+ * op_destroy), or NULL with the reason in op_last_error().
+ */
+op_t *op_create(uint32_t width, uint32_t height, uint32_t stride, int32_t radius, uint32_t levels);
+
+/* op_create_ex -- explicit bytes per pixel (3 or 4, stride >= width*bpp) and
+ * flags (OP_LEVEL_PAPER or OP_LEVEL_INTDIV3).  Otherwise as op_create. */
+op_t *op_create_ex(uint32_t width, uint32_t height, uint32_t stride, uint32_t bpp, int32_t radius,
+                   uint32_t levels, uint32_t flags);
+
+/* Status of the last op_create / op_create_ex / op_batch_create on this host
+ * thread (OP_OK after a success). */
+int op_last_error(void);
+
+/* Static, human-readable name of a status code. */
+const char *op_status_string(int status);
+
+/* Current launch configuration of `op` into *cfg. */
+int op_get_config(const op_t *op, op_config_t *cfg);
+
+/* Replace the launch configuration.  OP_E_INVALID for values out of range,
+ * OP_E_UNSUPPORTED if its shared memory does not fit one CTA on this device.
+ * The workspace size does not depend on the configuration. */
+int op_set_config(op_t *op, const op_config_t *cfg);
+
+/* Configuration op_create would pick for (radius, levels) on the current
+ * device: the tuning-table entry if one is set, else the built-in default. */
+int op_default_config(int32_t radius, uint32_t levels, op_config_t *cfg);
+
+/* Record a tuned configuration for (radius, levels) in this process's table
+ * (read by later op_create / op_batch_set calls).  Not persisted. */
+int op_tune_table_set(int32_t radius, uint32_t levels, const op_config_t *cfg);
+
+/* Bytes of device workspace op_run needs: the packed-word image of
+ * section 4's per-pixel level and colour (one 32-bit word per pixel, rows
+ * padded to 16 bytes). */
+size_t op_workspace_size(const op_t *op);
+
+/* Give `op` caller-owned device workspace of `bytes` >= op_workspace_size,
+ * 16-byte aligned; it must stay valid while runs that use it are in flight.
+ * Without it op_run allocates its own on first use (freed by op_destroy). */
+int op_set_workspace(op_t *op, void *d_ws, size_t bytes);
+
+/*
+ * op_run -- filter one image, asynchronously on `stream`.  d_in, d_out:
+ * device pointers to height*stride bytes each, non-overlapping.  Launches the
+ * pack prepass and the tiled filter kernel.  OP_E_CUDA if a launch fails.
+ */
+int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream);
+
+/*
+ * op_run_host -- the same filter on host buffers: copies h_in to device
+ * memory owned by `op`, runs, copies the result to h_out and synchronises
+ * `stream` before returning.  h_in, h_out: host pointers to height*stride
+ * bytes (page-locked memory makes the copies faster).  Only pixel bytes of
+ * h_out are written; its row padding is left untouched.  Device staging
+ * memory is allocated on the first call and freed by op_destroy.
+ */
+int op_run_host(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream);
+
+/* Profiling hook: when `event` (a cudaEvent_t passed as void*) is not NULL,
+ * every later op_run records it on the run's stream between the pack prepass
+ * and the filter kernel, so that events recorded by the caller before and
+ * after op_run time the two kernels separately.  NULL turns it off.  The
+ * event stays owned by the caller. */
+int op_set_profile_event(op_t *op, void *event);
+
+/* Synchronise `stream`, then report and clear the sticky device error word
+ * of `op`: OP_OK, OP_E_TIMEOUT, or OP_E_CUDA if the stream reported an error. */
+int op_sync_status(op_t *op, void *stream);
+
+/* Free `op` and everything it allocated.  NULL is accepted.  The caller
+ * must make sure no run using it is still in flight. */
+int op_destroy(op_t *op);
+
+/* ---- batched, persistent form ------------------------------------------- */
+
+/* One image of a batch.  in/out: device pointers (height*stride bytes, not
+ * overlapping); other fields as op_create_ex. */
+typedef struct {
+  const uint8_t *in;
+  uint8_t *out;
+  uint32_t width, height, stride, bpp;
+  int32_t radius;
+  uint32_t levels;
+  uint32_t flags;
+  uint32_t reserved; /* must be 0 */
+} op_image_t;
+
+typedef struct op_batch_s op_batch_t;
+
+/*
+ * op_batch_create -- a batch runner for up to `max_images` images holding at
+ * most `max_pixels` pixels in total, every radius <= max_radius and level
+ * count <= max_levels.  All images of a run share one persistent kernel
+ * launch: each CTA takes (image, tile) tickets from a device-side atomic
+ * counter until the queue is empty.  cfg: tile_w, chunk_rows and prefetch of
+ * that launch (NULL = defaults; tile_h is chosen per image).  Returns NULL
+ * with op_last_error() on failure.
+ */
+op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t max_radius,
+                            uint32_t max_levels, const op_config_t *cfg);
+
+/* Device workspace a batch needs: descriptors, tensor maps, tile tables and
+ * the packed-word images of max_pixels pixels. */
+size_t op_batch_workspace_size(const op_batch_t *b);
+
+/* Caller-owned workspace (device pointer, >= op_batch_workspace_size bytes,
+ * 256-byte aligned).  Without it the batch allocates its own on first set. */
+int op_batch_set_workspace(op_batch_t *b, void *d_ws, size_t bytes);
+
+/*
+ * op_batch_set -- describe the images of the next run(s): validates them,
+ * builds per-image descriptors, TMA tensor maps and the tile queue on the
+ * host, and copies them to the device workspace asynchronously on `stream`.
+ * A captured graph (op_batch_capture) reads these device tables, so it stays
+ * valid across op_batch_set calls.  n may be 0 (runs then do nothing).
+ */
+int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stream);
+
+/* Launch the batch's pack kernel and persistent filter kernel on `stream`
+ * (2 launches, fixed grids). */
+int op_batch_run(op_batch_t *b, void *stream);
+
+/* Capture op_batch_run's launches into a CUDA graph owned by `b` (replacing
+ * any earlier one).  `stream` must not be capturing already. */
+int op_batch_capture(op_batch_t *b, void *stream);
+
+/* Replay the captured graph on `stream`; OP_E_INVALID if none. */
+int op_batch_launch_graph(op_batch_t *b, void *stream);
+
+/* As op_sync_status, for the batch's error word. */
+int op_batch_sync_status(op_batch_t *b, void *stream);
+
+/* Free the batch (graph, host staging, owned workspace).  NULL accepted. */
+int op_batch_destroy(op_batch_t *b);
+
+/* ---- self-test of the bounded device wait -------------------------------- */
+
+/*
+ * op_selftest_wait_timeout -- launches one CTA that waits, through the same
+ * bounded mbarrier wait the filter kernels use, on a barrier that nothing
+ * completes, with a limit of `timeout_ns` nanoseconds (1..2e9).  The wait
+ * gives up, the kernel records OP_E_TIMEOUT in a device word and returns;
+ * this call synchronises `stream` and returns that status.  It exercises the
+ * error path without faulting or hanging the device.
+ */
+int op_selftest_wait_timeout(uint64_t timeout_ns, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OILPAINT_H */

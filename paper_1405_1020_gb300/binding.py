@@ -1,0 +1,233 @@
+"""ctypes binding of include/oilpaint.h -- argument marshalling only.
+
+Every function has the name and the argument order of the C entry point and
+returns what it returns (status codes are plain ints; handles are opaque
+ints).  Device pointers are ints (e.g. ``tensor.data_ptr()``), streams are
+ints (``torch.cuda.current_stream().cuda_stream``) or None.
+
+The library is ``liboilpaint.so`` next to this file, built by
+``__graft_entry__.build()`` (or ``python paper_1405_1020_gb300/csrc/build.py``).
+There is no fallback: if it is missing, every call raises ``OilPaintError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+OP_OK = 0
+OP_E_INVALID = -1
+OP_E_CUDA = -2
+OP_E_NOMEM = -3
+OP_E_TIMEOUT = -4
+OP_E_UNSUPPORTED = -5
+
+OP_LEVEL_PAPER = 0
+OP_LEVEL_INTDIV3 = 1
+
+OP_MAX_RADIUS = 44
+OP_MAX_LEVELS = 256
+OP_MAX_DIM = 65535
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboilpaint.so")
+
+# every symbol include/oilpaint.h declares
+EXPORTS = (
+    "op_create", "op_create_ex", "op_last_error", "op_status_string", "op_get_config",
+    "op_set_config", "op_default_config", "op_tune_table_set", "op_workspace_size",
+    "op_set_workspace", "op_run", "op_run_host", "op_set_profile_event", "op_sync_status",
+    "op_destroy",
+    "op_batch_create", "op_batch_workspace_size", "op_batch_set_workspace", "op_batch_set",
+    "op_batch_run", "op_batch_capture", "op_batch_launch_graph", "op_batch_sync_status",
+    "op_batch_destroy", "op_selftest_wait_timeout",
+)
+
+
+class OilPaintError(RuntimeError):
+    """A failed call (status in .status) or a missing library."""
+
+    def __init__(self, msg: str, status: int | None = None):
+        super().__init__(msg)
+        self.status = status
+
+
+class op_config_t(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_uint32), ("tile_h", ctypes.c_uint32),
+                ("chunk_rows", ctypes.c_uint32), ("prefetch", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+    @classmethod
+    def make(cls, tile_w: int, tile_h: int = 0, chunk_rows: int = 8, prefetch: int = 2):
+        return cls(tile_w, tile_h, chunk_rows, prefetch)
+
+
+class op_image_t(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("stride", ctypes.c_uint32), ("bpp", ctypes.c_uint32),
+                ("radius", ctypes.c_int32), ("levels", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liboilpaint.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OilPaintError(f"{path} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    u32, i32, u64 = ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64
+    vp, sz, ci = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    cfgp = ctypes.POINTER(op_config_t)
+    sig = {
+        "op_create": (vp, [u32, u32, u32, i32, u32]),
+        "op_create_ex": (vp, [u32, u32, u32, u32, i32, u32, u32]),
+        "op_last_error": (ci, []),
+        "op_status_string": (ctypes.c_char_p, [ci]),
+        "op_get_config": (ci, [vp, cfgp]),
+        "op_set_config": (ci, [vp, cfgp]),
+        "op_default_config": (ci, [i32, u32, cfgp]),
+        "op_tune_table_set": (ci, [i32, u32, cfgp]),
+        "op_workspace_size": (sz, [vp]),
+        "op_set_workspace": (ci, [vp, vp, sz]),
+        "op_run": (ci, [vp, vp, vp, vp]),
+        "op_run_host": (ci, [vp, vp, vp, vp]),
+        "op_set_profile_event": (ci, [vp, vp]),
+        "op_sync_status": (ci, [vp, vp]),
+        "op_destroy": (ci, [vp]),
+        "op_batch_create": (vp, [u32, u64, i32, u32, cfgp]),
+        "op_batch_workspace_size": (sz, [vp]),
+        "op_batch_set_workspace": (ci, [vp, vp, sz]),
+        "op_batch_set": (ci, [vp, ctypes.POINTER(op_image_t), u32, vp]),
+        "op_batch_run": (ci, [vp, vp]),
+        "op_batch_capture": (ci, [vp, vp]),
+        "op_batch_launch_graph": (ci, [vp, vp]),
+        "op_batch_sync_status": (ci, [vp, vp]),
+        "op_batch_destroy": (ci, [vp]),
+        "op_selftest_wait_timeout": (ci, [u64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().op_status_string(status).decode()
+
+
+def check(status: int, what: str = "call") -> int:
+    """Raise OilPaintError unless status == OP_OK."""
+    if status != OP_OK:
+        raise OilPaintError(f"{what} failed: {status_string(status)} ({status})", status)
+    return status
+
+
+# ---- same-named wrappers (argument marshalling only) ----------------------
+
+def op_create(width, height, stride, radius, levels):
+    return load().op_create(width, height, stride, radius, levels)
+
+
+def op_create_ex(width, height, stride, bpp, radius, levels, flags=OP_LEVEL_PAPER):
+    return load().op_create_ex(width, height, stride, bpp, radius, levels, flags)
+
+
+def op_last_error():
+    return load().op_last_error()
+
+
+def op_status_string(status):
+    return status_string(status)
+
+
+def op_get_config(op, cfg: op_config_t):
+    return load().op_get_config(op, ctypes.byref(cfg))
+
+
+def op_set_config(op, cfg: op_config_t):
+    return load().op_set_config(op, ctypes.byref(cfg))
+
+
+def op_default_config(radius, levels, cfg: op_config_t):
+    return load().op_default_config(radius, levels, ctypes.byref(cfg))
+
+
+def op_tune_table_set(radius, levels, cfg: op_config_t):
+    return load().op_tune_table_set(radius, levels, ctypes.byref(cfg))
+
+
+def op_workspace_size(op):
+    return load().op_workspace_size(op)
+
+
+def op_set_workspace(op, d_ws, nbytes):
+    return load().op_set_workspace(op, d_ws, nbytes)
+
+
+def op_run(op, d_in, d_out, stream=None):
+    return load().op_run(op, d_in, d_out, stream)
+
+
+def op_run_host(op, h_in, h_out, stream=None):
+    return load().op_run_host(op, h_in, h_out, stream)
+
+
+def op_set_profile_event(op, event):
+    return load().op_set_profile_event(op, event)
+
+
+def op_sync_status(op, stream=None):
+    return load().op_sync_status(op, stream)
+
+
+def op_destroy(op):
+    return load().op_destroy(op)
+
+
+def op_batch_create(max_images, max_pixels, max_radius, max_levels, cfg: op_config_t | None = None):
+    return load().op_batch_create(max_images, max_pixels, max_radius, max_levels,
+                                  ctypes.byref(cfg) if cfg is not None else None)
+
+
+def op_batch_workspace_size(b):
+    return load().op_batch_workspace_size(b)
+
+
+def op_batch_set_workspace(b, d_ws, nbytes):
+    return load().op_batch_set_workspace(b, d_ws, nbytes)
+
+
+def op_batch_set(b, images, n, stream=None):
+    return load().op_batch_set(b, images, n, stream)
+
+
+def op_batch_run(b, stream=None):
+    return load().op_batch_run(b, stream)
+
+
+def op_batch_capture(b, stream=None):
+    return load().op_batch_capture(b, stream)
+
+
+def op_batch_launch_graph(b, stream=None):
+    return load().op_batch_launch_graph(b, stream)
+
+
+def op_batch_sync_status(b, stream=None):
+    return load().op_batch_sync_status(b, stream)
+
+
+def op_batch_destroy(b):
+    return load().op_batch_destroy(b)
+
+
+def op_selftest_wait_timeout(timeout_ns, stream=None):
+    return load().op_selftest_wait_timeout(timeout_ns, stream)

@@ -1,0 +1,787 @@
+// oilpaint_api.cu -- the C ABI declared in include/oilpaint.h.
+//
+// Host side only: argument checks, launch configuration (tuning table,
+// automatic tile height), workspace management, TMA tensor-map encoding,
+// the batch descriptor tables and the CUDA-graph capture of a batch run.
+// All filtering happens in the kernels of oilpaint_kernels.cu.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "oilpaint.h"
+#include "oilpaint_internal.h"
+
+using opk::ImgDesc;
+using opk::RingCfg;
+
+namespace {
+
+thread_local int g_last_error = OP_OK;
+constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // bounded device waits give up after 1 s
+
+// ------------------------------------------------------------ tensor maps
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a packed image: w x h 32-bit words, rows ppitch words apart,
+// copied in {boxw, ch} boxes; out-of-range elements read as zero (the filter
+// never uses them: its windows are clipped to the image).
+int encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint32_t h,
+                      uint32_t ppitch, uint32_t boxw, uint32_t ch) {
+  auto fn = encode_fn();
+  if (!fn) return OP_E_CUDA;
+  cuuint64_t dims[2] = {w, h};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ppitch) * 4u};
+  cuuint32_t box[2] = {boxw, ch};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(packed), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? OP_OK : OP_E_CUDA;
+}
+
+// ------------------------------------------------------------ device info
+
+struct DevInfo {
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+int device_info(int dev, DevInfo *out) {
+  static std::mutex mu;
+  static std::map<int, DevInfo> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) {
+    *out = it->second;
+    return OP_OK;
+  }
+  DevInfo di;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return OP_E_CUDA;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return OP_E_CUDA;
+  di.smem_optin = static_cast<size_t>(v);
+  // The dynamic shared-memory limit is raised once per device and width to the maximum.
+  for (uint32_t tw : {32u, 64u, 128u, 256u})
+    if (opk::set_tile_smem_limit(tw, di.smem_optin - 1024u) != cudaSuccess) return OP_E_CUDA;
+  cache[dev] = di;
+  *out = di;
+  return OP_OK;
+}
+
+// ------------------------------------------------------------ configs
+
+std::mutex g_tune_mu;
+std::map<std::pair<int, uint32_t>, op_config_t> g_tune;
+
+bool tile_w_ok(uint32_t tw) { return tw == 32 || tw == 64 || tw == 128 || tw == 256; }
+
+size_t smem_for(const op_config_t &c, int r, uint32_t L) {
+  const RingCfg rc = opk::make_ring(r, c.chunk_rows, c.prefetch, opk::box_width(c.tile_w, r));
+  return opk::tile_smem_bytes(c.tile_w, L, opk::variant_for_radius(r), rc);
+}
+
+// Range checks plus "fits one CTA" for radius r and L levels.
+int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
+  if (!tile_w_ok(c.tile_w)) return OP_E_INVALID;
+  if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4)
+    return OP_E_INVALID;
+  if (c.tile_h > OP_MAX_DIM) return OP_E_INVALID;
+  if (opk::box_width(c.tile_w, r) > 256u) return OP_E_UNSUPPORTED;
+  if (smem_for(c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
+  return OP_OK;
+}
+
+// Built-in default: the widest tile whose histograms leave room for >= 2
+// CTAs per SM, 8-row halo chunks, 2 chunks in flight.
+op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
+  op_config_t best = {32, 0, 8, 2};
+  for (uint32_t tw : {128u, 64u, 32u}) {
+    op_config_t c = {tw, 0, 8, 2};
+    if (check_config(c, r, L, di) != OP_OK) continue;
+    if (smem_for(c, r, L) * 2 <= di.smem_optin || tw == 32) return c;
+  }
+  return best;
+}
+
+int pick_config(int r, uint32_t L, const DevInfo &di, op_config_t *out) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({r, L});
+    if (it != g_tune.end() && check_config(it->second, r, L, di) == OP_OK) {
+      *out = it->second;
+      return OP_OK;
+    }
+  }
+  *out = builtin_config(r, L, di);
+  return check_config(*out, r, L, di);
+}
+
+// Tile height that minimises (tiles per SM, rounded up) x (steps per tile),
+// where a tile of h output rows takes h + 2r steps; a penalty of 1.5 is
+// charged when an SM would hold a single CTA (too few warps to hide the
+// shared-memory latency).
+uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, int sms) {
+  double best = 1e300;
+  uint32_t best_h = H;
+  for (uint32_t t = 1; t <= H; ++t) {
+    const uint32_t th = (H + t - 1) / t;
+    if (t > 1 && (H + th - 1) / th != t) continue;  // same tiling as a smaller t
+    const uint64_t tiles = static_cast<uint64_t>(tiles_x) * t;
+    const uint64_t per_sm = (tiles + sms - 1) / sms;
+    double cost = static_cast<double>(per_sm) * (th + 2.0 * r);
+    if (per_sm < 2) cost *= 1.5;
+    if (cost < best) {
+      best = cost;
+      best_h = th;
+    }
+  }
+  return best_h;
+}
+
+uint32_t effective_tile_h(const op_config_t &c, uint32_t w, uint32_t h, int r, const DevInfo &di) {
+  if (c.tile_h) return std::min(c.tile_h, h);
+  return auto_tile_h(h, (w + c.tile_w - 1) / c.tile_w, r, di.sms);
+}
+
+bool valid_image(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int32_t r, uint32_t L,
+                 uint32_t flags) {
+  if (w < 1 || h < 1 || w > OP_MAX_DIM || h > OP_MAX_DIM) return false;
+  if (bpp != 3 && bpp != 4) return false;
+  if (static_cast<uint64_t>(stride) < static_cast<uint64_t>(w) * bpp) return false;
+  if (r < 0 || r > OP_MAX_RADIUS) return false;
+  if (L < 1 || L > OP_MAX_LEVELS) return false;
+  if (flags != OP_LEVEL_PAPER && flags != OP_LEVEL_INTDIV3) return false;
+  return true;
+}
+
+uint32_t packed_pitch(uint32_t w) { return (w + 3u) & ~3u; }
+
+bool ranges_overlap(const void *a, const void *b, size_t n) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + n && y < x + n;
+}
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return OP_OK;
+  return e == cudaErrorMemoryAllocation ? OP_E_NOMEM : OP_E_CUDA;
+}
+
+}  // namespace
+
+// ============================================================== single image
+
+struct op_s {
+  uint32_t w, h, stride, bpp;
+  int32_t r;
+  uint32_t L, flags;
+  int device;
+  DevInfo di;
+  op_config_t cfg;
+  uint32_t tile_h;  // effective tile height of cfg (auto_tile_h when cfg.tile_h == 0)
+  uint32_t ppitch;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  CUtensorMap map;
+  bool map_valid = false;
+  uint32_t *d_err = nullptr;
+  uint8_t *d_stage_in = nullptr, *d_stage_out = nullptr;
+  cudaEvent_t prof_ev = nullptr;
+};
+
+extern "C" {
+
+int op_last_error(void) { return g_last_error; }
+
+const char *op_status_string(int status) {
+  switch (status) {
+    case OP_OK: return "ok";
+    case OP_E_INVALID: return "invalid argument";
+    case OP_E_CUDA: return "CUDA error";
+    case OP_E_NOMEM: return "out of memory";
+    case OP_E_TIMEOUT: return "device wait timed out";
+    case OP_E_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+op_t *op_create_ex(uint32_t width, uint32_t height, uint32_t stride, uint32_t bpp, int32_t radius,
+                   uint32_t levels, uint32_t flags) {
+  if (!valid_image(width, height, stride, bpp, radius, levels, flags)) {
+    g_last_error = OP_E_INVALID;
+    return nullptr;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    g_last_error = OP_E_CUDA;
+    return nullptr;
+  }
+  DevInfo di;
+  int st = device_info(dev, &di);
+  if (st != OP_OK) {
+    g_last_error = st;
+    return nullptr;
+  }
+  op_config_t cfg;
+  st = pick_config(radius, levels, di, &cfg);
+  if (st != OP_OK) {
+    g_last_error = st;
+    return nullptr;
+  }
+  op_t *op = new (std::nothrow) op_t();
+  if (!op) {
+    g_last_error = OP_E_NOMEM;
+    return nullptr;
+  }
+  op->w = width;
+  op->h = height;
+  op->stride = stride;
+  op->bpp = bpp;
+  op->r = radius;
+  op->L = levels;
+  op->flags = flags;
+  op->device = dev;
+  op->di = di;
+  op->cfg = cfg;
+  op->tile_h = effective_tile_h(op->cfg, width, height, radius, di);
+  op->ppitch = packed_pitch(width);
+  if (cudaMalloc(&op->d_err, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(op->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+    cudaFree(op->d_err);
+    delete op;
+    g_last_error = OP_E_NOMEM;
+    return nullptr;
+  }
+  g_last_error = OP_OK;
+  return op;
+}
+
+op_t *op_create(uint32_t width, uint32_t height, uint32_t stride, int32_t radius,
+                uint32_t levels) {
+  const uint32_t bpp =
+      (static_cast<uint64_t>(stride) >= 4ull * width && stride % 4u == 0) ? 4u : 3u;
+  return op_create_ex(width, height, stride, bpp, radius, levels, OP_LEVEL_PAPER);
+}
+
+int op_get_config(const op_t *op, op_config_t *cfg) {
+  if (!op || !cfg) return OP_E_INVALID;
+  *cfg = op->cfg;
+  return OP_OK;
+}
+
+int op_set_config(op_t *op, const op_config_t *cfg) {
+  if (!op || !cfg) return OP_E_INVALID;
+  const int st = check_config(*cfg, op->r, op->L, op->di);
+  if (st != OP_OK) return st;
+  op->cfg = *cfg;
+  op->tile_h = effective_tile_h(op->cfg, op->w, op->h, op->r, op->di);
+  op->map_valid = false;
+  return OP_OK;
+}
+
+int op_default_config(int32_t radius, uint32_t levels, op_config_t *cfg) {
+  if (!cfg || radius < 0 || radius > OP_MAX_RADIUS || levels < 1 || levels > OP_MAX_LEVELS)
+    return OP_E_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OP_E_CUDA;
+  DevInfo di;
+  const int st = device_info(dev, &di);
+  if (st != OP_OK) return st;
+  return pick_config(radius, levels, di, cfg);
+}
+
+int op_tune_table_set(int32_t radius, uint32_t levels, const op_config_t *cfg) {
+  if (!cfg || radius < 0 || radius > OP_MAX_RADIUS || levels < 1 || levels > OP_MAX_LEVELS)
+    return OP_E_INVALID;
+  if (!tile_w_ok(cfg->tile_w) || cfg->chunk_rows < 1 || cfg->chunk_rows > 32 ||
+      cfg->prefetch < 1 || cfg->prefetch > 4 || cfg->tile_h > OP_MAX_DIM)
+    return OP_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[{radius, levels}] = *cfg;
+  return OP_OK;
+}
+
+size_t op_workspace_size(const op_t *op) {
+  if (!op) return 0;
+  return static_cast<size_t>(op->ppitch) * op->h * 4u;
+}
+
+int op_set_workspace(op_t *op, void *d_ws, size_t bytes) {
+  if (!op || !d_ws || bytes < op_workspace_size(op) || (reinterpret_cast<uintptr_t>(d_ws) & 15u))
+    return OP_E_INVALID;
+  if (op->ws_owned) cudaFree(op->ws);
+  op->ws = d_ws;
+  op->ws_bytes = bytes;
+  op->ws_owned = false;
+  op->map_valid = false;
+  return OP_OK;
+}
+
+static int ensure_workspace(op_t *op) {
+  if (op->ws) return OP_OK;
+  void *p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, op_workspace_size(op));
+  if (e != cudaSuccess) return cuda_status(e);
+  op->ws = p;
+  op->ws_bytes = op_workspace_size(op);
+  op->ws_owned = true;
+  op->map_valid = false;
+  return OP_OK;
+}
+
+int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
+  if (!op || !d_in || !d_out) return OP_E_INVALID;
+  const size_t bytes = static_cast<size_t>(op->h) * op->stride;
+  if (ranges_overlap(d_in, d_out, bytes)) return OP_E_INVALID;
+  int st = ensure_workspace(op);
+  if (st != OP_OK) return st;
+  const op_config_t &c = op->cfg;
+  const uint32_t boxw = opk::box_width(c.tile_w, op->r);
+  if (!op->map_valid) {
+    st = encode_packed_map(&op->map, static_cast<const uint32_t *>(op->ws), op->w, op->h,
+                           op->ppitch, boxw, c.chunk_rows);
+    if (st != OP_OK) return st;
+    op->map_valid = true;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ImgDesc d{};
+  d.in = d_in;
+  d.out = d_out;
+  d.packed = static_cast<uint32_t *>(op->ws);
+  d.tmap = nullptr;
+  d.w = op->w;
+  d.h = op->h;
+  d.stride = op->stride;
+  d.bpp = op->bpp;
+  d.r = op->r;
+  d.L = op->L;
+  d.mode = op->flags;
+  d.ppitch = op->ppitch;
+  d.tiles_x = (op->w + c.tile_w - 1) / c.tile_w;
+  d.tile_h = op->tile_h;
+  d.boxw = boxw;
+  d.variant = static_cast<uint32_t>(opk::variant_for_radius(op->r));
+  const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, boxw);
+  const size_t smem = opk::tile_smem_bytes(c.tile_w, op->L, static_cast<int>(d.variant), rc);
+  const int pack_grid = static_cast<int>(std::min<uint32_t>(op->h, 8u * op->di.sms));
+  cudaError_t e = opk::launch_pack_single(d, pack_grid, s);
+  if (e != cudaSuccess) return OP_E_CUDA;
+  if (op->prof_ev && cudaEventRecord(op->prof_ev, s) != cudaSuccess) return OP_E_CUDA;
+  const dim3 grid(d.tiles_x, (op->h + d.tile_h - 1) / d.tile_h);
+  e = opk::launch_tile_plain(c.tile_w, static_cast<int>(d.variant), d, op->map, rc, grid, smem,
+                             op->d_err, kWaitTimeoutNs, s);
+  return e == cudaSuccess ? OP_OK : OP_E_CUDA;
+}
+
+int op_run_host(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream) {
+  if (!op || !h_in || !h_out) return OP_E_INVALID;
+  const size_t bytes = static_cast<size_t>(op->h) * op->stride;
+  if (ranges_overlap(h_in, h_out, bytes)) return OP_E_INVALID;
+  if (!op->d_stage_in) {
+    cudaError_t e = cudaMalloc(&op->d_stage_in, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMalloc(&op->d_stage_out, bytes);
+    if (e != cudaSuccess) {
+      cudaFree(op->d_stage_in);
+      op->d_stage_in = nullptr;
+      return cuda_status(e);
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(op->d_stage_in, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return OP_E_CUDA;
+  int st = op_run(op, op->d_stage_in, op->d_stage_out, stream);
+  if (st != OP_OK) return st;
+  const size_t row = static_cast<size_t>(op->w) * op->bpp;
+  if (cudaMemcpy2DAsync(h_out, op->stride, op->d_stage_out, op->stride, row, op->h,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return OP_E_CUDA;
+  return op_sync_status(op, stream);
+}
+
+int op_set_profile_event(op_t *op, void *event) {
+  if (!op) return OP_E_INVALID;
+  op->prof_ev = static_cast<cudaEvent_t>(event);
+  return OP_OK;
+}
+
+int op_sync_status(op_t *op, void *stream) {
+  if (!op) return OP_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return OP_E_CUDA;
+  uint32_t err = 0;
+  if (cudaMemcpy(&err, op->d_err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OP_E_CUDA;
+  if (err) {
+    if (cudaMemset(op->d_err, 0, sizeof(err)) != cudaSuccess) return OP_E_CUDA;
+    return OP_E_TIMEOUT;
+  }
+  return OP_OK;
+}
+
+int op_destroy(op_t *op) {
+  if (!op) return OP_OK;
+  if (op->ws_owned) cudaFree(op->ws);
+  cudaFree(op->d_err);
+  cudaFree(op->d_stage_in);
+  cudaFree(op->d_stage_out);
+  delete op;
+  return OP_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== batch
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct op_batch_s {
+  uint32_t max_images;
+  uint64_t max_pixels;
+  int32_t max_r;
+  uint32_t max_L;
+  int device;
+  DevInfo di;
+  op_config_t cfg;
+  RingCfg rc;
+  size_t smem;
+  int grid_persist, grid_pack;
+  // workspace layout
+  size_t off_ctrl, off_hdr, off_descs, off_maps, off_tile_prefix, off_row_prefix, off_packed, total;
+  size_t stage_bytes;  // hdr .. row_prefix, copied in one transfer
+  uint8_t *ws = nullptr;
+  bool ws_owned = false;
+  bool ctrl_clean = false;
+  uint8_t *h_stage = nullptr;  // pinned mirror of [hdr .. row_prefix]
+  cudaEvent_t stage_done = nullptr;
+  uint32_t n = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t max_radius,
+                            uint32_t max_levels, const op_config_t *cfg) {
+  if (max_images < 1 || max_images > (1u << 20) || max_pixels < 1 || max_radius < 0 ||
+      max_radius > OP_MAX_RADIUS || max_levels < 1 || max_levels > OP_MAX_LEVELS ||
+      max_pixels > (1ull << 34)) {
+    g_last_error = OP_E_INVALID;
+    return nullptr;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    g_last_error = OP_E_CUDA;
+    return nullptr;
+  }
+  DevInfo di;
+  int st = device_info(dev, &di);
+  if (st != OP_OK) {
+    g_last_error = st;
+    return nullptr;
+  }
+  op_config_t c;
+  if (cfg) {
+    c = *cfg;
+  } else {
+    st = pick_config(max_radius, max_levels, di, &c);
+    if (st != OP_OK) {
+      g_last_error = st;
+      return nullptr;
+    }
+  }
+  st = check_config(c, max_radius, max_levels, di);
+  if (st != OP_OK) {
+    g_last_error = st;
+    return nullptr;
+  }
+  op_batch_t *b = new (std::nothrow) op_batch_t();
+  if (!b) {
+    g_last_error = OP_E_NOMEM;
+    return nullptr;
+  }
+  b->max_images = max_images;
+  b->max_pixels = max_pixels;
+  b->max_r = max_radius;
+  b->max_L = max_levels;
+  b->device = dev;
+  b->di = di;
+  b->cfg = c;
+  b->rc = opk::make_ring(max_radius, c.chunk_rows, c.prefetch, opk::box_width(c.tile_w, max_radius));
+  b->smem = opk::tile_smem_bytes(c.tile_w, max_levels, opk::variant_for_radius(max_radius), b->rc);
+  const int occ = opk::tile_occupancy(c.tile_w, -1, b->smem);
+  if (occ < 1) {
+    delete b;
+    g_last_error = OP_E_UNSUPPORTED;
+    return nullptr;
+  }
+  b->grid_persist = occ * di.sms;
+  b->grid_pack = 8 * di.sms;
+  size_t o = 0;
+  b->off_ctrl = o;
+  o = align_up(o + 2 * sizeof(uint32_t), kAlign);
+  b->off_hdr = o;
+  o = align_up(o + sizeof(uint32_t), kAlign);
+  b->off_descs = o;
+  o = align_up(o + static_cast<size_t>(max_images) * sizeof(ImgDesc), kAlign);
+  b->off_maps = o;
+  o = align_up(o + static_cast<size_t>(max_images) * sizeof(CUtensorMap), kAlign);
+  b->off_tile_prefix = o;
+  o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
+  b->off_row_prefix = o;
+  o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
+  b->off_packed = o;
+  b->stage_bytes = o - b->off_hdr;
+  o = align_up(o + static_cast<size_t>(max_pixels) * 4u + static_cast<size_t>(max_images) * kAlign,
+               kAlign);
+  b->total = o;
+  if (cudaMallocHost(&b->h_stage, b->stage_bytes) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFreeHost(b->h_stage);
+    delete b;
+    g_last_error = OP_E_NOMEM;
+    return nullptr;
+  }
+  g_last_error = OP_OK;
+  return b;
+}
+
+size_t op_batch_workspace_size(const op_batch_t *b) { return b ? b->total : 0; }
+
+int op_batch_set_workspace(op_batch_t *b, void *d_ws, size_t bytes) {
+  if (!b || !d_ws || bytes < b->total || (reinterpret_cast<uintptr_t>(d_ws) & (kAlign - 1)))
+    return OP_E_INVALID;
+  if (b->ws_owned) cudaFree(b->ws);
+  b->ws = static_cast<uint8_t *>(d_ws);
+  b->ws_owned = false;
+  b->ctrl_clean = false;
+  if (b->exec) {  // a captured graph points at the old workspace
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return OP_OK;
+}
+
+int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stream) {
+  if (!b || (n && !images) || n > b->max_images) return OP_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!b->ws) {
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, b->total);
+    if (e != cudaSuccess) return cuda_status(e);
+    b->ws = static_cast<uint8_t *>(p);
+    b->ws_owned = true;
+    b->ctrl_clean = false;
+  }
+  // validate and order the images: most expensive tiles first
+  const uint32_t tw = b->cfg.tile_w;
+  std::vector<uint32_t> order(n);
+  std::vector<double> tile_cost(n);
+  std::vector<uint32_t> tile_h(n);
+  uint64_t padded = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const op_image_t &im = images[i];
+    if (!im.in || !im.out || im.reserved ||
+        !valid_image(im.width, im.height, im.stride, im.bpp, im.radius, im.levels, im.flags) ||
+        im.radius > b->max_r || im.levels > b->max_L)
+      return OP_E_INVALID;
+    if (ranges_overlap(im.in, im.out, static_cast<size_t>(im.height) * im.stride))
+      return OP_E_INVALID;
+    padded += static_cast<uint64_t>(packed_pitch(im.width)) * im.height;
+    uint32_t th = 0;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find({im.radius, im.levels});
+      if (it != g_tune.end()) th = it->second.tile_h;
+    }
+    if (th == 0) th = std::max<uint32_t>(64u, 16u * static_cast<uint32_t>(im.radius));
+    th = std::min(th, im.height);
+    tile_h[i] = th;
+    const double r = im.radius;
+    tile_cost[i] = (th + 2.0 * r) * (4.0 * r + 2.0) + th * (im.levels + 10.0);
+    order[i] = i;
+  }
+  if (padded > b->max_pixels) return OP_E_INVALID;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t a, uint32_t c) { return tile_cost[a] > tile_cost[c]; });
+  // the previous op_batch_set's copy must have left the pinned staging buffer
+  if (cudaEventSynchronize(b->stage_done) != cudaSuccess) return OP_E_CUDA;
+  uint32_t *hn = reinterpret_cast<uint32_t *>(b->h_stage);
+  ImgDesc *hd = reinterpret_cast<ImgDesc *>(b->h_stage + (b->off_descs - b->off_hdr));
+  CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(b->h_stage + (b->off_maps - b->off_hdr));
+  uint32_t *htp = reinterpret_cast<uint32_t *>(b->h_stage + (b->off_tile_prefix - b->off_hdr));
+  uint32_t *hrp = reinterpret_cast<uint32_t *>(b->h_stage + (b->off_row_prefix - b->off_hdr));
+  const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(b->ws + b->off_maps);
+  size_t poff = b->off_packed;
+  uint64_t tiles = 0, rows = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const op_image_t &im = images[order[k]];
+    ImgDesc d{};
+    d.in = im.in;
+    d.out = im.out;
+    d.packed = reinterpret_cast<uint32_t *>(b->ws + poff);
+    d.tmap = dmaps + k;
+    d.w = im.width;
+    d.h = im.height;
+    d.stride = im.stride;
+    d.bpp = im.bpp;
+    d.r = im.radius;
+    d.L = im.levels;
+    d.mode = im.flags;
+    d.ppitch = packed_pitch(im.width);
+    d.tile_h = tile_h[order[k]];
+    d.tiles_x = (im.width + tw - 1) / tw;
+    d.boxw = opk::box_width(tw, im.radius);
+    d.variant = static_cast<uint32_t>(opk::variant_for_radius(im.radius));
+    const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc.ch);
+    if (st != OP_OK) return st;
+    hd[k] = d;
+    htp[k] = static_cast<uint32_t>(tiles);
+    hrp[k] = static_cast<uint32_t>(rows);
+    tiles += static_cast<uint64_t>(d.tiles_x) * ((d.h + d.tile_h - 1) / d.tile_h);
+    rows += d.h;
+    poff = align_up(poff + static_cast<size_t>(d.ppitch) * d.h * 4u, kAlign);
+  }
+  if (tiles >= 0xFFFFFFFFull || poff > b->total) return OP_E_INVALID;
+  htp[n] = static_cast<uint32_t>(tiles);
+  hrp[n] = static_cast<uint32_t>(rows);
+  *hn = n;
+  if (!b->ctrl_clean) {
+    if (cudaMemsetAsync(b->ws + b->off_ctrl, 0, 2 * sizeof(uint32_t), s) != cudaSuccess)
+      return OP_E_CUDA;
+    b->ctrl_clean = true;
+  }
+  if (cudaMemcpyAsync(b->ws + b->off_hdr, b->h_stage, b->stage_bytes, cudaMemcpyHostToDevice,
+                      s) != cudaSuccess ||
+      cudaEventRecord(b->stage_done, s) != cudaSuccess)
+    return OP_E_CUDA;
+  b->n = n;
+  return OP_OK;
+}
+
+int op_batch_run(op_batch_t *b, void *stream) {
+  if (!b || !b->ws) return OP_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t *ctrl = reinterpret_cast<uint32_t *>(b->ws + b->off_ctrl);
+  const uint32_t *d_n = reinterpret_cast<const uint32_t *>(b->ws + b->off_hdr);
+  const ImgDesc *descs = reinterpret_cast<const ImgDesc *>(b->ws + b->off_descs);
+  const uint32_t *tp = reinterpret_cast<const uint32_t *>(b->ws + b->off_tile_prefix);
+  const uint32_t *rp = reinterpret_cast<const uint32_t *>(b->ws + b->off_row_prefix);
+  // Fixed grids; the image count and the tables are read from device memory,
+  // so the launches do not depend on the current batch and a captured graph
+  // stays valid across op_batch_set calls.
+  cudaError_t e = opk::launch_pack_batch(descs, rp, d_n, ctrl, b->grid_pack, s);
+  if (e != cudaSuccess) return OP_E_CUDA;
+  e = opk::launch_persistent(b->cfg.tile_w, descs, tp, d_n, ctrl, b->rc, b->max_L,
+                             b->grid_persist, b->smem, ctrl + 1, kWaitTimeoutNs, s);
+  return e == cudaSuccess ? OP_OK : OP_E_CUDA;
+}
+
+int op_batch_capture(op_batch_t *b, void *stream) {
+  if (!b || !b->ws) return OP_E_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return OP_E_CUDA;
+  const int st = op_batch_run(b, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != OP_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return st != OP_OK ? st : OP_E_CUDA;
+  }
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    b->exec = nullptr;
+    return OP_E_CUDA;
+  }
+  b->graph = g;
+  return OP_OK;
+}
+
+int op_batch_launch_graph(op_batch_t *b, void *stream) {
+  if (!b || !b->exec) return OP_E_INVALID;
+  return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? OP_OK
+                                                                                      : OP_E_CUDA;
+}
+
+int op_batch_sync_status(op_batch_t *b, void *stream) {
+  if (!b || !b->ws) return OP_E_INVALID;
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return OP_E_CUDA;
+  uint32_t err = 0;
+  uint32_t *d_err = reinterpret_cast<uint32_t *>(b->ws + b->off_ctrl) + 1;
+  if (cudaMemcpy(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return OP_E_CUDA;
+  if (err) {
+    if (cudaMemset(d_err, 0, sizeof(err)) != cudaSuccess) return OP_E_CUDA;
+    return OP_E_TIMEOUT;
+  }
+  return OP_OK;
+}
+
+int op_batch_destroy(op_batch_t *b) {
+  if (!b) return OP_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->stage_done) cudaEventDestroy(b->stage_done);
+  if (b->ws_owned) cudaFree(b->ws);
+  cudaFreeHost(b->h_stage);
+  delete b;
+  return OP_OK;
+}
+
+int op_selftest_wait_timeout(uint64_t timeout_ns, void *stream) {
+  if (timeout_ns < 1 || timeout_ns > 2000000000ull) return OP_E_INVALID;
+  uint32_t *d_err = nullptr;
+  if (cudaMalloc(&d_err, sizeof(uint32_t)) != cudaSuccess) return OP_E_NOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = OP_OK;
+  if (cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s) != cudaSuccess ||
+      opk::launch_selftest_wait(d_err, timeout_ns, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    st = OP_E_CUDA;
+  } else {
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = OP_E_CUDA;
+    else if (err & opk::kErrTimeout)
+      st = OP_E_TIMEOUT;
+  }
+  cudaFree(d_err);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+"""Torch-facing wrappers over the C ABI.
+
+PyTorch provides device memory (the workspace and the image tensors) and
+streams; every step of the filter runs in the library's CUDA kernels.  There
+is no CPU path: without the built library every call raises OilPaintError.
+"""
+from __future__ import annotations
+
+from typing import Iterable, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check_dev_buf(t: torch.Tensor, nbytes: int, name: str) -> None:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise B.OilPaintError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.uint8 or not t.is_contiguous():
+        raise B.OilPaintError(f"{name} must be a contiguous uint8 tensor")
+    if t.numel() < nbytes:
+        raise B.OilPaintError(f"{name} holds {t.numel()} bytes, needs {nbytes}")
+
+
+def _config(cfg) -> B.op_config_t:
+    if cfg is None or isinstance(cfg, B.op_config_t):
+        return cfg
+    d = dict(cfg)
+    return B.op_config_t.make(d.get("tile_w", 128), d.get("tile_h", 0), d.get("chunk_rows", 8),
+                              d.get("prefetch", 2))
+
+
+class OilPaint:
+    """One image geometry: width x height pixels, `bpp` bytes per pixel, rows
+    `stride` bytes apart, radius r, L levels (section 4's filter)."""
+
+    def __init__(self, width: int, height: int, radius: int, levels: int, bpp: int = 3,
+                 stride: int | None = None, flags: int = B.OP_LEVEL_PAPER, config=None,
+                 device: int | torch.device | None = None):
+        self.width, self.height, self.radius, self.levels = width, height, radius, levels
+        self.bpp = bpp
+        self.stride = stride if stride is not None else width * bpp
+        self.flags = flags
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self._h = None
+        with torch.cuda.device(self.device):
+            h = B.op_create_ex(width, height, self.stride, bpp, radius, levels, flags)
+            if not h:
+                st = B.op_last_error()
+                raise B.OilPaintError(f"op_create_ex: {B.status_string(st)}", st)
+            self._h = h
+            if config is not None:
+                B.check(B.op_set_config(h, _config(config)), "op_set_config")
+            n = B.op_workspace_size(h)
+            self._ws = torch.empty(max(n, 16), dtype=torch.uint8, device=self.device)
+            B.check(B.op_set_workspace(h, self._ws.data_ptr(), self._ws.numel()),
+                    "op_set_workspace")
+
+    @property
+    def nbytes(self) -> int:
+        return self.height * self.stride
+
+    @property
+    def handle(self):
+        return self._h
+
+    def config(self) -> dict:
+        c = B.op_config_t()
+        B.check(B.op_get_config(self._h, c), "op_get_config")
+        return c.as_dict()
+
+    def set_config(self, cfg) -> None:
+        B.check(B.op_set_config(self._h, _config(cfg)), "op_set_config")
+
+    def run(self, src: torch.Tensor, dst: torch.Tensor, stream=None) -> None:
+        """Asynchronous on `stream` (default: torch's current stream)."""
+        _check_dev_buf(src, self.nbytes, "src")
+        _check_dev_buf(dst, self.nbytes, "dst")
+        B.check(B.op_run(self._h, src.data_ptr(), dst.data_ptr(), _stream_handle(stream)),
+                "op_run")
+
+    def __call__(self, src: torch.Tensor, dst: torch.Tensor | None = None, stream=None):
+        if dst is None:
+            dst = torch.empty_like(src)
+        self.run(src, dst, stream)
+        return dst
+
+    def run_host(self, h_in, h_out, stream=None) -> None:
+        """Host buffers in and out (numpy arrays or CPU tensors, ideally pinned);
+        synchronous."""
+        def ptr(a):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.uint8 or not a.is_contiguous():
+                    raise B.OilPaintError("host buffers must be contiguous uint8 CPU tensors")
+                if a.numel() < self.nbytes:
+                    raise B.OilPaintError("host buffer too small")
+                return a.data_ptr()
+            a = np.asarray(a)
+            if a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"] or a.size < self.nbytes:
+                raise B.OilPaintError("host buffers must be contiguous uint8 arrays")
+            return a.ctypes.data
+        B.check(B.op_run_host(self._h, ptr(h_in), ptr(h_out), _stream_handle(stream)),
+                "op_run_host")
+
+    def sync_status(self, stream=None) -> int:
+        return B.op_sync_status(self._h, _stream_handle(stream))
+
+    def close(self) -> None:
+        if self._h:
+            B.op_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many images in one persistent launch (see op_batch_create)."""
+
+    def __init__(self, max_images: int, max_pixels: int, max_radius: int, max_levels: int,
+                 config=None, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        self._h = None
+        with torch.cuda.device(self.device):
+            h = B.op_batch_create(max_images, max_pixels, max_radius, max_levels, _config(config))
+            if not h:
+                st = B.op_last_error()
+                raise B.OilPaintError(f"op_batch_create: {B.status_string(st)}", st)
+            self._h = h
+            n = B.op_batch_workspace_size(h)
+            self._ws = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+            base = self._ws.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            B.check(B.op_batch_set_workspace(h, aligned, n), "op_batch_set_workspace")
+        self._keep: list = []
+        self.n = 0
+
+    @staticmethod
+    def padded_pixels(images: Iterable[tuple]) -> int:
+        """Pixels the batch workspace needs for images given as (w, h, ...)."""
+        return sum(((w + 3) // 4 * 4) * h for w, h, *_ in images)
+
+    def set(self, images: Sequence[tuple], stream=None) -> None:
+        """images: (src, dst, width, height, stride, bpp, radius, levels[, flags])
+        with src/dst CUDA uint8 tensors."""
+        arr = (B.op_image_t * max(1, len(images)))()
+        keep = []
+        for i, im in enumerate(images):
+            src, dst, w, h, stride, bpp, r, L = im[:8]
+            flags = im[8] if len(im) > 8 else B.OP_LEVEL_PAPER
+            _check_dev_buf(src, h * stride, f"images[{i}].src")
+            _check_dev_buf(dst, h * stride, f"images[{i}].dst")
+            arr[i] = B.op_image_t(src.data_ptr(), dst.data_ptr(), w, h, stride, bpp, r, L, flags, 0)
+            keep += [src, dst]
+        B.check(B.op_batch_set(self._h, arr, len(images), _stream_handle(stream)), "op_batch_set")
+        self._keep = keep
+        self.n = len(images)
+
+    def run(self, stream=None) -> None:
+        B.check(B.op_batch_run(self._h, _stream_handle(stream)), "op_batch_run")
+
+    def capture(self, stream) -> None:
+        """Capture run() into a CUDA graph; `stream` must be a non-default stream."""
+        B.check(B.op_batch_capture(self._h, _stream_handle(stream)), "op_batch_capture")
+
+    def launch_graph(self, stream=None) -> None:
+        B.check(B.op_batch_launch_graph(self._h, _stream_handle(stream)), "op_batch_launch_graph")
+
+    def sync_status(self, stream=None) -> int:
+        return B.op_batch_sync_status(self._h, _stream_handle(stream))
+
+    def close(self) -> None:
+        if self._h:
+            B.op_batch_destroy(self._h)
+            self._h = None
+            self._ws = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -1,0 +1,223 @@
+"""CUDA path vs the CPU oracle, byte for byte, through the C ABI.
+
+Every comparison covers the whole output buffer: pixel bytes must equal the
+oracle's, alpha must be copied, and row padding must keep the fill byte both
+sides started from.
+"""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle
+from paper_1405_1020_gb300 import binding as B
+from paper_1405_1020_gb300 import synth
+from paper_1405_1020_gb300.filter import OilPaint
+from tests.pins import OUT_FILL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def gpu_filter(buf, w, h, stride, bpp, r, L, mode=0, config=None):
+    src = torch.from_numpy(np.ascontiguousarray(buf)).cuda()
+    dst = torch.full_like(src, OUT_FILL)
+    op = OilPaint(w, h, r, L, bpp=bpp, stride=stride, flags=mode, config=config)
+    op.run(src, dst)
+    assert op.sync_status() == B.OP_OK
+    out = dst.cpu().numpy()
+    op.close()
+    return out
+
+
+def cpu_filter(buf, w, h, stride, bpp, r, L, mode=0):
+    out = np.full(buf.size, OUT_FILL, np.uint8)
+    return oracle.oilpaint(buf, w, h, stride, bpp, r, L, mode=mode, out=out)
+
+
+def assert_same(got, want, w, h, stride, bpp, what=""):
+    if np.array_equal(got, want):
+        return
+    g = got[: h * stride].reshape(h, stride)
+    e = want[: h * stride].reshape(h, stride)
+    ys, xs = np.nonzero(g != e)
+    msg = f"{what}: {ys.size} bytes differ; first at row {ys[0]}, byte {xs[0]} " \
+          f"(pixel {xs[0] // bpp}, channel {xs[0] % bpp}): got {g[ys[0], xs[0]]} want {e[ys[0], xs[0]]}"
+    raise AssertionError(msg)
+
+
+def check_case(img, r, L, bpp=3, pad=0, mode=0, config=None, what=""):
+    h, w = img.shape[:2]
+    buf, stride = synth.to_strided(img, bpp=bpp, stride=w * bpp + pad)
+    got = gpu_filter(buf, w, h, stride, bpp, r, L, mode, config)
+    want = cpu_filter(buf, w, h, stride, bpp, r, L, mode)
+    assert_same(got, want, w, h, stride, bpp, what or f"{w}x{h} r={r} L={L} bpp={bpp}")
+
+
+# ---- the workloads ---------------------------------------------------------
+
+def test_uniform_256_r2_L20():
+    """256x256 i.i.d. uniform RGB (seed 0), r=2, L=20: whole image."""
+    check_case(synth.uniform_rgb(256, 256, seed=0), 2, 20)
+
+
+@pytest.fixture(scope="module")
+def blobs_fhd():
+    return synth.blobs_rgb(1080, 1920, seed=1)
+
+
+@pytest.mark.parametrize("r", list(range(1, 11)))
+def test_blobs_1920x1080_radius_sweep(blobs_fhd, r):
+    """1920x1080 blobs (seed 1), r = 1..10, L=20: whole image."""
+    check_case(blobs_fhd, r, 20)
+
+
+@pytest.fixture(scope="module")
+def camera_12mp():
+    img = synth.camera_like(3000, 4000, seed=2)
+    buf, stride = synth.to_strided(img, bpp=4, stride=16000)
+    return buf, stride
+
+
+def _sample_rows(h, r, n, seed):
+    rng = np.random.default_rng(seed)
+    rows = set(range(0, min(h, r + 2))) | set(range(max(0, h - r - 2), h))
+    rows |= set(int(v) for v in rng.integers(0, h, n))
+    return sorted(rows)
+
+
+@pytest.mark.parametrize("L", [20, 64, 256])
+def test_camera_12mp_rgba_r15_sampled_rows(camera_12mp, L):
+    """4000x3000 RGBA-stride camera-like (seed 2), r=15: the whole GPU output
+    against oracle rows covering both borders plus random rows."""
+    buf, stride = camera_12mp
+    w, h, r = 4000, 3000, 15
+    got = gpu_filter(buf, w, h, stride, 4, r, L)
+    rows = _sample_rows(h, r, 24, seed=L)
+    want = np.full(buf.size, OUT_FILL, np.uint8)
+    for y in rows:
+        oracle.oilpaint_rows(buf, w, h, stride, 4, r, L, y, y + 1, out=want)
+    g = got[: h * stride].reshape(h, stride)
+    e = want[: h * stride].reshape(h, stride)
+    for y in rows:
+        assert np.array_equal(g[y], e[y]), f"row {y} differs (L={L})"
+    # random single pixels anywhere
+    rng = np.random.default_rng(100 + L)
+    xs = rng.integers(0, w, 300)
+    ys = rng.integers(0, h, 300)
+    rgb = oracle.oilpaint_pixels(buf, w, h, stride, 4, r, L, xs, ys)
+    px = oracle.view_pixels(got, w, h, stride, 4)
+    assert np.array_equal(px[ys, xs, :3], rgb)
+    assert (px[..., 3] == 255).all()
+
+
+# ---- fuzz grid ---------------------------------------------------------------
+
+def _fuzz_cases(n=48, seed=7):
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n):
+        w = int(rng.choice([1, 2, 3, 5, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200, 257, 300]))
+        h = int(rng.choice([1, 2, 7, 8, 9, 17, 40, 100, 161, 300]))
+        r = int(rng.choice([0, 1, 2, 3, 7, 15, 16, 20, 31, 44]))
+        L = int(rng.choice([1, 2, 3, 16, 20, 32, 64, 128, 255, 256]))
+        bpp = int(rng.choice([3, 4]))
+        pad = int(rng.choice([0, 1, 4, 13]))
+        mode = int(rng.integers(0, 2))
+        tw = int(rng.choice([32, 64, 128]))
+        cfg = {"tile_w": tw, "tile_h": int(rng.choice([0, 1, 5, 16, 64])),
+               "chunk_rows": int(rng.choice([1, 2, 3, 8, 16, 32])),
+               "prefetch": int(rng.integers(1, 5))}
+        cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
+    return cases
+
+
+@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _fuzz_cases())
+def test_fuzz(k, w, h, r, L, bpp, pad, mode, cfg):
+    img = synth.camera_like(h, w, seed=500 + k, npoly=12, rad_range=(1, 60)) if k % 2 else \
+        synth.uniform_rgb(h, w, seed=500 + k)
+    try:
+        check_case(img, r, L, bpp, pad, mode, cfg)
+    except B.OilPaintError as e:
+        # the only acceptable refusal: a tile too wide for the radius or shared memory
+        assert e.status == B.OP_E_UNSUPPORTED, e
+
+
+# ---- edge cases --------------------------------------------------------------
+
+@pytest.mark.parametrize("w,h,r,L", [
+    (1, 1, 0, 1), (1, 1, 5, 256), (1, 37, 3, 20), (37, 1, 3, 20), (3, 2, 44, 20),
+    (128, 128, 15, 256), (128, 128, 16, 256), (129, 65, 44, 256), (300, 45, 44, 1),
+    (257, 33, 15, 20), (64, 300, 20, 32),
+])
+def test_edge_shapes(w, h, r, L):
+    img = synth.camera_like(h, w, seed=w * 1000 + h, npoly=8, rad_range=(1, 50))
+    check_case(img, r, L, bpp=3, pad=3)
+    check_case(img, r, L, bpp=4, pad=0)
+
+
+def test_constant_white_and_black():
+    for colour in (255, 0):
+        img = np.full((70, 90, 3), colour, np.uint8)
+        for L in (1, 20, 256):
+            check_case(img, 6, L)
+
+
+def test_every_config_gives_the_same_bytes():
+    img = synth.camera_like(233, 301, seed=9, npoly=30, rad_range=(3, 120))
+    h, w = img.shape[:2]
+    buf, stride = synth.to_strided(img, bpp=3, stride=w * 3 + 2)
+    want = cpu_filter(buf, w, h, stride, 3, 9, 20)
+    for tw in (32, 64, 128):
+        for ch in (1, 4, 8, 16):
+            for pf in (1, 2, 4):
+                for th in (0, 1, 23, 233):
+                    cfg = {"tile_w": tw, "tile_h": th, "chunk_rows": ch, "prefetch": pf}
+                    got = gpu_filter(buf, w, h, stride, 3, 9, 20, config=cfg)
+                    assert_same(got, want, w, h, stride, 3, str(cfg))
+
+
+def test_tile_w_256_only_without_halo():
+    op = OilPaint(300, 20, 0, 20)
+    op.set_config({"tile_w": 256})  # r = 0: the 256-word box fits
+    op.close()
+    op = OilPaint(300, 20, 1, 20)
+    with pytest.raises(B.OilPaintError) as e:
+        op.set_config({"tile_w": 256})
+    assert e.value.status == B.OP_E_UNSUPPORTED
+    op.close()
+    check_case(synth.uniform_rgb(40, 600, seed=3), 0, 20, config={"tile_w": 256})
+
+
+def test_run_host_matches_oracle():
+    img = synth.blobs_rgb(180, 250, seed=4, nblobs=10, sigma_range=(5, 40))
+    h, w = img.shape[:2]
+    buf, stride = synth.to_strided(img, bpp=4, stride=w * 4 + 8)
+    op = OilPaint(w, h, 5, 20, bpp=4, stride=stride)
+    out = np.full(buf.size, OUT_FILL, np.uint8)
+    op.run_host(buf, out)
+    op.close()
+    assert_same(out, cpu_filter(buf, w, h, stride, 4, 5, 20), w, h, stride, 4, "run_host")
+
+
+def test_invalid_calls_on_device():
+    op = OilPaint(64, 32, 3, 20)
+    src = torch.zeros(op.nbytes, dtype=torch.uint8, device="cuda")
+    assert B.op_run(op.handle, src.data_ptr(), src.data_ptr(), None) == B.OP_E_INVALID
+    assert B.op_run(op.handle, src.data_ptr(), src.data_ptr() + 16, None) == B.OP_E_INVALID
+    assert B.op_set_workspace(op.handle, src.data_ptr(), 16) == B.OP_E_INVALID
+    assert B.op_set_config(op.handle, B.op_config_t.make(48)) == B.OP_E_INVALID
+    assert B.op_set_config(op.handle, B.op_config_t.make(64, chunk_rows=40)) == B.OP_E_INVALID
+    op.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A wait on an mbarrier nothing completes gives up after the limit and
+    reports OP_E_TIMEOUT; the context keeps working afterwards."""
+    assert B.op_selftest_wait_timeout(20_000_000, None) == B.OP_E_TIMEOUT
+    check_case(synth.uniform_rgb(50, 60, seed=6), 2, 20)
