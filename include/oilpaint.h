@@ -65,17 +65,24 @@ typedef struct op_s op_t;
 /*
  * Launch configuration of the filter kernel.  op_create picks it from the
  * tuning table (see op_tune_table_set); the autotuner overrides it.
- *   tile_w     output columns per CTA = threads per CTA: 32, 64, 128 or 256;
- *   tile_h     output rows per CTA (0 = chosen from the image size and the
- *              number of resident CTAs);
- *   chunk_rows input rows per TMA halo copy, 1..32;
- *   prefetch   halo copies in flight ahead of the one being consumed, 1..4.
+ *   tile_w          output columns per CTA = threads x cols_per_thread, with
+ *                   32, 64, 96 or 128 threads;
+ *   tile_h          output rows per CTA (0 = chosen from the image size and
+ *                   the number of resident CTAs);
+ *   chunk_rows      input rows per TMA halo copy, 1..32;
+ *   prefetch        halo copies in flight ahead of the one being consumed, 1..4;
+ *   cols_per_thread output columns per thread: 1 (one running histogram per
+ *                   output column) or 2 (two neighbouring columns share the
+ *                   2r window columns they have in common); 0 = 1.
+ * The halo copy of a tile is tile_w + 2r + up to 3 columns wide and must not
+ * exceed 256 columns.
  */
 typedef struct {
   uint32_t tile_w;
   uint32_t tile_h;
   uint32_t chunk_rows;
   uint32_t prefetch;
+  uint32_t cols_per_thread;
 } op_config_t;
 
 /*
@@ -185,6 +192,10 @@ typedef struct op_batch_s op_batch_t;
  */
 op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t max_radius,
                             uint32_t max_levels, const op_config_t *cfg);
+
+/* Launch configuration of the batch's persistent kernel into *cfg (tile_h
+ * is 0: it is chosen per image). */
+int op_batch_get_config(const op_batch_t *b, op_config_t *cfg);
 
 /* Device workspace a batch needs: descriptors, tensor maps, tile tables and
  * the packed-word images of max_pixels pixels. */

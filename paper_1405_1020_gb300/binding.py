@@ -36,7 +36,8 @@ EXPORTS = (
     "op_set_config", "op_default_config", "op_tune_table_set", "op_workspace_size",
     "op_set_workspace", "op_run", "op_run_host", "op_set_profile_event", "op_sync_status",
     "op_destroy",
-    "op_batch_create", "op_batch_workspace_size", "op_batch_set_workspace", "op_batch_set",
+    "op_batch_create", "op_batch_get_config", "op_batch_workspace_size",
+    "op_batch_set_workspace", "op_batch_set",
     "op_batch_run", "op_batch_capture", "op_batch_launch_graph", "op_batch_sync_status",
     "op_batch_destroy", "op_selftest_wait_timeout",
 )
@@ -52,14 +53,16 @@ class OilPaintError(RuntimeError):
 
 class op_config_t(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_uint32), ("tile_h", ctypes.c_uint32),
-                ("chunk_rows", ctypes.c_uint32), ("prefetch", ctypes.c_uint32)]
+                ("chunk_rows", ctypes.c_uint32), ("prefetch", ctypes.c_uint32),
+                ("cols_per_thread", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
     @classmethod
-    def make(cls, tile_w: int, tile_h: int = 0, chunk_rows: int = 8, prefetch: int = 2):
-        return cls(tile_w, tile_h, chunk_rows, prefetch)
+    def make(cls, tile_w: int, tile_h: int = 0, chunk_rows: int = 8, prefetch: int = 2,
+             cols_per_thread: int = 1):
+        return cls(tile_w, tile_h, chunk_rows, prefetch, cols_per_thread)
 
 
 class op_image_t(ctypes.Structure):
@@ -101,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "op_sync_status": (ci, [vp, vp]),
         "op_destroy": (ci, [vp]),
         "op_batch_create": (vp, [u32, u64, i32, u32, cfgp]),
+        "op_batch_get_config": (ci, [vp, cfgp]),
         "op_batch_workspace_size": (sz, [vp]),
         "op_batch_set_workspace": (ci, [vp, vp, sz]),
         "op_batch_set": (ci, [vp, ctypes.POINTER(op_image_t), u32, vp]),
@@ -195,6 +199,10 @@ def op_destroy(op):
 def op_batch_create(max_images, max_pixels, max_radius, max_levels, cfg: op_config_t | None = None):
     return load().op_batch_create(max_images, max_pixels, max_radius, max_levels,
                                   ctypes.byref(cfg) if cfg is not None else None)
+
+
+def op_batch_get_config(b, cfg: op_config_t):
+    return load().op_batch_get_config(b, ctypes.byref(cfg))
 
 
 def op_batch_workspace_size(b):

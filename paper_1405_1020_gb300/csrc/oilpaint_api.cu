@@ -81,9 +81,8 @@ int device_info(int dev, DevInfo *out) {
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return OP_E_CUDA;
   di.smem_optin = static_cast<size_t>(v);
-  // The dynamic shared-memory limit is raised once per device and width to the maximum.
-  for (uint32_t tw : {32u, 64u, 128u, 256u})
-    if (opk::set_tile_smem_limit(tw, di.smem_optin - 1024u) != cudaSuccess) return OP_E_CUDA;
+  // The dynamic shared-memory limit is raised once per device to the maximum.
+  if (opk::set_tile_smem_limit(di.smem_optin - 1024u) != cudaSuccess) return OP_E_CUDA;
   cache[dev] = di;
   *out = di;
   return OP_OK;
@@ -94,34 +93,48 @@ int device_info(int dev, DevInfo *out) {
 std::mutex g_tune_mu;
 std::map<std::pair<int, uint32_t>, op_config_t> g_tune;
 
-bool tile_w_ok(uint32_t tw) { return tw == 32 || tw == 64 || tw == 128 || tw == 256; }
+// Output columns per thread and threads per CTA of a configuration.
+int cols_per_thread(const op_config_t &c) { return c.cols_per_thread == 2 ? 2 : 1; }
+uint32_t threads_of(const op_config_t &c) { return c.tile_w / cols_per_thread(c); }
+
+// Range checks that need no device.
+bool config_in_range(const op_config_t &c) {
+  if (c.cols_per_thread > 2) return false;
+  const uint32_t cpt = static_cast<uint32_t>(cols_per_thread(c));
+  if (c.tile_w % cpt) return false;
+  const uint32_t nt = c.tile_w / cpt;
+  if (nt != 32 && nt != 64 && nt != 96 && nt != 128) return false;
+  if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4) return false;
+  return c.tile_h <= OP_MAX_DIM;
+}
 
 size_t smem_for(const op_config_t &c, int r, uint32_t L) {
   const RingCfg rc = opk::make_ring(r, c.chunk_rows, c.prefetch, opk::box_width(c.tile_w, r));
-  return opk::tile_smem_bytes(c.tile_w, L, opk::variant_for_radius(r), rc);
+  return opk::tile_smem_bytes(threads_of(c), cols_per_thread(c), L, opk::variant_for_radius(r),
+                              rc);
 }
 
 // Range checks plus "fits one CTA" for radius r and L levels.
 int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
-  if (!tile_w_ok(c.tile_w)) return OP_E_INVALID;
-  if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4)
-    return OP_E_INVALID;
-  if (c.tile_h > OP_MAX_DIM) return OP_E_INVALID;
+  if (!config_in_range(c)) return OP_E_INVALID;
   if (opk::box_width(c.tile_w, r) > 256u) return OP_E_UNSUPPORTED;
   if (smem_for(c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
   return OP_OK;
 }
 
-// Built-in default: the widest tile whose histograms leave room for >= 2
-// CTAs per SM, 8-row halo chunks, 2 chunks in flight.
+// Built-in default: the first of a preference list whose shared memory
+// leaves room for >= 2 CTAs per SM, 8-row halo chunks, one chunk in flight.
+// (Measured on GB300: one column per thread beats two at every tested
+// radius and level count, because three histograms per thread cap the
+// resident warps; 64-128 threads are within a few percent of each other.)
 op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
-  op_config_t best = {32, 0, 8, 2};
-  for (uint32_t tw : {128u, 64u, 32u}) {
-    op_config_t c = {tw, 0, 8, 2};
+  static const uint32_t prefs[][2] = {{128, 1}, {96, 1}, {64, 1}, {32, 1}};
+  for (const auto &p : prefs) {
+    op_config_t c = {p[0] * p[1], 0, 8, 1, p[1]};
     if (check_config(c, r, L, di) != OP_OK) continue;
-    if (smem_for(c, r, L) * 2 <= di.smem_optin || tw == 32) return c;
+    if (smem_for(c, r, L) * 2 <= di.smem_optin) return c;
   }
-  return best;
+  return op_config_t{32, 0, 4, 1, 1};
 }
 
 int pick_config(int r, uint32_t L, const DevInfo &di, op_config_t *out) {
@@ -137,20 +150,20 @@ int pick_config(int r, uint32_t L, const DevInfo &di, op_config_t *out) {
   return check_config(*out, r, L, di);
 }
 
-// Tile height that minimises (tiles per SM, rounded up) x (steps per tile),
-// where a tile of h output rows takes h + 2r steps; a penalty of 1.5 is
-// charged when an SM would hold a single CTA (too few warps to hide the
-// shared-memory latency).
-uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, int sms) {
+// Tile height for an image of H rows cut into tiles_x tile columns when
+// `slots` CTAs can be resident at once: minimises waves x steps per tile,
+// where a tile of h output rows takes h + 2r steps (2r of them only fill the
+// running histogram) and a wave is `slots` tiles running side by side.
+uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
   double best = 1e300;
   uint32_t best_h = H;
+  if (slots < 1) slots = 1;
   for (uint32_t t = 1; t <= H; ++t) {
     const uint32_t th = (H + t - 1) / t;
     if (t > 1 && (H + th - 1) / th != t) continue;  // same tiling as a smaller t
     const uint64_t tiles = static_cast<uint64_t>(tiles_x) * t;
-    const uint64_t per_sm = (tiles + sms - 1) / sms;
-    double cost = static_cast<double>(per_sm) * (th + 2.0 * r);
-    if (per_sm < 2) cost *= 1.5;
+    const uint64_t waves = (tiles + slots - 1) / slots;
+    const double cost = static_cast<double>(waves) * (th + 2.0 * r);
     if (cost < best) {
       best = cost;
       best_h = th;
@@ -159,9 +172,13 @@ uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, int sms) {
   return best_h;
 }
 
-uint32_t effective_tile_h(const op_config_t &c, uint32_t w, uint32_t h, int r, const DevInfo &di) {
+uint32_t effective_tile_h(const op_config_t &c, uint32_t w, uint32_t h, int r, uint32_t L,
+                          const DevInfo &di) {
   if (c.tile_h) return std::min(c.tile_h, h);
-  return auto_tile_h(h, (w + c.tile_w - 1) / c.tile_w, r, di.sms);
+  const int variant = opk::variant_for_radius(r);
+  const int occ = std::max(1, opk::tile_occupancy(threads_of(c), cols_per_thread(c), variant,
+                                                  smem_for(c, r, L)));
+  return auto_tile_h(h, (w + c.tile_w - 1) / c.tile_w, r, static_cast<uint64_t>(occ) * di.sms);
 }
 
 bool valid_image(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int32_t r, uint32_t L,
@@ -264,7 +281,7 @@ op_t *op_create_ex(uint32_t width, uint32_t height, uint32_t stride, uint32_t bp
   op->device = dev;
   op->di = di;
   op->cfg = cfg;
-  op->tile_h = effective_tile_h(op->cfg, width, height, radius, di);
+  op->tile_h = effective_tile_h(op->cfg, width, height, radius, levels, di);
   op->ppitch = packed_pitch(width);
   if (cudaMalloc(&op->d_err, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(op->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
@@ -295,7 +312,7 @@ int op_set_config(op_t *op, const op_config_t *cfg) {
   const int st = check_config(*cfg, op->r, op->L, op->di);
   if (st != OP_OK) return st;
   op->cfg = *cfg;
-  op->tile_h = effective_tile_h(op->cfg, op->w, op->h, op->r, op->di);
+  op->tile_h = effective_tile_h(op->cfg, op->w, op->h, op->r, op->L, op->di);
   op->map_valid = false;
   return OP_OK;
 }
@@ -314,9 +331,7 @@ int op_default_config(int32_t radius, uint32_t levels, op_config_t *cfg) {
 int op_tune_table_set(int32_t radius, uint32_t levels, const op_config_t *cfg) {
   if (!cfg || radius < 0 || radius > OP_MAX_RADIUS || levels < 1 || levels > OP_MAX_LEVELS)
     return OP_E_INVALID;
-  if (!tile_w_ok(cfg->tile_w) || cfg->chunk_rows < 1 || cfg->chunk_rows > 32 ||
-      cfg->prefetch < 1 || cfg->prefetch > 4 || cfg->tile_h > OP_MAX_DIM)
-    return OP_E_INVALID;
+  if (!config_in_range(*cfg)) return OP_E_INVALID;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[{radius, levels}] = *cfg;
   return OP_OK;
@@ -383,13 +398,14 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   d.boxw = boxw;
   d.variant = static_cast<uint32_t>(opk::variant_for_radius(op->r));
   const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, boxw);
-  const size_t smem = opk::tile_smem_bytes(c.tile_w, op->L, static_cast<int>(d.variant), rc);
+  const size_t smem = smem_for(c, op->r, op->L);
   const int pack_grid = static_cast<int>(std::min<uint32_t>(op->h, 8u * op->di.sms));
   cudaError_t e = opk::launch_pack_single(d, pack_grid, s);
   if (e != cudaSuccess) return OP_E_CUDA;
   if (op->prof_ev && cudaEventRecord(op->prof_ev, s) != cudaSuccess) return OP_E_CUDA;
   const dim3 grid(d.tiles_x, (op->h + d.tile_h - 1) / d.tile_h);
-  e = opk::launch_tile_plain(c.tile_w, static_cast<int>(d.variant), d, op->map, rc, grid, smem,
+  e = opk::launch_tile_plain(threads_of(c), cols_per_thread(c), static_cast<int>(d.variant), d,
+                             op->map, rc, grid, smem,
                              op->d_err, kWaitTimeoutNs, s);
   return e == cudaSuccess ? OP_OK : OP_E_CUDA;
 }
@@ -534,8 +550,8 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
   b->di = di;
   b->cfg = c;
   b->rc = opk::make_ring(max_radius, c.chunk_rows, c.prefetch, opk::box_width(c.tile_w, max_radius));
-  b->smem = opk::tile_smem_bytes(c.tile_w, max_levels, opk::variant_for_radius(max_radius), b->rc);
-  const int occ = opk::tile_occupancy(c.tile_w, -1, b->smem);
+  b->smem = smem_for(c, max_radius, max_levels);
+  const int occ = opk::tile_occupancy(threads_of(c), cols_per_thread(c), -1, b->smem);
   if (occ < 1) {
     delete b;
     g_last_error = OP_E_UNSUPPORTED;
@@ -573,6 +589,13 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
 }
 
 size_t op_batch_workspace_size(const op_batch_t *b) { return b ? b->total : 0; }
+
+int op_batch_get_config(const op_batch_t *b, op_config_t *cfg) {
+  if (!b || !cfg) return OP_E_INVALID;
+  *cfg = b->cfg;
+  cfg->tile_h = 0;
+  return OP_OK;
+}
 
 int op_batch_set_workspace(op_batch_t *b, void *d_ws, size_t bytes) {
   if (!b || !d_ws || bytes < b->total || (reinterpret_cast<uintptr_t>(d_ws) & (kAlign - 1)))
@@ -700,7 +723,8 @@ int op_batch_run(op_batch_t *b, void *stream) {
   // stays valid across op_batch_set calls.
   cudaError_t e = opk::launch_pack_batch(descs, rp, d_n, ctrl, b->grid_pack, s);
   if (e != cudaSuccess) return OP_E_CUDA;
-  e = opk::launch_persistent(b->cfg.tile_w, descs, tp, d_n, ctrl, b->rc, b->max_L,
+  e = opk::launch_persistent(threads_of(b->cfg), cols_per_thread(b->cfg), descs, tp, d_n, ctrl,
+                             b->rc, b->max_L,
                              b->grid_persist, b->smem, ctrl + 1, kWaitTimeoutNs, s);
   return e == cudaSuccess ? OP_OK : OP_E_CUDA;
 }

@@ -59,12 +59,16 @@ struct __align__(16) ImgDesc {
   uint32_t tile_h, tiles_x, boxw, variant;
 };
 
-// Geometry of the shared-memory halo ring, fixed per launch.
+// Geometry of the shared-memory halo ring, fixed per launch.  Chunk k of a
+// tile brings the ch rows entering the window during its steps and the ch
+// rows leaving it (2r+1 rows earlier, read again from L2 rather than kept),
+// so the ring never holds more than pf + 1 chunks whatever the radius.
 struct RingCfg {
   uint32_t ch;          // rows per chunk (TMA box height)
   uint32_t pf;          // chunks in flight ahead of the one being consumed
-  uint32_t nslot;       // ring slots, >= pf + ceil((2r+1)/ch) + 1
-  uint32_t slot_bytes;  // bytes per slot, multiple of 128
+  uint32_t nslot;       // ring slots = pf + 1
+  uint32_t half_bytes;  // bytes of one half (entering or leaving rows), multiple of 128
+  uint32_t slot_bytes;  // 2 * half_bytes
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -181,6 +185,38 @@ __device__ __forceinline__ void cnt_add(uint32_t addr, uint32_t d) {
       "r"(d));
 }
 
+// Two independent 64-bit read-modify-writes issued together: +(alo,ahi) at
+// addr_a and -(blo,bhi) at addr_b.  Both loads are issued before either add,
+// so the two updates share one shared-memory latency.  addr_a != addr_b.
+__device__ __forceinline__ void bin_addsub64(uint32_t addr_a, uint32_t alo, uint32_t ahi,
+                                             uint32_t addr_b, uint32_t blo, uint32_t bhi) {
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
+      "add.cc.u32 a0, a0, %1;\n\t"
+      "addc.u32 a1, a1, %2;\n\t"
+      "sub.cc.u32 b0, b0, %4;\n\t"
+      "subc.u32 b1, b1, %5;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(addr_a),
+      "r"(alo), "r"(ahi), "r"(addr_b), "r"(blo), "r"(bhi));
+}
+
+// The same for two 32-bit counts: +da at addr_a, -db at addr_b.
+__device__ __forceinline__ void cnt_addsub(uint32_t addr_a, uint32_t da, uint32_t addr_b,
+                                           uint32_t db) {
+  asm volatile(
+      "{\n\t.reg .u32 a, b;\n\t"
+      "ld.shared.u32 a, [%0];\n\t"
+      "ld.shared.u32 b, [%2];\n\t"
+      "add.u32 a, a, %1;\n\t"
+      "sub.u32 b, b, %3;\n\t"
+      "st.shared.u32 [%0], a;\n\t"
+      "st.shared.u32 [%2], b;\n\t}" ::"r"(addr_a),
+      "r"(da), "r"(addr_b), "r"(db));
+}
+
 // ------------------------------------------------------------ pack prepass
 
 // Section 4's intensity level of one pixel, clamped to L-1.
@@ -231,160 +267,292 @@ __device__ __forceinline__ void delta_b(uint32_t w, uint32_t &lo, uint32_t &hi) 
   hi = (w >> 6) & 0x0003FC00u;
 }
 
-template <int TW, int VAR>
+// One histogram owned by one thread: level l of thread t lives at
+// sums + l * NT * 8 (+ cnts + l * NT * 4 for variant B), so the 32 lanes of a
+// warp always touch 32 consecutive bins whatever their levels.  Level L is a
+// scratch bin that absorbs the no-op half of a paired update.
+template <int NT, int VAR>
 struct Hist {
-  // byte distance between consecutive levels of one thread's histogram
-  static constexpr uint32_t kLevelStride64 = TW * 8u;
-  static constexpr uint32_t kLevelStride32 = TW * 4u;
-  uint32_t sums;  // smem address of this thread's level-0 64-bit bin
-  uint32_t cnts;  // smem address of this thread's level-0 count (variant B)
+  static constexpr uint32_t kStride64 = NT * 8u;
+  static constexpr uint32_t kStride32 = NT * 4u;
+  uint32_t sums;     // smem address of level 0's 64-bit bin
+  uint32_t cnts;     // smem address of level 0's count (variant B)
+  uint32_t scratch;  // level L (the scratch bin), as a level index
 
   __device__ __forceinline__ void clear(uint32_t L) const {
     for (uint32_t l = 0; l < L; ++l) {
-      sts_zero64(sums + l * kLevelStride64);
-      if (VAR == kVarB) sts_zero32(cnts + l * kLevelStride32);
+      sts_zero64(sums + l * kStride64);
+      if (VAR == kVarB) sts_zero32(cnts + l * kStride32);
     }
+  }
+  __device__ __forceinline__ void delta(uint32_t w, uint32_t &lo, uint32_t &hi) const {
+    if (VAR == kVarA)
+      delta_a(w, lo, hi);
+    else
+      delta_b(w, lo, hi);
   }
   __device__ __forceinline__ void add(uint32_t w) const {
     const uint32_t lvl = w >> 24;
     uint32_t lo, hi;
-    if (VAR == kVarA) {
-      delta_a(w, lo, hi);
-      bin_add64(sums + lvl * kLevelStride64, lo, hi);
-    } else {
-      delta_b(w, lo, hi);
-      bin_add64(sums + lvl * kLevelStride64, lo, hi);
-      cnt_add(cnts + lvl * kLevelStride32, 1u);
-    }
+    delta(w, lo, hi);
+    bin_add64(sums + lvl * kStride64, lo, hi);
+    if (VAR == kVarB) cnt_add(cnts + lvl * kStride32, 1u);
   }
   __device__ __forceinline__ void sub(uint32_t w) const {
     const uint32_t lvl = w >> 24;
     uint32_t lo, hi;
-    if (VAR == kVarA) {
-      delta_a(w, lo, hi);
-      bin_sub64(sums + lvl * kLevelStride64, lo, hi);
-    } else {
-      delta_b(w, lo, hi);
-      bin_sub64(sums + lvl * kLevelStride64, lo, hi);
-      cnt_add(cnts + lvl * kLevelStride32, 0xFFFFFFFFu);
-    }
+    delta(w, lo, hi);
+    bin_sub64(sums + lvl * kStride64, lo, hi);
+    if (VAR == kVarB) cnt_add(cnts + lvl * kStride32, 0xFFFFFFFFu);
   }
-  // Most populated level (lowest on a tie) and its truncated channel means.
-  __device__ __forceinline__ void mode_colour(uint32_t L, uint32_t &oR, uint32_t &oG,
-                                              uint32_t &oB) const {
-    uint32_t m = 0, cnt, R, G, B, lo, hi;
-    if (VAR == kVarA) {
-      uint32_t best = 0;  // count field of the best bin, kept in place (bits 22..31)
-      for (uint32_t l = 0; l < L; ++l) {
-        const uint32_t k = lds_u32(sums + l * kLevelStride64 + 4u) & 0xFFC00000u;
-        if (k > best) {
-          best = k;
-          m = l;
-        }
-      }
-      lds_v2(sums + m * kLevelStride64, lo, hi);
-      cnt = hi >> 22;
-      R = (hi >> 4) & 0x3FFFFu;
-      G = ((hi & 0xFu) << 14) | (lo >> 18);
-      B = lo & 0x3FFFFu;
-    } else {
-      uint32_t best = 0;
-      for (uint32_t l = 0; l < L; ++l) {
-        const uint32_t c = lds_u32(cnts + l * kLevelStride32);
-        if (c > best) {
-          best = c;
-          m = l;
-        }
-      }
-      cnt = best;
-      lds_v2(sums + m * kLevelStride64, lo, hi);
-      R = hi >> 10;
-      G = (lo >> 21) | ((hi & 0x3FFu) << 11);
-      B = lo & 0x1FFFFFu;
+  // Adds pixel win and removes pixel wout as one two-deep update.  When both
+  // fall in the same level the net delta goes to that bin and the removal is
+  // redirected to the scratch bin, so the two addresses always differ.
+  __device__ __forceinline__ void addsub(uint32_t win, uint32_t wout) const {
+    const uint32_t la = win >> 24;
+    uint32_t lb = wout >> 24;
+    uint32_t alo, ahi, blo, bhi;
+    delta(win, alo, ahi);
+    delta(wout, blo, bhi);
+    uint32_t ca = 1u;
+    if (la == lb) {
+      const uint64_t net = (static_cast<uint64_t>(ahi) << 32 | alo) -
+                           (static_cast<uint64_t>(bhi) << 32 | blo);
+      alo = static_cast<uint32_t>(net);
+      ahi = static_cast<uint32_t>(net >> 32);
+      ca = 0u;
+      lb = scratch;
     }
-    oR = R / cnt;
-    oG = G / cnt;
-    oB = B / cnt;
+    bin_addsub64(sums + la * kStride64, alo, ahi, sums + lb * kStride64, blo, bhi);
+    if (VAR == kVarB) cnt_addsub(cnts + la * kStride32, ca, cnts + lb * kStride32, 1u);
+  }
+  // Count of level l, for variant A kept in place in bits 22..31 of the high
+  // word (comparing these words compares counts).
+  __device__ __forceinline__ uint32_t count_key(uint32_t l) const {
+    if (VAR == kVarA) return lds_u32(sums + l * kStride64 + 4u) & 0xFFC00000u;
+    return lds_u32(cnts + l * kStride32);
+  }
+  __device__ __forceinline__ void bin(uint32_t l, uint32_t &lo, uint32_t &hi) const {
+    lds_v2(sums + l * kStride64, lo, hi);
   }
 };
+
+// Sum of two disjoint histograms' count keys.  For variant A the high words
+// are added without the carry out of the low words: that carry could only
+// reach the top bits of the G field, which stay below 2^4 for any window of
+// at most 961 pixels, so the count bits are exact.
+template <int VAR>
+__device__ __forceinline__ uint32_t key_sum(uint32_t a, uint32_t b) {
+  return VAR == kVarA ? ((a + b) & 0xFFC00000u) : a + b;
+}
+
+// Channel sums and count of a (possibly combined) 64-bit bin.
+template <int VAR>
+__device__ __forceinline__ void unpack_bin(uint32_t lo, uint32_t hi, uint32_t cnt_b,
+                                           uint32_t &cnt, uint32_t &R, uint32_t &G,
+                                           uint32_t &B) {
+  if (VAR == kVarA) {
+    cnt = hi >> 22;
+    R = (hi >> 4) & 0x3FFFFu;
+    G = ((hi & 0xFu) << 14) | (lo >> 18);
+    B = lo & 0x3FFFFu;
+  } else {
+    cnt = cnt_b;
+    R = hi >> 10;
+    G = (lo >> 21) | ((hi & 0x3FFu) << 11);
+    B = lo & 0x1FFFFFu;
+  }
+}
+
+// ------------------------------------------------------------ division
+
+// Truncating n / d for the channel means.  Variant A (n < 2^18, d <= 961):
+// Granlund and Montgomery's multiply-high by m = ceil(2^31 / d) from a
+// per-CTA table, q = floor(2n * m / 2^32); with e = m*d - 2^31 < d the error
+// term n*e / 2^31 stays below 2^28 / 2^31 < 1, so q is exact.  Variant B
+// uses integer division.
+constexpr uint32_t kRcpEntries = 962;  // d = 0..961 (entry 0 unused)
+
+__device__ __forceinline__ void fill_rcp_table(uint32_t *rcp) {
+  for (uint32_t d = threadIdx.x; d < kRcpEntries; d += blockDim.x)
+    rcp[d] = d ? static_cast<uint32_t>(((1ull << 31) + d - 1u) / d) : 0u;
+}
+
+template <int VAR>
+__device__ __forceinline__ uint32_t div_mean(uint32_t n, uint32_t d, uint32_t m) {
+  if (VAR == kVarA) return __umulhi(n << 1, m);
+  return n / d;
+}
 
 // ----------------------------------------------------------------- tiles
 
 // Shared-memory carve-up common to both kernels.  `smem` is the dynamic
-// shared memory base; returns the 128-byte aligned addresses.
+// shared memory base; every region starts on a 128-byte boundary.
 struct SmemMap {
   uint32_t bars;  // nslot mbarriers
   uint32_t ring;  // nslot * slot_bytes
-  uint32_t sums;  // L * TW * 8
-  uint32_t cnts;  // L * TW * 4 (variant B)
+  uint32_t rcp;   // kRcpEntries reciprocals
+  uint32_t sums;  // nhist * (L + 1) * NT * 8
+  uint32_t cnts;  // nhist * (L + 1) * NT * 4 (variant B)
   uint8_t *ring_ptr;
+  uint32_t *rcp_ptr;
 };
 
-__device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc, uint32_t tw,
-                                              uint32_t lmax) {
+constexpr uint32_t kRcpBytes = (kRcpEntries * 4u + 127u) & ~127u;
+
+__device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc,
+                                              uint32_t nhist_bins) {
   SmemMap s;
   const uint32_t base = smem_addr(smem);
   const uint32_t a = (base + 127u) & ~127u;
   s.bars = a;
   s.ring = a + ((rc.nslot * 8u + 127u) & ~127u);
-  s.sums = s.ring + rc.nslot * rc.slot_bytes;
-  s.cnts = s.sums + lmax * tw * 8u;
+  s.rcp = s.ring + rc.nslot * rc.slot_bytes;
+  s.sums = s.rcp + kRcpBytes;
+  s.cnts = s.sums + nhist_bins * 8u;
   s.ring_ptr = smem + (s.ring - base);
+  s.rcp_ptr = reinterpret_cast<uint32_t *>(smem + (s.rcp - base));
   return s;
 }
 
-// Output tile [x0, x0+TW) x [y0, y1) of image d.  Chunk k of the tile holds
-// the entering rows [y0 - r + k*ch, y0 - r + (k+1)*ch); it lives in ring
-// slot (chunk_ctr + k) % nslot, whose mbarrier completes its phase
-// ((chunk_ctr + k) / nslot) & 1.  chunk_ctr counts the chunks this CTA has
-// consumed so far and is advanced by the tile.  Returns false if a halo copy
-// did not arrive within timeout_ns (error recorded in *err).
-template <int TW, int VAR>
+// Writes the output pixel (x, y): R, G, B and, with 4 bytes per pixel, alpha.
+__device__ __forceinline__ void store_pixel(const ImgDesc &d, int x, int y, uint32_t R,
+                                            uint32_t G, uint32_t B, uint32_t alpha) {
+  uint8_t *o = d.out + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * d.bpp;
+  if (d.bpp == 4) {
+    const uint32_t v = R | (G << 8) | (B << 16) | (alpha << 24);
+    if ((reinterpret_cast<uintptr_t>(o) & 3u) == 0) {
+      *reinterpret_cast<uint32_t *>(o) = v;
+    } else {
+      o[0] = static_cast<uint8_t>(R);
+      o[1] = static_cast<uint8_t>(G);
+      o[2] = static_cast<uint8_t>(B);
+      o[3] = static_cast<uint8_t>(alpha);
+    }
+  } else {
+    o[0] = static_cast<uint8_t>(R);
+    o[1] = static_cast<uint8_t>(G);
+    o[2] = static_cast<uint8_t>(B);
+  }
+}
+
+__device__ __forceinline__ uint32_t load_alpha(const ImgDesc &d, int x, int y) {
+  return __ldg(d.in + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * 4u + 3u);
+}
+
+// CPT = 2, interior thread: one step's updates over the 2r+2 ring words of
+// columns xa-r .. xa+r+1 (EL, the 2r core columns, ER) of the entering row pe
+// (ADD) and/or the leaving row pl (RM).  Words are read in 8-byte pairs from
+// even ring indices (ring rows are 16-byte aligned): with an even start the
+// pairs are (EL, core), (core, core)..., (core, ER); with an odd start EL
+// and ER are single words around core pairs.
+template <int NT, int VAR, bool ADD, bool RM>
+__device__ __forceinline__ void window2_update(const Hist<NT, VAR> *hs, const uint32_t *pe,
+                                               const uint32_t *pl, int r, bool odd) {
+  auto upd = [&](const Hist<NT, VAR> &h, uint32_t a, uint32_t b) {
+    if (ADD && RM)
+      h.addsub(a, b);
+    else if (ADD)
+      h.add(a);
+    else
+      h.sub(b);
+  };
+  auto pair = [&](int j, const Hist<NT, VAR> &hx, const Hist<NT, VAR> &hy) {
+    uint2 a = make_uint2(0u, 0u), b = make_uint2(0u, 0u);
+    if (ADD) a = *reinterpret_cast<const uint2 *>(pe + j);
+    if (RM) b = *reinterpret_cast<const uint2 *>(pl + j);
+    upd(hx, a.x, b.x);
+    upd(hy, a.y, b.y);
+  };
+  auto single = [&](int j, const Hist<NT, VAR> &h) {
+    upd(h, ADD ? pe[j] : 0u, RM ? pl[j] : 0u);
+  };
+  if (!odd) {
+    pair(0, hs[1], r ? hs[0] : hs[2]);
+#pragma unroll 2
+    for (int j = 2; j <= 2 * r - 2; j += 2) pair(j, hs[0], hs[0]);
+    if (r) pair(2 * r, hs[0], hs[2]);
+  } else {
+    single(0, hs[1]);
+#pragma unroll 2
+    for (int j = 1; j <= 2 * r - 1; j += 2) pair(j, hs[0], hs[0]);
+    single(2 * r + 1, hs[2]);
+  }
+}
+
+// Output tile [x0, x0 + NT*CPT) x [y0, y1) of image d; thread t owns the CPT
+// output columns x0 + CPT*t ...
+//
+// CPT = 1: one histogram per thread, the window's 2r+1 columns.
+// CPT = 2: outputs x and x+1 share the 2r columns x-r+1 .. x+r.  The thread
+//   keeps a "core" histogram of those columns and two one-column histograms,
+//   EL of column x-r and ER of column x+r+1; output x is core + EL, output x+1
+//   core + ER.  A step then costs 2(2r+2) bin updates for two outputs instead
+//   of 2 * 2(2r+1).
+//
+// Step s of the tile adds entering row y0 - r + s and removes leaving row
+// y0 - r + s - (2r+1).  Chunk k covers steps [k*ch, (k+1)*ch): its entering
+// and leaving rows arrive by two TMA copies in ring slot (chunk_ctr + k) %
+// nslot, whose mbarrier completes its phase ((chunk_ctr + k) / nslot) & 1.
+// chunk_ctr counts the chunks this CTA has consumed and is advanced by the
+// tile.  Returns false if a halo copy did not arrive within timeout_ns (error
+// recorded in *err).
+template <int NT, int CPT, int VAR>
 __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
                          const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
                          uint32_t *err, uint64_t timeout_ns) {
+  static_assert(CPT == 1 || CPT == 2, "one or two output columns per thread");
   const int t = threadIdx.x;
   const int r = d.r;
   const int W = static_cast<int>(d.w), H = static_cast<int>(d.h);
-  const int x = x0 + t;
+  const uint32_t L = d.L;
+  const int xa = x0 + CPT * t;   // first output column of this thread
   const int xs = (x0 - r) & ~3;  // box start, rounded down to 16 bytes
-  const int clo = max(x - r, 0), chi = min(x + r, W - 1);
-  const int nseg = x < W ? chi - clo + 1 : 0;
-  const int jlo = clo - xs;
-  const int E0 = y0 - r;  // first entering row
+  const int cl = xa - r;            // leftmost window column touched
+  const int cr = xa + CPT - 1 + r;  // rightmost window column touched
+  const bool active = xa < W;
+  const bool interior = cl >= 0 && cr < W;
+  const int jl = cl - xs;  // ring index of column cl (>= 0)
+  const int E0 = y0 - r;   // first entering row
   const int nsteps = (y1 - y0) + 2 * r;
   const int ch = static_cast<int>(rc.ch);
   const int nchunks = (nsteps + ch - 1) / ch;
   const uint32_t box_bytes = d.boxw * rc.ch * 4u;
+  const uint32_t boxw = d.boxw;
+  const uint32_t *rcp = sm.rcp_ptr;
 
-  Hist<TW, VAR> hist;
-  hist.sums = sm.sums + static_cast<uint32_t>(t) * 8u;
-  hist.cnts = sm.cnts + static_cast<uint32_t>(t) * 4u;
-  hist.clear(d.L);
+  // histograms: [0] the window (CPT 1) or the core (CPT 2), [1] EL, [2] ER;
+  // each has L + 1 levels (the last one is the scratch bin)
+  const uint32_t lvl_bins = (L + 1u) * NT;
+  Hist<NT, VAR> hs[CPT == 1 ? 1 : 3];
+#pragma unroll
+  for (int i = 0; i < (CPT == 1 ? 1 : 3); ++i) {
+    hs[i].sums = sm.sums + (i * lvl_bins + t) * 8u;
+    hs[i].cnts = sm.cnts + (i * lvl_bins + t) * 4u;
+    hs[i].scratch = L;
+    hs[i].clear(L);
+  }
 
   auto issue = [&](int k) {
     const uint32_t g = chunk_ctr + static_cast<uint32_t>(k);
     const uint32_t slot = g % rc.nslot;
     const uint32_t bar = sm.bars + slot * 8u;
-    mbar_arrive_expect_tx(bar, box_bytes);
-    tma_load_2d(sm.ring + slot * rc.slot_bytes, tmap, xs, E0 + k * ch, bar);
+    const uint32_t dst = sm.ring + slot * rc.slot_bytes;
+    mbar_arrive_expect_tx(bar, 2u * box_bytes);
+    tma_load_2d(dst, tmap, xs, E0 + k * ch, bar);
+    tma_load_2d(dst + rc.half_bytes, tmap, xs, E0 + k * ch - 2 * r - 1, bar);
   };
 
   __syncthreads();  // the previous tile no longer reads the ring
-  int issued = 0;
+  int issued = min(static_cast<int>(rc.pf), nchunks);
   if (t == 0) {
     fence_proxy_async_smem();
-    for (; issued < static_cast<int>(rc.pf) && issued < nchunks; ++issued) issue(issued);
+    for (int k = 0; k < issued; ++k) issue(k);
   }
-  issued = min(static_cast<int>(rc.pf), nchunks);
 
   const uint32_t *ring = reinterpret_cast<const uint32_t *>(sm.ring_ptr);
   const uint32_t slot_words = rc.slot_bytes / 4u;
-  auto row_ptr = [&](int e) -> const uint32_t * {
-    const int rel = e - E0;
-    const uint32_t slot = (chunk_ctr + static_cast<uint32_t>(rel / ch)) % rc.nslot;
-    return ring + slot * slot_words + static_cast<uint32_t>(rel % ch) * d.boxw + jlo;
-  };
+  const uint32_t half_words = rc.half_bytes / 4u;
 
   for (int k = 0; k < nchunks; ++k) {
     const uint32_t g = chunk_ctr + static_cast<uint32_t>(k);
@@ -402,6 +570,7 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
       __syncthreads();
       return false;
     }
+    // every thread has finished chunk k-1, whose slot receives chunk k + pf
     if (k + static_cast<int>(rc.pf) < nchunks) {
       if (t == 0) {
         fence_proxy_async_smem();
@@ -409,61 +578,108 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
       }
       ++issued;
     }
+    const uint32_t *base_e = ring + (g % rc.nslot) * slot_words + jl;
+    const uint32_t *base_l = base_e + half_words;
     const int s_end = min((k + 1) * ch, nsteps);
     for (int s = k * ch; s < s_end; ++s) {
       const int e = E0 + s;         // entering row
       const int l = e - 2 * r - 1;  // leaving row
       const bool do_add = e >= 0 && e < H;
       const bool do_rm = l >= 0 && l >= E0 && l < H;
-      if (do_add && do_rm) {
-        const uint32_t *pe = row_ptr(e);
-        const uint32_t *pl = row_ptr(l);
-        int j = 0;
-        for (; j + 4 <= nseg; j += 4) {
-          const uint32_t a0 = pe[j], a1 = pe[j + 1], a2 = pe[j + 2], a3 = pe[j + 3];
-          const uint32_t b0 = pl[j], b1 = pl[j + 1], b2 = pl[j + 2], b3 = pl[j + 3];
-          hist.sub(b0);
-          hist.add(a0);
-          hist.sub(b1);
-          hist.add(a1);
-          hist.sub(b2);
-          hist.add(a2);
-          hist.sub(b3);
-          hist.add(a3);
-        }
-        for (; j < nseg; ++j) {
-          const uint32_t a = pe[j], b = pl[j];
-          hist.sub(b);
-          hist.add(a);
-        }
-      } else if (do_add) {
-        const uint32_t *pe = row_ptr(e);
-        for (int j = 0; j < nseg; ++j) hist.add(pe[j]);
-      } else if (do_rm) {
-        const uint32_t *pl = row_ptr(l);
-        for (int j = 0; j < nseg; ++j) hist.sub(pl[j]);
+      const bool out_now = s >= 2 * r && active;  // output row e - r is complete after this step
+      const uint32_t *pe = base_e + (s - k * ch) * boxw;
+      const uint32_t *pl = base_l + (s - k * ch) * boxw;
+      // the alpha bytes are fetched before the updates so their latency is hidden
+      uint32_t alpha0 = 0, alpha1 = 0;
+      if (out_now && d.bpp == 4) {
+        alpha0 = load_alpha(d, xa, e - r);
+        if (CPT == 2 && xa + 1 < W) alpha1 = load_alpha(d, xa + 1, e - r);
       }
-      if (s >= 2 * r && x < W) {
-        const int y = e - r;
-        uint32_t R, G, B;
-        hist.mode_colour(d.L, R, G, B);
-        uint8_t *o = d.out + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * d.bpp;
-        if (d.bpp == 4) {
-          const uint32_t a =
-              __ldg(d.in + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * 4u + 3u);
-          const uint32_t v = R | (G << 8) | (B << 16) | (a << 24);
-          if ((reinterpret_cast<uintptr_t>(o) & 3u) == 0) {
-            *reinterpret_cast<uint32_t *>(o) = v;
-          } else {
-            o[0] = static_cast<uint8_t>(R);
-            o[1] = static_cast<uint8_t>(G);
-            o[2] = static_cast<uint8_t>(B);
-            o[3] = static_cast<uint8_t>(a);
+      if (CPT == 1) {
+        const Hist<NT, VAR> &h = hs[0];
+        const int j0 = interior ? 0 : max(cl, 0) - cl;
+        const int j1 = interior ? 2 * r + 1 : (active ? min(cr, W - 1) - cl + 1 : 0);
+        if (do_add && do_rm) {
+          int j = j0;
+          for (; j + 4 <= j1; j += 4) {
+            const uint32_t a0 = pe[j], a1 = pe[j + 1], a2 = pe[j + 2], a3 = pe[j + 3];
+            const uint32_t b0 = pl[j], b1 = pl[j + 1], b2 = pl[j + 2], b3 = pl[j + 3];
+            h.addsub(a0, b0);
+            h.addsub(a1, b1);
+            h.addsub(a2, b2);
+            h.addsub(a3, b3);
           }
+          for (; j < j1; ++j) h.addsub(pe[j], pl[j]);
+        } else if (do_add) {
+          for (int j = j0; j < j1; ++j) h.add(pe[j]);
+        } else if (do_rm) {
+          for (int j = j0; j < j1; ++j) h.sub(pl[j]);
+        }
+      } else if (interior && do_add && do_rm) {
+        window2_update<NT, VAR, true, true>(hs, pe, pl, r, (jl & 1) != 0);
+      } else if (interior && do_add) {
+        window2_update<NT, VAR, true, false>(hs, pe, pl, r, (jl & 1) != 0);
+      } else if (interior && do_rm) {
+        window2_update<NT, VAR, false, true>(hs, pe, pl, r, (jl & 1) != 0);
+      } else if (active && (do_add || do_rm)) {
+        // border thread: columns outside the image are skipped
+        const int last = 2 * r + 1;
+        for (int j = 0; j <= last; ++j) {
+          const int c = cl + j;
+          if (c < 0 || c >= W) continue;
+          const Hist<NT, VAR> &hh = j == 0 ? hs[1] : (j == last ? hs[2] : hs[0]);
+          if (do_rm) hh.sub(pl[j]);
+          if (do_add) hh.add(pe[j]);
+        }
+      }
+      if (out_now) {
+        const int y = e - r;
+        if (CPT == 1) {
+          uint32_t m = 0, best = 0;
+          for (uint32_t lv = 0; lv < L; ++lv) {
+            const uint32_t kk = hs[0].count_key(lv);
+            if (kk > best) {
+              best = kk;
+              m = lv;
+            }
+          }
+          uint32_t lo, hi, cnt, R, G, B;
+          hs[0].bin(m, lo, hi);
+          unpack_bin<VAR>(lo, hi, VAR == kVarB ? best : 0u, cnt, R, G, B);
+          const uint32_t mul = VAR == kVarA ? rcp[cnt] : 0u;
+          store_pixel(d, xa, y, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
+                      div_mean<VAR>(B, cnt, mul), alpha0);
         } else {
-          o[0] = static_cast<uint8_t>(R);
-          o[1] = static_cast<uint8_t>(G);
-          o[2] = static_cast<uint8_t>(B);
+          uint32_t m0 = 0, m1 = 0, b0 = 0, b1 = 0;
+          for (uint32_t lv = 0; lv < L; ++lv) {
+            const uint32_t kc = hs[0].count_key(lv);
+            const uint32_t k0 = key_sum<VAR>(kc, hs[1].count_key(lv));
+            const uint32_t k1 = key_sum<VAR>(kc, hs[2].count_key(lv));
+            if (k0 > b0) {
+              b0 = k0;
+              m0 = lv;
+            }
+            if (k1 > b1) {
+              b1 = k1;
+              m1 = lv;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            if (i == 1 && xa + 1 >= W) break;
+            const uint32_t m = i ? m1 : m0;
+            uint32_t clo, chi, elo, ehi, cnt, R, G, B;
+            hs[0].bin(m, clo, chi);
+            hs[1 + i].bin(m, elo, ehi);
+            // 64-bit sum of the core and edge bins
+            const uint64_t v = (static_cast<uint64_t>(chi) << 32 | clo) +
+                               (static_cast<uint64_t>(ehi) << 32 | elo);
+            unpack_bin<VAR>(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32),
+                            VAR == kVarB ? (i ? b1 : b0) : 0u, cnt, R, G, B);
+            const uint32_t mul = VAR == kVarA ? rcp[cnt] : 0u;
+            store_pixel(d, xa + i, y, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
+                        div_mean<VAR>(B, cnt, mul), i ? alpha1 : alpha0);
+          }
         }
       }
     }
@@ -472,11 +688,13 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
   return true;
 }
 
-__device__ __forceinline__ void init_ring_barriers(const SmemMap &sm, const RingCfg &rc) {
+// Barrier init and the reciprocal table; ends with a CTA barrier.
+__device__ __forceinline__ void init_cta(const SmemMap &sm, const RingCfg &rc) {
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < rc.nslot; ++s) mbar_init(sm.bars + s * 8u, 1u);
     mbar_fence_init();
   }
+  fill_rcp_table(sm.rcp_ptr);
   __syncthreads();
 }
 

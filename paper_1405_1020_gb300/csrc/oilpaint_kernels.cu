@@ -3,8 +3,9 @@
 //   pack_single_kernel / pack_batch_kernel  the pack prepass (one image / a
 //                                           batch; the batch form also resets
 //                                           the tile-queue counter)
-//   tile_plain_kernel<TW, VAR>              one CTA per output tile
-//   persistent_kernel<TW>                   grid-sized CTAs pulling
+//   tile_plain_kernel<NT, CPT, VAR>         one CTA per output tile (NT threads,
+//                                           CPT output columns per thread)
+//   persistent_kernel<NT, CPT>              grid-sized CTAs pulling
 //                                           (image, tile) tickets from a
 //                                           device atomic until the queue of a
 //                                           whole batch is empty
@@ -45,29 +46,35 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int TW, int VAR>
-__global__ void __launch_bounds__(TW)
+// Histogram bins per CTA: nhist histograms of L levels plus a scratch level
+// for each of NT threads.
+__device__ __forceinline__ uint32_t hist_bins(int cpt, uint32_t L, uint32_t nt) {
+  return (cpt == 1 ? 1u : 3u) * (L + 1u) * nt;
+}
+
+template <int NT, int CPT, int VAR>
+__global__ void __launch_bounds__(NT, 1)
     tile_plain_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d, const RingCfg rc,
                       uint32_t *err, uint64_t timeout_ns) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const SmemMap sm = carve_smem(smem, rc, TW, d.L);
-  init_ring_barriers(sm, rc);
+  const SmemMap sm = carve_smem(smem, rc, hist_bins(CPT, d.L, NT));
+  init_cta(sm, rc);
   uint32_t ctr = 0;
-  const int x0 = static_cast<int>(blockIdx.x) * TW;
+  const int x0 = static_cast<int>(blockIdx.x) * NT * CPT;
   const int y0 = static_cast<int>(blockIdx.y * d.tile_h);
   const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
-  run_tile<TW, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+  run_tile<NT, CPT, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
-template <int TW>
-__global__ void __launch_bounds__(TW)
+template <int NT, int CPT>
+__global__ void __launch_bounds__(NT, 1)
     persistent_kernel(const ImgDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
                       const uint32_t *__restrict__ d_n, uint32_t *queue, const RingCfg rc,
                       uint32_t lmax, uint32_t *err, uint64_t timeout_ns) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_job[2];
-  const SmemMap sm = carve_smem(smem, rc, TW, lmax);
-  init_ring_barriers(sm, rc);
+  const SmemMap sm = carve_smem(smem, rc, hist_bins(CPT, lmax, NT));
+  init_cta(sm, rc);
   const uint32_t n = __ldg(d_n);
   if (n == 0) return;
   const uint32_t total = __ldg(tile_prefix + n);
@@ -87,12 +94,17 @@ __global__ void __launch_bounds__(TW)
     const uint32_t img = s_job[0], local = s_job[1];
     if (img == 0xFFFFFFFFu) break;
     const ImgDesc d = descs[img];
-    const int x0 = static_cast<int>(local % d.tiles_x) * TW;
+    // this image's histograms are laid out for its own L inside the region
+    SmemMap smi = sm;
+    smi.cnts = sm.sums + hist_bins(CPT, d.L, NT) * 8u;
+    const int x0 = static_cast<int>(local % d.tiles_x) * NT * CPT;
     const int y0 = static_cast<int>((local / d.tiles_x) * d.tile_h);
     const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
     const bool ok = d.variant == kVarA
-                        ? run_tile<TW, kVarA>(d, d.tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns)
-                        : run_tile<TW, kVarB>(d, d.tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+                        ? run_tile<NT, CPT, kVarA>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
+                                                   timeout_ns)
+                        : run_tile<NT, CPT, kVarB>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
+                                                   timeout_ns);
     if (!ok) break;
   }
 }
@@ -123,49 +135,71 @@ cudaError_t launch_pack_batch(const ImgDesc *d_descs, const uint32_t *d_row_pref
   return cudaGetLastError();
 }
 
-template <int TW>
-static cudaError_t launch_plain_tw(int variant, const ImgDesc &d, const CUtensorMap &map,
-                                   const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
-                                   uint64_t timeout_ns, cudaStream_t s) {
+template <int NT, int CPT>
+static void plain_nc(int variant, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
+                     dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
   if (variant == kVarA)
-    tile_plain_kernel<TW, kVarA><<<grid, TW, smem, s>>>(map, d, rc, err, timeout_ns);
+    tile_plain_kernel<NT, CPT, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
   else
-    tile_plain_kernel<TW, kVarB><<<grid, TW, smem, s>>>(map, d, rc, err, timeout_ns);
+    tile_plain_kernel<NT, CPT, kVarB><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+}
+
+template <int NT>
+static void plain_n(int cpt, int variant, const ImgDesc &d, const CUtensorMap &map,
+                    const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
+                    uint64_t timeout_ns, cudaStream_t s) {
+  if (cpt == 2)
+    plain_nc<NT, 2>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
+  else
+    plain_nc<NT, 1>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
+}
+
+cudaError_t launch_tile_plain(uint32_t nt, int cpt, int variant, const ImgDesc &d,
+                              const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
+                              uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  switch (nt) {
+    case 32: plain_n<32>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+    case 64: plain_n<64>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+    case 96: plain_n<96>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+    case 128: plain_n<128>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_plain(uint32_t tw, int variant, const ImgDesc &d, const CUtensorMap &map,
-                              const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
-                              uint64_t timeout_ns, cudaStream_t s) {
-  switch (tw) {
-    case 32: return launch_plain_tw<32>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
-    case 64: return launch_plain_tw<64>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
-    case 128: return launch_plain_tw<128>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
-    case 256: return launch_plain_tw<256>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
-    default: return cudaErrorInvalidValue;
-  }
+template <int NT>
+static void persistent_n(int cpt, const ImgDesc *d_descs, const uint32_t *d_tile_prefix,
+                         const uint32_t *d_n, uint32_t *d_queue, const RingCfg &rc,
+                         uint32_t lmax, int grid, size_t smem, uint32_t *err,
+                         uint64_t timeout_ns, cudaStream_t s) {
+  if (cpt == 2)
+    persistent_kernel<NT, 2><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
+                                                    lmax, err, timeout_ns);
+  else
+    persistent_kernel<NT, 1><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
+                                                    lmax, err, timeout_ns);
 }
 
-cudaError_t launch_persistent(uint32_t tw, const ImgDesc *d_descs, const uint32_t *d_tile_prefix,
-                              const uint32_t *d_n, uint32_t *d_queue, const RingCfg &rc, uint32_t lmax,
-                              int grid, size_t smem, uint32_t *err, uint64_t timeout_ns,
-                              cudaStream_t s) {
-  switch (tw) {
+cudaError_t launch_persistent(uint32_t nt, int cpt, const ImgDesc *d_descs,
+                              const uint32_t *d_tile_prefix, const uint32_t *d_n,
+                              uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
+                              size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  switch (nt) {
     case 32:
-      persistent_kernel<32><<<grid, 32, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc, lmax,
-                                                   err, timeout_ns);
+      persistent_n<32>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+                       timeout_ns, s);
       break;
     case 64:
-      persistent_kernel<64><<<grid, 64, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc, lmax,
-                                                   err, timeout_ns);
+      persistent_n<64>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+                       timeout_ns, s);
+      break;
+    case 96:
+      persistent_n<96>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+                       timeout_ns, s);
       break;
     case 128:
-      persistent_kernel<128><<<grid, 128, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
-                                                     lmax, err, timeout_ns);
-      break;
-    case 256:
-      persistent_kernel<256><<<grid, 256, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
-                                                     lmax, err, timeout_ns);
+      persistent_n<128>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+                        timeout_ns, s);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -177,48 +211,56 @@ cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStrea
   return cudaGetLastError();
 }
 
-template <int TW>
-static cudaError_t set_limit_tw(size_t bytes) {
+template <int NT, int CPT>
+static cudaError_t set_limit_nc(int b) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, CPT, kVarA>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, CPT, kVarB>, a, b)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(persistent_kernel<NT, CPT>, a, b);
+}
+
+template <int NT>
+static cudaError_t set_limit_n(int b) {
+  const cudaError_t e = set_limit_nc<NT, 1>(b);
+  return e != cudaSuccess ? e : set_limit_nc<NT, 2>(b);
+}
+
+cudaError_t set_tile_smem_limit(size_t bytes) {
   const int b = static_cast<int>(bytes);
-  cudaError_t e = cudaFuncSetAttribute(tile_plain_kernel<TW, kVarA>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(tile_plain_kernel<TW, kVarB>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(persistent_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              b);
+  cudaError_t e;
+  if ((e = set_limit_n<32>(b)) != cudaSuccess) return e;
+  if ((e = set_limit_n<64>(b)) != cudaSuccess) return e;
+  if ((e = set_limit_n<96>(b)) != cudaSuccess) return e;
+  return set_limit_n<128>(b);
 }
 
-cudaError_t set_tile_smem_limit(uint32_t tw, size_t bytes) {
-  switch (tw) {
-    case 32: return set_limit_tw<32>(bytes);
-    case 64: return set_limit_tw<64>(bytes);
-    case 128: return set_limit_tw<128>(bytes);
-    case 256: return set_limit_tw<256>(bytes);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int TW>
-static int occupancy_tw(int variant, size_t smem) {
+template <int NT, int CPT>
+static int occupancy_nc(int variant, size_t smem) {
   int n = 0;
   cudaError_t e;
   if (variant == kVarA)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tile_plain_kernel<TW, kVarA>, TW, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tile_plain_kernel<NT, CPT, kVarA>, NT,
+                                                      smem);
   else if (variant == kVarB)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tile_plain_kernel<TW, kVarB>, TW, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tile_plain_kernel<NT, CPT, kVarB>, NT,
+                                                      smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<TW>, TW, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<NT, CPT>, NT, smem);
   return e == cudaSuccess ? n : 0;
 }
 
-int tile_occupancy(uint32_t tw, int variant, size_t smem) {
-  switch (tw) {
-    case 32: return occupancy_tw<32>(variant, smem);
-    case 64: return occupancy_tw<64>(variant, smem);
-    case 128: return occupancy_tw<128>(variant, smem);
-    case 256: return occupancy_tw<256>(variant, smem);
+template <int NT>
+static int occupancy_n(int cpt, int variant, size_t smem) {
+  return cpt == 2 ? occupancy_nc<NT, 2>(variant, smem) : occupancy_nc<NT, 1>(variant, smem);
+}
+
+int tile_occupancy(uint32_t nt, int cpt, int variant, size_t smem) {
+  switch (nt) {
+    case 32: return occupancy_n<32>(cpt, variant, smem);
+    case 64: return occupancy_n<64>(cpt, variant, smem);
+    case 96: return occupancy_n<96>(cpt, variant, smem);
+    case 128: return occupancy_n<128>(cpt, variant, smem);
     default: return 0;
   }
 }

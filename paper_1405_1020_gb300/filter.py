@@ -6,12 +6,39 @@ is no CPU path: without the built library every call raises OilPaintError.
 """
 from __future__ import annotations
 
+import json
+import os
 from typing import Iterable, Sequence
 
 import numpy as np
 import torch
 
 from . import binding as B
+
+TUNING_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+_tuned_loaded = False
+
+
+def load_tuning(path: str = TUNING_TABLE) -> int:
+    """Load the autotuner's saved (radius, levels) -> launch-configuration
+    table into the library (once per process unless `path` is given
+    explicitly); returns the number of entries."""
+    global _tuned_loaded
+    if not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        table = json.load(f)
+    entries = table.get("entries", {})
+    for key, ent in entries.items():
+        r, L = (int(v) for v in key.split(","))
+        B.check(B.op_tune_table_set(r, L, B.op_config_t.make(**ent["config"])), "tune table")
+    _tuned_loaded = True
+    return len(entries)
+
+
+def _ensure_tuned() -> None:
+    if not _tuned_loaded:
+        load_tuning()
 
 
 def _stream_handle(stream) -> int:
@@ -36,7 +63,7 @@ def _config(cfg) -> B.op_config_t:
         return cfg
     d = dict(cfg)
     return B.op_config_t.make(d.get("tile_w", 128), d.get("tile_h", 0), d.get("chunk_rows", 8),
-                              d.get("prefetch", 2))
+                              d.get("prefetch", 2), d.get("cols_per_thread", 1))
 
 
 class OilPaint:
@@ -53,6 +80,7 @@ class OilPaint:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self._h = None
+        _ensure_tuned()
         with torch.cuda.device(self.device):
             h = B.op_create_ex(width, height, self.stride, bpp, radius, levels, flags)
             if not h:
@@ -142,6 +170,7 @@ class Batch:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         self._h = None
+        _ensure_tuned()
         with torch.cuda.device(self.device):
             h = B.op_batch_create(max_images, max_pixels, max_radius, max_levels, _config(config))
             if not h:
@@ -176,6 +205,11 @@ class Batch:
         B.check(B.op_batch_set(self._h, arr, len(images), _stream_handle(stream)), "op_batch_set")
         self._keep = keep
         self.n = len(images)
+
+    def config(self) -> dict:
+        c = B.op_config_t()
+        B.check(B.op_batch_get_config(self._h, c), "op_batch_get_config")
+        return c.as_dict()
 
     def run(self, stream=None) -> None:
         B.check(B.op_batch_run(self._h, _stream_handle(stream)), "op_batch_run")

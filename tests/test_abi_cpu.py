@@ -72,6 +72,8 @@ def test_null_handles(lib):
 
 def test_tune_table_validation(lib):
     assert B.op_tune_table_set(3, 20, B.op_config_t.make(48)) == B.OP_E_INVALID
+    assert B.op_tune_table_set(3, 20, B.op_config_t.make(96, cols_per_thread=2)) == B.OP_E_INVALID
+    assert B.op_tune_table_set(3, 20, B.op_config_t.make(64, cols_per_thread=3)) == B.OP_E_INVALID
     assert B.op_tune_table_set(3, 20, B.op_config_t.make(64, chunk_rows=0)) == B.OP_E_INVALID
     assert B.op_tune_table_set(3, 20, B.op_config_t.make(64, prefetch=5)) == B.OP_E_INVALID
     assert B.op_tune_table_set(99, 20, B.op_config_t.make(64)) == B.OP_E_INVALID

@@ -1,0 +1,168 @@
+"""The persistent batched kernel: mixed images in one launch, eagerly and
+replayed from a CUDA graph, against the CPU oracle and against solo runs."""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+import oracle
+from paper_1405_1020_gb300 import binding as B
+from paper_1405_1020_gb300 import synth
+from paper_1405_1020_gb300.filter import Batch, OilPaint
+from tests.pins import OUT_FILL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def make_images(n, seed, max_r=44, levels=(1, 3, 16, 20, 32, 64, 256)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        w = int(rng.integers(1, 260))
+        h = int(rng.integers(1, 180))
+        r = int(rng.choice([v for v in (0, 1, 2, 5, 15, 16, 20, 44) if v <= max_r]))
+        L = int(rng.choice(levels))
+        bpp = int(rng.choice([3, 4]))
+        pad = int(rng.choice([0, 1, 8]))
+        mode = int(rng.integers(0, 2))
+        img = synth.camera_like(h, w, seed=seed * 100 + i, npoly=10, rad_range=(2, 80))
+        buf, stride = synth.to_strided(img, bpp=bpp, stride=w * bpp + pad)
+        out.append(dict(buf=buf, w=w, h=h, stride=stride, bpp=bpp, r=r, L=L, mode=mode))
+    return out
+
+
+def to_device(images):
+    for im in images:
+        im["src"] = torch.from_numpy(im["buf"]).cuda()
+        im["dst"] = torch.full_like(im["src"], OUT_FILL)
+    torch.cuda.synchronize()  # the fills ran on the default stream
+    return [(im["src"], im["dst"], im["w"], im["h"], im["stride"], im["bpp"], im["r"], im["L"],
+             im["mode"]) for im in images]
+
+
+def oracle_out(im):
+    out = np.full(im["buf"].size, OUT_FILL, np.uint8)
+    return oracle.oilpaint(im["buf"], im["w"], im["h"], im["stride"], im["bpp"], im["r"],
+                           im["L"], mode=im["mode"], out=out)
+
+
+def check_all(images, what):
+    torch.cuda.synchronize()
+    for k, im in enumerate(images):
+        got = im["dst"].cpu().numpy()
+        want = oracle_out(im)
+        assert np.array_equal(got, want), (
+            f"{what}: image {k} ({im['w']}x{im['h']} r={im['r']} L={im['L']} bpp={im['bpp']})")
+
+
+def reset(images):
+    for im in images:
+        im["dst"].fill_(OUT_FILL)
+    torch.cuda.synchronize()
+
+
+def new_batch(images, max_images=64, cfg=None):
+    pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
+    return Batch(max_images, max(pix, 1) + 4096, 44, 256, config=cfg)
+
+
+def test_mixed_batch_eager_and_graph():
+    images = make_images(24, seed=1)
+    descs = to_device(images)
+    b = new_batch(images)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.set(descs, stream)
+        b.run(stream)
+    assert b.sync_status(stream) == B.OP_OK
+    check_all(images, "eager")
+    reset(images)
+    b.capture(stream)
+    b.launch_graph(stream)
+    assert b.sync_status(stream) == B.OP_OK
+    check_all(images, "graph")
+    # a different batch through the same graph: the tables are device-resident
+    other = make_images(17, seed=2)
+    d2 = to_device(other)
+    # capacity of the first batch's workspace must hold the second
+    if Batch.padded_pixels([(im["w"], im["h"]) for im in other]) <= \
+            Batch.padded_pixels([(im["w"], im["h"]) for im in images]) + 4096:
+        b.set(d2, stream)
+        b.launch_graph(stream)
+        assert b.sync_status(stream) == B.OP_OK
+        check_all(other, "graph, second batch")
+    b.close()
+
+
+@pytest.mark.parametrize("cfg", [None,
+                                 {"tile_w": 64, "chunk_rows": 4, "prefetch": 2},
+                                 {"tile_w": 128, "chunk_rows": 16, "prefetch": 1,
+                                  "cols_per_thread": 2}])
+def test_batch_equals_solo_runs(cfg):
+    images = make_images(12, seed=3, max_r=20, levels=(16, 20, 32))
+    descs = to_device(images)
+    pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
+    try:
+        b = Batch(16, pix + 64, 20, 32, config=cfg)
+    except B.OilPaintError as e:
+        assert e.status == B.OP_E_UNSUPPORTED
+        pytest.skip("configuration does not fit this device")
+    b.set(descs)
+    b.run()
+    assert b.sync_status() == B.OP_OK
+    torch.cuda.synchronize()
+    for im in images:
+        solo = torch.full_like(im["src"], OUT_FILL)
+        op = OilPaint(im["w"], im["h"], im["r"], im["L"], bpp=im["bpp"], stride=im["stride"],
+                      flags=im["mode"])
+        op.run(im["src"], solo)
+        assert op.sync_status() == B.OP_OK
+        op.close()
+        assert torch.equal(solo, im["dst"])
+    b.close()
+
+
+def test_empty_batch_and_reuse():
+    b = Batch(4, 10000, 5, 20)
+    b.set([])
+    b.run()
+    assert b.sync_status() == B.OP_OK
+    images = make_images(3, seed=4, max_r=5, levels=(20,))
+    # keep the set inside the 10000-pixel capacity
+    small = [im for im in images if ((im["w"] + 3) // 4 * 4) * im["h"] <= 3000]
+    if small:
+        descs = to_device(small)
+        b.set(descs)
+        b.run()
+        assert b.sync_status() == B.OP_OK
+        check_all(small, "after empty batch")
+    b.close()
+
+
+def test_batch_rejects_invalid_sets():
+    img = torch.zeros(30 * 20 * 3, dtype=torch.uint8, device="cuda")
+    out = torch.zeros_like(img)
+    b = Batch(2, 4096, 5, 20)
+    ok = (img, out, 30, 20, 90, 3, 5, 20)
+    with pytest.raises(B.OilPaintError) as e:
+        b.set([ok, ok, ok])  # more than max_images
+    assert e.value.status == B.OP_E_INVALID
+    with pytest.raises(B.OilPaintError):
+        b.set([(img, out, 30, 20, 90, 3, 6, 20)])  # radius above the batch maximum
+    with pytest.raises(B.OilPaintError):
+        b.set([(img, out, 30, 20, 90, 3, 5, 21)])  # levels above the batch maximum
+    with pytest.raises(B.OilPaintError):
+        b.set([(img, img, 30, 20, 90, 3, 5, 20)])  # in == out
+    big = torch.zeros(100 * 50 * 3, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.OilPaintError):
+        b.set([(big, torch.zeros_like(big), 100, 50, 300, 3, 5, 20)])  # over the pixel capacity
+    b.set([ok])
+    b.run()
+    assert b.sync_status() == B.OP_OK
+    b.close()

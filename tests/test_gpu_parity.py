@@ -129,10 +129,11 @@ def _fuzz_cases(n=48, seed=7):
         bpp = int(rng.choice([3, 4]))
         pad = int(rng.choice([0, 1, 4, 13]))
         mode = int(rng.integers(0, 2))
-        tw = int(rng.choice([32, 64, 128]))
-        cfg = {"tile_w": tw, "tile_h": int(rng.choice([0, 1, 5, 16, 64])),
+        nt = int(rng.choice([32, 64, 96, 128]))
+        cpt = int(rng.choice([1, 2]))
+        cfg = {"tile_w": nt * cpt, "tile_h": int(rng.choice([0, 1, 5, 16, 64])),
                "chunk_rows": int(rng.choice([1, 2, 3, 8, 16, 32])),
-               "prefetch": int(rng.integers(1, 5))}
+               "prefetch": int(rng.integers(1, 5)), "cols_per_thread": cpt}
         cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
     return cases
 
@@ -173,25 +174,58 @@ def test_every_config_gives_the_same_bytes():
     h, w = img.shape[:2]
     buf, stride = synth.to_strided(img, bpp=3, stride=w * 3 + 2)
     want = cpu_filter(buf, w, h, stride, 3, 9, 20)
-    for tw in (32, 64, 128):
-        for ch in (1, 4, 8, 16):
-            for pf in (1, 2, 4):
-                for th in (0, 1, 23, 233):
-                    cfg = {"tile_w": tw, "tile_h": th, "chunk_rows": ch, "prefetch": pf}
-                    got = gpu_filter(buf, w, h, stride, 3, 9, 20, config=cfg)
-                    assert_same(got, want, w, h, stride, 3, str(cfg))
+    for nt in (32, 64, 96, 128):
+        for cpt in (1, 2):
+            for ch in (1, 4, 8, 16):
+                for pf in (1, 2, 4):
+                    for th in (0, 1, 23, 233):
+                        cfg = {"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch,
+                               "prefetch": pf, "cols_per_thread": cpt}
+                        if nt * cpt + 2 * 9 + 3 > 256:
+                            continue  # halo wider than one TMA box: refused by the library
+                        got = gpu_filter(buf, w, h, stride, 3, 9, 20, config=cfg)
+                        assert_same(got, want, w, h, stride, 3, str(cfg))
+
+
+@pytest.mark.parametrize("cpt", [1, 2])
+@pytest.mark.parametrize("r,L", [(0, 20), (1, 7), (2, 20), (14, 20), (15, 20), (16, 20),
+                                 (20, 32), (15, 256), (44, 64), (13, 3)])
+def test_columns_per_thread_both_variants(cpt, r, L):
+    """Both histogram variants and both column-per-thread layouts, with odd
+    and even halo offsets (r mod 4), on images whose width is not a tile
+    multiple.  Configurations the library refuses (shared memory) are
+    skipped; at least one must run."""
+    img = synth.camera_like(190, 270, seed=r * L + 1, npoly=25, rad_range=(3, 100))
+    ran = 0
+    for bpp, pad, nt, ch in ((4, 4, 64, 8), (3, 1, 32, 3)):
+        try:
+            check_case(img, r, L, bpp=bpp, pad=pad,
+                       config={"tile_w": nt * cpt, "cols_per_thread": cpt, "chunk_rows": ch})
+            ran += 1
+        except B.OilPaintError as e:
+            assert e.status == B.OP_E_UNSUPPORTED, e
+    assert ran
+
+
+@pytest.mark.parametrize("w,h,r,L", [(300, 40, 15, 20), (301, 41, 14, 20), (97, 50, 13, 16)])
+def test_border_threads_two_columns(w, h, r, L):
+    """Images narrower than two tiles: most threads clip their windows."""
+    img = synth.uniform_rgb(h, w, seed=w + r)
+    for nt in (32, 64):
+        check_case(img, r, L, bpp=3, config={"tile_w": 2 * nt, "cols_per_thread": 2})
 
 
 def test_tile_w_256_only_without_halo():
     op = OilPaint(300, 20, 0, 20)
-    op.set_config({"tile_w": 256})  # r = 0: the 256-word box fits
+    op.set_config({"tile_w": 256, "cols_per_thread": 2})  # r = 0: the 256-word box fits
     op.close()
     op = OilPaint(300, 20, 1, 20)
     with pytest.raises(B.OilPaintError) as e:
-        op.set_config({"tile_w": 256})
+        op.set_config({"tile_w": 256, "cols_per_thread": 2})
     assert e.value.status == B.OP_E_UNSUPPORTED
     op.close()
-    check_case(synth.uniform_rgb(40, 600, seed=3), 0, 20, config={"tile_w": 256})
+    check_case(synth.uniform_rgb(40, 600, seed=3), 0, 20,
+               config={"tile_w": 256, "cols_per_thread": 2})
 
 
 def test_run_host_matches_oracle():
@@ -212,6 +246,8 @@ def test_invalid_calls_on_device():
     assert B.op_run(op.handle, src.data_ptr(), src.data_ptr() + 16, None) == B.OP_E_INVALID
     assert B.op_set_workspace(op.handle, src.data_ptr(), 16) == B.OP_E_INVALID
     assert B.op_set_config(op.handle, B.op_config_t.make(48)) == B.OP_E_INVALID
+    assert B.op_set_config(op.handle, B.op_config_t.make(64, cols_per_thread=3)) == B.OP_E_INVALID
+    assert B.op_set_config(op.handle, B.op_config_t.make(96, cols_per_thread=2)) == B.OP_E_INVALID
     assert B.op_set_config(op.handle, B.op_config_t.make(64, chunk_rows=40)) == B.OP_E_INVALID
     op.close()
 
