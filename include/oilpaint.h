@@ -243,6 +243,38 @@ int op_batch_destroy(op_batch_t *b);
  */
 int op_selftest_wait_timeout(uint64_t timeout_ns, void *stream);
 
+/* ---- allocation-free entry point ------------------------------------------
+ * The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate device memory -- a plugin inside a host application that
+ * owns all device memory through its own pool, code on a latency-critical
+ * path that cannot afford the device-wide synchronisation of cudaMalloc and
+ * cudaFree, or a process whose free memory another allocator already holds.
+ */
+
+/* Words of the fixed scratch array behind op_run_noalloc: 16 MiB, held by
+ * every GPU that loads this library until the process exits. */
+#define OP_NOALLOC_MAX_WORDS (4u * 1024u * 1024u)
+
+/*
+ * op_run_noalloc -- the filter of op_run on one image without allocating:
+ * no cudaMalloc, no cudaFree, no allocating library call.  Its packed-word
+ * scratch is a file-scope device array of OP_NOALLOC_MAX_WORDS words inside
+ * the library, so the image must satisfy ((width + 3) & ~3) * height <=
+ * OP_NOALLOC_MAX_WORDS (e.g. 2048 x 2048); larger images return
+ * OP_E_UNSUPPORTED.  Other arguments as op_create_ex / op_run; d_in and d_out
+ * are device pointers the caller owns (height * stride bytes each).
+ * The call is synchronous: it returns after `stream` has completed the work,
+ * with OP_OK, OP_E_TIMEOUT (a bounded device wait gave up) or OP_E_CUDA.
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress), so make it before any stream capture.
+ * All calls share the one array and it keeps the last call's contents;
+ * calls that overlap on the GPU (other host threads, other streams) race on
+ * it and must be serialised by the caller.
+ */
+int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t width, uint32_t height,
+                   uint32_t stride, uint32_t bpp, int32_t radius, uint32_t levels,
+                   uint32_t flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

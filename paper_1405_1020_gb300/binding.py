@@ -27,6 +27,7 @@ OP_LEVEL_INTDIV3 = 1
 OP_MAX_RADIUS = 44
 OP_MAX_LEVELS = 256
 OP_MAX_DIM = 65535
+OP_NOALLOC_MAX_WORDS = 4 * 1024 * 1024
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboilpaint.so")
 
@@ -39,7 +40,7 @@ EXPORTS = (
     "op_batch_create", "op_batch_get_config", "op_batch_workspace_size",
     "op_batch_set_workspace", "op_batch_set",
     "op_batch_run", "op_batch_capture", "op_batch_launch_graph", "op_batch_sync_status",
-    "op_batch_destroy", "op_selftest_wait_timeout",
+    "op_batch_destroy", "op_selftest_wait_timeout", "op_run_noalloc",
 )
 
 
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "op_batch_sync_status": (ci, [vp, vp]),
         "op_batch_destroy": (ci, [vp]),
         "op_selftest_wait_timeout": (ci, [u64, vp]),
+        "op_run_noalloc": (ci, [vp, vp, u32, u32, u32, u32, i32, u32, u32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,3 +241,9 @@ def op_batch_destroy(b):
 
 def op_selftest_wait_timeout(timeout_ns, stream=None):
     return load().op_selftest_wait_timeout(timeout_ns, stream)
+
+
+def op_run_noalloc(d_in, d_out, width, height, stride, bpp, radius, levels,
+                   flags=OP_LEVEL_PAPER, stream=None):
+    return load().op_run_noalloc(d_in, d_out, width, height, stride, bpp, radius, levels, flags,
+                                 stream)

@@ -17,7 +17,7 @@ PKG = os.path.dirname(CSRC)
 ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liboilpaint.so")
-SOURCES = ["oilpaint_kernels.cu", "oilpaint_api.cu"]
+SOURCES = ["oilpaint_kernels.cu", "oilpaint_api.cu", "oilpaint_noalloc.cu"]
 HEADERS = ["oilpaint_device.cuh", "oilpaint_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
