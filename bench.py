@@ -15,7 +15,8 @@ One JSON line is printed (rank 0).  Besides the headline it carries
   cpu_baseline  the CPU oracle on a bounded row band of the same image,
   batched       the 64-image mixed batch, one persistent launch (CUDA graph)
                 vs one plain op_run per image,
-  served        the continuous-batching server at offered loads (short runs),
+  served        the continuous-batching server at 50/200/800 Mpix/s offered
+                (3 s per load by default; --serve-seconds 60 for the long run),
   clocks        SM clocks and throttle reasons sampled during the timed region.
 
 --impl reference runs the CPU oracle (the only other implementation) on the
@@ -62,6 +63,19 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def reduce_max(x: float) -> float:
+    """Maximum of x over the ranks of the default process group (x itself
+    when there is none); the tensor lives where the backend wants it."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -88,7 +102,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -143,8 +157,8 @@ def cpu_baseline(buf, target_s: float = 10.0):
     """The oracle, as it stands, on a band of rows of the same image."""
     import oracle
     cores = oracle.num_cpus()
-    y0 = H // 2
-    probe = 16
+    y0 = 0
+    probe = 32
     t = time.perf_counter()
     oracle.oilpaint_rows(buf, W, H, STRIDE, BPP, RADIUS, LEVELS, y0, y0 + probe)
     dt = time.perf_counter() - t
@@ -257,11 +271,7 @@ def run_ours(args):
     step_ms = [e[0].elapsed_time(e[2]) for e in ev]
     pack_ms = [e[0].elapsed_time(e[1]) for e in ev]
     filt_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(statistics.mean(step_ms))
     value = world * W * H / (ms / 1e3) / 1e6
 
     # roofline of the dominant kernel (the filter): integer-ALU bound
@@ -344,13 +354,14 @@ def _kernel_hash() -> str:
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--config", default=None, help="launch config JSON, e.g. '{\"tile_w\": 64}'")
     p.add_argument("--autotune", action="store_true", help="search the launch config first")
     p.add_argument("--skip-batch", action="store_true")
-    p.add_argument("--serve-seconds", type=float, default=0.0)
+    p.add_argument("--serve-seconds", type=float, default=3.0,
+                   help="seconds of served traffic per offered load (0 skips serving)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--ref-rows", type=int, default=96, help="rows per reference step")

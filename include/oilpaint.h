@@ -167,8 +167,11 @@ int op_destroy(op_t *op);
 
 /* ---- batched, persistent form ------------------------------------------- */
 
-/* One image of a batch.  in/out: device pointers (height*stride bytes, not
- * overlapping); other fields as op_create_ex. */
+/* One image of a batch.  in/out: device pointers; the input's rows are
+ * `stride` bytes apart, the output's `out_stride` bytes apart (0 = stride),
+ * so the input may be a strided crop of a larger image and the output packed.
+ * The (height-1) pitches plus one row of pixels that each spans must not
+ * overlap.  Other fields as op_create_ex. */
 typedef struct {
   const uint8_t *in;
   uint8_t *out;
@@ -176,7 +179,7 @@ typedef struct {
   int32_t radius;
   uint32_t levels;
   uint32_t flags;
-  uint32_t reserved; /* must be 0 */
+  uint32_t out_stride;
 } op_image_t;
 
 typedef struct op_batch_s op_batch_t;

@@ -71,7 +71,7 @@ class op_image_t(ctypes.Structure):
                 ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("stride", ctypes.c_uint32), ("bpp", ctypes.c_uint32),
                 ("radius", ctypes.c_int32), ("levels", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("out_stride", ctypes.c_uint32)]
 
 
 _lib = None

@@ -388,6 +388,7 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   d.w = op->w;
   d.h = op->h;
   d.stride = op->stride;
+  d.ostride = op->stride;
   d.bpp = op->bpp;
   d.r = op->r;
   d.L = op->L;
@@ -560,8 +561,8 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
   b->grid_persist = occ * di.sms;
   b->grid_pack = 8 * di.sms;
   size_t o = 0;
-  b->off_ctrl = o;
-  o = align_up(o + 2 * sizeof(uint32_t), kAlign);
+  b->off_ctrl = o;  // queue counter, error word, timeout diagnostic record (words 8..23)
+  o = align_up(o + 24 * sizeof(uint32_t), kAlign);
   b->off_hdr = o;
   o = align_up(o + sizeof(uint32_t), kAlign);
   b->off_descs = o;
@@ -632,12 +633,19 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
   uint64_t padded = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const op_image_t &im = images[i];
-    if (!im.in || !im.out || im.reserved ||
+    const uint32_t ostride = im.out_stride ? im.out_stride : im.stride;
+    if (!im.in || !im.out ||
         !valid_image(im.width, im.height, im.stride, im.bpp, im.radius, im.levels, im.flags) ||
+        static_cast<uint64_t>(ostride) < static_cast<uint64_t>(im.width) * im.bpp ||
         im.radius > b->max_r || im.levels > b->max_L)
       return OP_E_INVALID;
-    if (ranges_overlap(im.in, im.out, static_cast<size_t>(im.height) * im.stride))
-      return OP_E_INVALID;
+    // the bytes each image actually spans: (h-1) pitches plus one row of pixels
+    const size_t row = static_cast<size_t>(im.width) * im.bpp;
+    const uintptr_t ia = reinterpret_cast<uintptr_t>(im.in);
+    const uintptr_t oa = reinterpret_cast<uintptr_t>(im.out);
+    const size_t in_span = static_cast<size_t>(im.height - 1) * im.stride + row;
+    const size_t out_span = static_cast<size_t>(im.height - 1) * ostride + row;
+    if (ia < oa + out_span && oa < ia + in_span) return OP_E_INVALID;
     padded += static_cast<uint64_t>(packed_pitch(im.width)) * im.height;
     uint32_t th = 0;
     {
@@ -675,6 +683,7 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     d.w = im.width;
     d.h = im.height;
     d.stride = im.stride;
+    d.ostride = im.out_stride ? im.out_stride : im.stride;
     d.bpp = im.bpp;
     d.r = im.radius;
     d.L = im.levels;
@@ -698,7 +707,7 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
   hrp[n] = static_cast<uint32_t>(rows);
   *hn = n;
   if (!b->ctrl_clean) {
-    if (cudaMemsetAsync(b->ws + b->off_ctrl, 0, 2 * sizeof(uint32_t), s) != cudaSuccess)
+    if (cudaMemsetAsync(b->ws + b->off_ctrl, 0, 24 * sizeof(uint32_t), s) != cudaSuccess)
       return OP_E_CUDA;
     b->ctrl_clean = true;
   }

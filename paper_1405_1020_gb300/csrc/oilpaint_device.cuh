@@ -46,17 +46,22 @@ constexpr int kMaxRadiusB = 44;
 
 // bits of the device error word
 constexpr uint32_t kErrTimeout = 1u;
+// Words of the timeout diagnostic record: [0] set once, then image w, h,
+// tile x0, y0, y1, chunk k, chunks, global chunk, slots, expected parity,
+// chunks issued, barrier word lo, hi, r | L << 16, box width | ch << 16.
+constexpr int kDiagWords = 16;
 
 // One image, as the kernels see it.
 struct __align__(16) ImgDesc {
-  const uint8_t *in;        // device, h*stride bytes
-  uint8_t *out;             // device, h*stride bytes
+  const uint8_t *in;        // device, rows `stride` bytes apart
+  uint8_t *out;             // device, rows `ostride` bytes apart
   uint32_t *packed;         // device, h*ppitch words (pack prepass output)
   const CUtensorMap *tmap;  // device copy of the packed image's tensor map (batch path)
   uint32_t w, h, stride, bpp;
   int32_t r;
   uint32_t L, mode, ppitch;  // mode: 0 = paper level, 1 = divide by 3 first
   uint32_t tile_h, tiles_x, boxw, variant;
+  uint32_t ostride;  // output row pitch in bytes
 };
 
 // Geometry of the shared-memory halo ring, fixed per launch.  Chunk k of a
@@ -118,6 +123,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     if (mbar_try_wait(bar, parity)) return true;
     if (global_timer_ns() - t0 > timeout_ns) return false;
   }
+}
+
+// Makes the tensor-map proxy re-read a 128-byte tensor map in global memory:
+// the batch path rewrites its device-resident tensor maps between launches
+// (by host copies), and a descriptor cached from an earlier launch would
+// describe another image and another box size.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -418,7 +433,7 @@ __device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc,
 // Writes the output pixel (x, y): R, G, B and, with 4 bytes per pixel, alpha.
 __device__ __forceinline__ void store_pixel(const ImgDesc &d, int x, int y, uint32_t R,
                                             uint32_t G, uint32_t B, uint32_t alpha) {
-  uint8_t *o = d.out + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * d.bpp;
+  uint8_t *o = d.out + static_cast<size_t>(y) * d.ostride + static_cast<size_t>(x) * d.bpp;
   if (d.bpp == 4) {
     const uint32_t v = R | (G << 8) | (B << 16) | (alpha << 24);
     if ((reinterpret_cast<uintptr_t>(o) & 3u) == 0) {
@@ -497,10 +512,17 @@ __device__ __forceinline__ void window2_update(const Hist<NT, VAR> *hs, const ui
 // chunk_ctr counts the chunks this CTA has consumed and is advanced by the
 // tile.  Returns false if a halo copy did not arrive within timeout_ns (error
 // recorded in *err).
+//
+// diag (may be null): 16 words that receive, on the first timeout only, where
+// the wait gave up -- see kDiagWords.
+//
+// tmap_global: the tensor map lives in global memory (batch path) and may
+// have been rewritten since an earlier launch; it is fenced before use.
 template <int NT, int CPT, int VAR>
 __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
                          const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
-                         uint32_t *err, uint64_t timeout_ns) {
+                         uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
+                         bool tmap_global = false) {
   static_assert(CPT == 1 || CPT == 2, "one or two output columns per thread");
   const int t = threadIdx.x;
   const int r = d.r;
@@ -546,6 +568,7 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
   __syncthreads();  // the previous tile no longer reads the ring
   int issued = min(static_cast<int>(rc.pf), nchunks);
   if (t == 0) {
+    if (tmap_global) fence_tensormap_acquire(tmap);
     fence_proxy_async_smem();
     for (int k = 0; k < issued; ++k) issue(k);
   }
@@ -561,6 +584,21 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicOr(err, kErrTimeout);
+        if (diag && atomicCAS(diag, 0u, 1u) == 0u) {
+          const uint32_t slot = g % rc.nslot;
+          uint32_t blo, bhi;
+          asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                       : "=r"(blo), "=r"(bhi)
+                       : "r"(sm.bars + slot * 8u));
+          const uint32_t rec[15] = {d.w, d.h, static_cast<uint32_t>(x0),
+                                    static_cast<uint32_t>(y0), static_cast<uint32_t>(y1),
+                                    static_cast<uint32_t>(k), static_cast<uint32_t>(nchunks), g,
+                                    rc.nslot, (g / rc.nslot) & 1u, static_cast<uint32_t>(issued),
+                                    blo, bhi, static_cast<uint32_t>(r) | (L << 16),
+                                    d.boxw | (rc.ch << 16)};
+          for (int i = 0; i < 15; ++i) diag[1 + i] = rec[i];
+          __threadfence();
+        }
         // wait, again bounded, for the copies still in flight
         for (int j = k; j < issued; ++j) {
           const uint32_t gj = chunk_ctr + static_cast<uint32_t>(j);
@@ -622,14 +660,23 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
       } else if (interior && do_rm) {
         window2_update<NT, VAR, false, true>(hs, pe, pl, r, (jl & 1) != 0);
       } else if (active && (do_add || do_rm)) {
-        // border thread: columns outside the image are skipped
+        // border thread: EL and ER only when inside the image, the core
+        // clipped to it; same paired updates, no per-column branches
         const int last = 2 * r + 1;
-        for (int j = 0; j <= last; ++j) {
-          const int c = cl + j;
-          if (c < 0 || c >= W) continue;
-          const Hist<NT, VAR> &hh = j == 0 ? hs[1] : (j == last ? hs[2] : hs[0]);
-          if (do_rm) hh.sub(pl[j]);
-          if (do_add) hh.add(pe[j]);
+        const bool el_ok = cl >= 0, er_ok = cr < W;
+        const int j0 = max(cl + 1, 0) - cl, j1 = min(cr - 1, W - 1) - cl;
+        if (do_add && do_rm) {
+          if (el_ok) hs[1].addsub(pe[0], pl[0]);
+          for (int j = j0; j <= j1; ++j) hs[0].addsub(pe[j], pl[j]);
+          if (er_ok) hs[2].addsub(pe[last], pl[last]);
+        } else if (do_add) {
+          if (el_ok) hs[1].add(pe[0]);
+          for (int j = j0; j <= j1; ++j) hs[0].add(pe[j]);
+          if (er_ok) hs[2].add(pe[last]);
+        } else {
+          if (el_ok) hs[1].sub(pl[0]);
+          for (int j = j0; j <= j1; ++j) hs[0].sub(pl[j]);
+          if (er_ok) hs[2].sub(pl[last]);
         }
       }
       if (out_now) {

@@ -100,11 +100,14 @@ __global__ void __launch_bounds__(NT, 1)
     const int x0 = static_cast<int>(local % d.tiles_x) * NT * CPT;
     const int y0 = static_cast<int>((local / d.tiles_x) * d.tile_h);
     const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
+    // the batch's control block keeps a timeout diagnostic record 8 words
+    // after the error word
+    uint32_t *diag = err + 7;
     const bool ok = d.variant == kVarA
                         ? run_tile<NT, CPT, kVarA>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
-                                                   timeout_ns)
+                                                   timeout_ns, diag, true)
                         : run_tile<NT, CPT, kVarB>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
-                                                   timeout_ns);
+                                                   timeout_ns, diag, true);
     if (!ok) break;
   }
 }

@@ -140,6 +140,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   d.w = width;
   d.h = height;
   d.stride = stride;
+  d.ostride = stride;
   d.bpp = bpp;
   d.r = radius;
   d.L = levels;

@@ -181,6 +181,7 @@ class Batch:
             self._ws = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
             base = self._ws.data_ptr()
             aligned = (base + 255) // 256 * 256
+            self._ws_off = aligned - base
             B.check(B.op_batch_set_workspace(h, aligned, n), "op_batch_set_workspace")
         self._keep: list = []
         self.n = 0
@@ -191,16 +192,20 @@ class Batch:
         return sum(((w + 3) // 4 * 4) * h for w, h, *_ in images)
 
     def set(self, images: Sequence[tuple], stream=None) -> None:
-        """images: (src, dst, width, height, stride, bpp, radius, levels[, flags])
-        with src/dst CUDA uint8 tensors."""
+        """images: (src, dst, width, height, stride, bpp, radius, levels[, flags
+        [, out_stride]]) with src/dst CUDA uint8 tensors; out_stride is the
+        output's row pitch (default: stride)."""
         arr = (B.op_image_t * max(1, len(images)))()
         keep = []
         for i, im in enumerate(images):
             src, dst, w, h, stride, bpp, r, L = im[:8]
             flags = im[8] if len(im) > 8 else B.OP_LEVEL_PAPER
-            _check_dev_buf(src, h * stride, f"images[{i}].src")
-            _check_dev_buf(dst, h * stride, f"images[{i}].dst")
-            arr[i] = B.op_image_t(src.data_ptr(), dst.data_ptr(), w, h, stride, bpp, r, L, flags, 0)
+            ostride = im[9] if len(im) > 9 and im[9] else stride
+            # a strided crop only needs its last row's pixels after (h-1) pitches
+            _check_dev_buf(src, (h - 1) * stride + w * bpp, f"images[{i}].src")
+            _check_dev_buf(dst, (h - 1) * ostride + w * bpp, f"images[{i}].dst")
+            arr[i] = B.op_image_t(src.data_ptr(), dst.data_ptr(), w, h, stride, bpp, r, L, flags,
+                                  ostride)
             keep += [src, dst]
         B.check(B.op_batch_set(self._h, arr, len(images), _stream_handle(stream)), "op_batch_set")
         self._keep = keep
@@ -210,6 +215,15 @@ class Batch:
         c = B.op_config_t()
         B.check(B.op_batch_get_config(self._h, c), "op_batch_get_config")
         return c.as_dict()
+
+    def diagnostics(self) -> list[int]:
+        """The timeout diagnostic record of the batch's control block (16
+        words: a set flag, then image w, h, tile x0, y0, y1, chunk, chunks,
+        global chunk, ring slots, expected parity, chunks issued, barrier
+        word lo/hi, r | L << 16, box width | chunk rows << 16)."""
+        torch.cuda.synchronize()
+        words = self._ws[self._ws_off + 32:self._ws_off + 96].cpu().numpy().view("<u4")
+        return [int(v) for v in words]
 
     def run(self, stream=None) -> None:
         B.check(B.op_batch_run(self._h, _stream_handle(stream)), "op_batch_run")

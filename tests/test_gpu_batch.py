@@ -145,6 +145,40 @@ def test_empty_batch_and_reuse():
     b.close()
 
 
+def test_strided_crops_with_packed_outputs():
+    """Inputs that are crops of a larger image (its row pitch) written to
+    packed outputs (a different pitch), as the server does."""
+    big = synth.camera_like(300, 500, seed=12, npoly=30, rad_range=(5, 150))
+    pool = torch.from_numpy(big.reshape(300, -1)).cuda()
+    pstride = 500 * 3
+    rng = np.random.default_rng(13)
+    crops = []
+    for i in range(10):
+        w, h = int(rng.integers(1, 200)), int(rng.integers(1, 120))
+        x0, y0 = int(rng.integers(0, 500 - w + 1)), int(rng.integers(0, 300 - h + 1))
+        if i == 0:  # a crop ending at the pool's last byte
+            w, h, x0, y0 = 77, 40, 500 - 77, 300 - 40
+        crops.append((w, h, x0, y0, int(rng.choice([2, 7, 15])), 20))
+    descs, outs = [], []
+    for w, h, x0, y0, r, L in crops:
+        src = pool.view(-1)[y0 * pstride + x0 * 3:]
+        out = torch.full((w * h * 3,), OUT_FILL, dtype=torch.uint8, device="cuda")
+        outs.append(out)
+        descs.append((src, out, w, h, pstride, 3, r, L, 0, w * 3))
+    torch.cuda.synchronize()
+    b = Batch(16, 200000, 15, 20)
+    b.set(descs)
+    b.run()
+    assert b.sync_status() == B.OP_OK
+    torch.cuda.synchronize()
+    for (w, h, x0, y0, r, L), out in zip(crops, outs):
+        crop = np.ascontiguousarray(big[y0:y0 + h, x0:x0 + w])
+        want = oracle.oilpaint(crop.reshape(-1), w, h, w * 3, 3, r, L,
+                               out=np.full(w * h * 3, OUT_FILL, np.uint8))
+        assert np.array_equal(out.cpu().numpy(), want), (w, h, x0, y0, r)
+    b.close()
+
+
 def test_batch_rejects_invalid_sets():
     img = torch.zeros(30 * 20 * 3, dtype=torch.uint8, device="cuda")
     out = torch.zeros_like(img)
