@@ -71,11 +71,21 @@ typedef struct op_s op_t;
  *                   the number of resident CTAs);
  *   chunk_rows      input rows per TMA halo copy, 1..32;
  *   prefetch        halo copies in flight ahead of the one being consumed, 1..4;
- *   cols_per_thread output columns per thread: 1 (one running histogram per
- *                   output column) or 2 (two neighbouring columns share the
- *                   2r window columns they have in common); 0 = 1.
- * The halo copy of a tile is tile_w + 2r + up to 3 columns wide and must not
- * exceed 256 columns.
+ *   cols_per_thread output columns per thread: 1 (one running histogram of
+ *                   the window per output column), 2 or 4 (difference
+ *                   histograms: each thread keeps the window histogram H of
+ *                   its first column and, for each next column i, the
+ *                   histogram D_i of the column entering minus the column
+ *                   leaving the window, so the window of column i is
+ *                   H + D_1 + ... + D_i; 2(2r+1) + 4(K-1) bin updates per K
+ *                   outputs instead of 2(2r+1) per output); 0 = 1.  2 and 4
+ *                   need radius <= 15 and levels <= 32, else the
+ *                   configuration is refused (OP_E_UNSUPPORTED) by
+ *                   op_set_config; a batch runs its other images on the
+ *                   one-column path.
+ * The halo copy of a tile is at most 256 columns wide: tile_w + 2r + up to
+ * 3 columns for one column per thread, K * (threads - 1 + ceil((2r+K-1)/K)
+ * + 1) rounded up to 4 for K columns per thread.
  */
 typedef struct {
   uint32_t tile_w;
@@ -189,8 +199,11 @@ typedef struct op_batch_s op_batch_t;
  * most `max_pixels` pixels in total, every radius <= max_radius and level
  * count <= max_levels.  All images of a run share one persistent kernel
  * launch: each CTA takes (image, tile) tickets from a device-side atomic
- * counter until the queue is empty.  cfg: tile_w, chunk_rows and prefetch of
- * that launch (NULL = defaults; tile_h is chosen per image).  Returns NULL
+ * counter until the queue is empty.  cfg: tile_w, chunk_rows, prefetch and
+ * cols_per_thread of that launch (NULL = defaults; tile_h is chosen per
+ * image); with 2 or 4 columns per thread, images of radius <= 15 and
+ * <= 32 levels take the difference-histogram path and the others one
+ * column per thread with tile_w / cols_per_thread threads.  Returns NULL
  * with op_last_error() on failure.
  */
 op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t max_radius,

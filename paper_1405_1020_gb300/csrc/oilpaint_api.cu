@@ -94,12 +94,19 @@ std::mutex g_tune_mu;
 std::map<std::pair<int, uint32_t>, op_config_t> g_tune;
 
 // Output columns per thread and threads per CTA of a configuration.
-int cols_per_thread(const op_config_t &c) { return c.cols_per_thread == 2 ? 2 : 1; }
-uint32_t threads_of(const op_config_t &c) { return c.tile_w / cols_per_thread(c); }
+int cols_per_thread(const op_config_t &c) {
+  return (c.cols_per_thread == 2 || c.cols_per_thread == 4) ? static_cast<int>(c.cols_per_thread)
+                                                           : 1;
+}
+uint32_t threads_of(const op_config_t &c) {
+  return c.tile_w / static_cast<uint32_t>(cols_per_thread(c));
+}
 
 // Range checks that need no device.
 bool config_in_range(const op_config_t &c) {
-  if (c.cols_per_thread > 2) return false;
+  if (c.cols_per_thread != 0 && c.cols_per_thread != 1 && c.cols_per_thread != 2 &&
+      c.cols_per_thread != 4)
+    return false;
   const uint32_t cpt = static_cast<uint32_t>(cols_per_thread(c));
   if (c.tile_w % cpt) return false;
   const uint32_t nt = c.tile_w / cpt;
@@ -108,27 +115,63 @@ bool config_in_range(const op_config_t &c) {
   return c.tile_h <= OP_MAX_DIM;
 }
 
-size_t smem_for(const op_config_t &c, int r, uint32_t L) {
-  const RingCfg rc = opk::make_ring(r, c.chunk_rows, c.prefetch, opk::box_width(c.tile_w, r));
-  return opk::tile_smem_bytes(threads_of(c), cols_per_thread(c), L, opk::variant_for_radius(r),
-                              rc);
+opk::Geometry geometry_of(const op_config_t &c, int r, uint32_t L, uint32_t w) {
+  return opk::image_geometry(threads_of(c), cols_per_thread(c), r, L, w);
 }
 
-// Range checks plus "fits one CTA" for radius r and L levels.
+size_t smem_of(const opk::Geometry &g, const op_config_t &c, int r, uint32_t L) {
+  const RingCfg rc = opk::make_ring(r, c.chunk_rows, c.prefetch, g.boxw);
+  return opk::tile_smem_bytes(opk::hist_bytes(g.nt, g.kcols, L, g.variant), rc);
+}
+
+size_t smem_for(const op_config_t &c, int r, uint32_t L) {
+  return smem_of(geometry_of(c, r, L, 1u), c, r, L);
+}
+
+// What a persistent CTA of configuration c needs to run every image of
+// radius <= max_r and levels <= max_L: the widest halo box and the largest
+// histogram area over the one-column path (any image) and, for 2 or 4
+// columns per thread, the difference-histogram path (r <= 15, L <= 32).
+struct BatchNeeds {
+  uint32_t boxw;
+  size_t hist;
+};
+
+BatchNeeds batch_needs(const op_config_t &c, int max_r, uint32_t max_L) {
+  const uint32_t nt = threads_of(c);
+  const int k = cols_per_thread(c);
+  BatchNeeds n;
+  n.boxw = opk::box_width(nt, max_r);
+  n.hist = opk::hist_bytes(nt, 1, max_L, opk::variant_for_radius(max_r));
+  if (k > 1) {
+    const int rd = std::min(max_r, static_cast<int>(opk::kDeltaMaxRadius));
+    const uint32_t Ld = std::min(max_L, static_cast<uint32_t>(opk::kDeltaMaxLevels));
+    n.boxw = std::max(n.boxw, opk::delta_box_width(nt, k, rd));
+    n.hist = std::max(n.hist, opk::hist_bytes(nt, k, Ld, opk::kVarA));
+  }
+  return n;
+}
+
+size_t batch_smem(const op_config_t &c, const BatchNeeds &n) {
+  return opk::tile_smem_bytes(n.hist, opk::make_ring(0, c.chunk_rows, c.prefetch, n.boxw));
+}
+
+// Range checks plus "runs as asked and fits one CTA" for radius r, L levels.
 int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
   if (!config_in_range(c)) return OP_E_INVALID;
-  if (opk::box_width(c.tile_w, r) > 256u) return OP_E_UNSUPPORTED;
-  if (smem_for(c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
+  const opk::Geometry g = geometry_of(c, r, L, 1u);
+  if (g.kcols != cols_per_thread(c)) return OP_E_UNSUPPORTED;  // no difference path here
+  if (g.boxw > 256u) return OP_E_UNSUPPORTED;
+  if (smem_of(g, c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
   return OP_OK;
 }
 
-// Built-in default: the first of a preference list whose shared memory
-// leaves room for >= 2 CTAs per SM, 8-row halo chunks, one chunk in flight.
-// (Measured on GB300: one column per thread beats two at every tested
-// radius and level count, because three histograms per thread cap the
-// resident warps; 64-128 threads are within a few percent of each other.)
+// Built-in default: the first of a preference list that runs and whose shared
+// memory leaves room for >= 2 CTAs per SM, 8-row halo chunks, one chunk in
+// flight; difference histograms over 4 or 2 columns per thread first where
+// they apply (r <= 15, L <= 32).
 op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
-  static const uint32_t prefs[][2] = {{128, 1}, {96, 1}, {64, 1}, {32, 1}};
+  static const uint32_t prefs[][2] = {{32, 4}, {64, 2}, {128, 1}, {96, 1}, {64, 1}, {32, 1}};
   for (const auto &p : prefs) {
     op_config_t c = {p[0] * p[1], 0, 8, 1, p[1]};
     if (check_config(c, r, L, di) != OP_OK) continue;
@@ -175,10 +218,10 @@ uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
 uint32_t effective_tile_h(const op_config_t &c, uint32_t w, uint32_t h, int r, uint32_t L,
                           const DevInfo &di) {
   if (c.tile_h) return std::min(c.tile_h, h);
-  const int variant = opk::variant_for_radius(r);
-  const int occ = std::max(1, opk::tile_occupancy(threads_of(c), cols_per_thread(c), variant,
-                                                  smem_for(c, r, L)));
-  return auto_tile_h(h, (w + c.tile_w - 1) / c.tile_w, r, static_cast<uint64_t>(occ) * di.sms);
+  const opk::Geometry g = geometry_of(c, r, L, w);
+  const int occ = std::max(1, opk::tile_occupancy(g.nt, false, g.kcols, g.variant,
+                                                  smem_of(g, c, r, L)));
+  return auto_tile_h(h, g.tiles_x, r, static_cast<uint64_t>(occ) * di.sms);
 }
 
 bool valid_image(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int32_t r, uint32_t L,
@@ -372,10 +415,10 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   int st = ensure_workspace(op);
   if (st != OP_OK) return st;
   const op_config_t &c = op->cfg;
-  const uint32_t boxw = opk::box_width(c.tile_w, op->r);
+  const opk::Geometry g = geometry_of(c, op->r, op->L, op->w);
   if (!op->map_valid) {
     st = encode_packed_map(&op->map, static_cast<const uint32_t *>(op->ws), op->w, op->h,
-                           op->ppitch, boxw, c.chunk_rows);
+                           op->ppitch, g.boxw, c.chunk_rows);
     if (st != OP_OK) return st;
     op->map_valid = true;
   }
@@ -394,20 +437,21 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   d.L = op->L;
   d.mode = op->flags;
   d.ppitch = op->ppitch;
-  d.tiles_x = (op->w + c.tile_w - 1) / c.tile_w;
+  d.tiles_x = g.tiles_x;
   d.tile_h = op->tile_h;
-  d.boxw = boxw;
-  d.variant = static_cast<uint32_t>(opk::variant_for_radius(op->r));
-  const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, boxw);
-  const size_t smem = smem_for(c, op->r, op->L);
+  d.boxw = g.boxw;
+  d.variant = static_cast<uint32_t>(g.variant);
+  d.kcols = static_cast<uint32_t>(g.kcols);
+  d.xshift = g.xshift;
+  const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, g.boxw);
+  const size_t smem = smem_of(g, c, op->r, op->L);
   const int pack_grid = static_cast<int>(std::min<uint32_t>(op->h, 8u * op->di.sms));
   cudaError_t e = opk::launch_pack_single(d, pack_grid, s);
   if (e != cudaSuccess) return OP_E_CUDA;
   if (op->prof_ev && cudaEventRecord(op->prof_ev, s) != cudaSuccess) return OP_E_CUDA;
   const dim3 grid(d.tiles_x, (op->h + d.tile_h - 1) / d.tile_h);
-  e = opk::launch_tile_plain(threads_of(c), cols_per_thread(c), static_cast<int>(d.variant), d,
-                             op->map, rc, grid, smem,
-                             op->d_err, kWaitTimeoutNs, s);
+  e = opk::launch_tile(g.nt, g.kcols, g.variant, d, op->map, rc, grid, smem, op->d_err,
+                       kWaitTimeoutNs, s);
   return e == cudaSuccess ? OP_OK : OP_E_CUDA;
 }
 
@@ -533,9 +577,13 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
       return nullptr;
     }
   }
-  st = check_config(c, max_radius, max_levels, di);
-  if (st != OP_OK) {
-    g_last_error = st;
+  if (!config_in_range(c)) {
+    g_last_error = OP_E_INVALID;
+    return nullptr;
+  }
+  const BatchNeeds needs = batch_needs(c, max_radius, max_levels);
+  if (needs.boxw > 256u || batch_smem(c, needs) > di.smem_optin - 1024u) {
+    g_last_error = OP_E_UNSUPPORTED;
     return nullptr;
   }
   op_batch_t *b = new (std::nothrow) op_batch_t();
@@ -550,9 +598,9 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
   b->device = dev;
   b->di = di;
   b->cfg = c;
-  b->rc = opk::make_ring(max_radius, c.chunk_rows, c.prefetch, opk::box_width(c.tile_w, max_radius));
-  b->smem = smem_for(c, max_radius, max_levels);
-  const int occ = opk::tile_occupancy(threads_of(c), cols_per_thread(c), -1, b->smem);
+  b->rc = opk::make_ring(max_radius, c.chunk_rows, c.prefetch, needs.boxw);
+  b->smem = batch_smem(c, needs);
+  const int occ = opk::tile_occupancy(threads_of(c), true, cols_per_thread(c), -1, b->smem);
   if (occ < 1) {
     delete b;
     g_last_error = OP_E_UNSUPPORTED;
@@ -626,8 +674,10 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     b->ctrl_clean = false;
   }
   // validate and order the images: most expensive tiles first
-  const uint32_t tw = b->cfg.tile_w;
+  const uint32_t nt = threads_of(b->cfg);
+  const int kc = cols_per_thread(b->cfg);
   std::vector<uint32_t> order(n);
+  std::vector<opk::Geometry> geo(n);
   std::vector<double> tile_cost(n);
   std::vector<uint32_t> tile_h(n);
   uint64_t padded = 0;
@@ -656,8 +706,12 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     if (th == 0) th = std::max<uint32_t>(64u, 16u * static_cast<uint32_t>(im.radius));
     th = std::min(th, im.height);
     tile_h[i] = th;
-    const double r = im.radius;
-    tile_cost[i] = (th + 2.0 * r) * (4.0 * r + 2.0) + th * (im.levels + 10.0);
+    geo[i] = opk::image_geometry(nt, kc, im.radius, im.levels, im.width);
+    // per step a tile slides one window column (4r + 2 bin updates) and
+    // K - 1 difference columns (4 each); per output row it scans K argmaxes
+    const double r = im.radius, k = geo[i].kcols;
+    tile_cost[i] = (th + 2.0 * r) * (4.0 * r + 2.0 + 4.0 * (k - 1.0)) +
+                   th * k * (im.levels + 10.0);
     order[i] = i;
   }
   if (padded > b->max_pixels) return OP_E_INVALID;
@@ -690,9 +744,12 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     d.mode = im.flags;
     d.ppitch = packed_pitch(im.width);
     d.tile_h = tile_h[order[k]];
-    d.tiles_x = (im.width + tw - 1) / tw;
-    d.boxw = opk::box_width(tw, im.radius);
-    d.variant = static_cast<uint32_t>(opk::variant_for_radius(im.radius));
+    const opk::Geometry &g = geo[order[k]];
+    d.tiles_x = g.tiles_x;
+    d.boxw = g.boxw;
+    d.variant = static_cast<uint32_t>(g.variant);
+    d.kcols = static_cast<uint32_t>(g.kcols);
+    d.xshift = g.xshift;
     const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc.ch);
     if (st != OP_OK) return st;
     hd[k] = d;

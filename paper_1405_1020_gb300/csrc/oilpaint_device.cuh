@@ -62,7 +62,15 @@ struct __align__(16) ImgDesc {
   uint32_t L, mode, ppitch;  // mode: 0 = paper level, 1 = divide by 3 first
   uint32_t tile_h, tiles_x, boxw, variant;
   uint32_t ostride;  // output row pitch in bytes
+  uint32_t kcols;    // 1: one column per thread (word format 0); 2 or 4: difference
+                     // histograms over kcols columns per thread (word format 1)
+  int32_t xshift;    // x of the first tile (0, or -3..0 so that x0 - r is 4-aligned)
 };
+
+// The difference-histogram path needs r <= 15 (64-bit bins) and L <= 32
+// (5-bit level field next to the valid bit).
+constexpr int kDeltaMaxRadius = 15;
+constexpr uint32_t kDeltaMaxLevels = 32;
 
 // Geometry of the shared-memory halo ring, fixed per launch.  Chunk k of a
 // tile brings the ch rows entering the window during its steps and the ch
@@ -242,9 +250,21 @@ __device__ __forceinline__ uint32_t level_of(uint32_t R, uint32_t G, uint32_t B,
   return l < L ? l : L - 1u;
 }
 
+// Word format 0: level << 24 | R << 16 | G << 8 | B.
 __device__ __forceinline__ uint32_t pack_word(uint32_t R, uint32_t G, uint32_t B, uint32_t L,
                                               uint32_t mode) {
   return (level_of(R, G, B, L, mode) << 24) | (R << 16) | (G << 8) | B;
+}
+
+// Word format 1 (L <= 32), laid out so that one mask gives the low word and
+// one shift and mask the high word of the pixel's bin delta (see DHist):
+//   bit 0 valid (1 for every image pixel; the zero words TMA supplies outside
+//   the image therefore add nothing), bits 1..5 level, 6..9 G >> 4,
+//   10..17 R, 20..27 B, 28..31 G & 15.
+__device__ __forceinline__ uint32_t pack_word_delta(uint32_t R, uint32_t G, uint32_t B,
+                                                    uint32_t L, uint32_t mode) {
+  return 1u | (level_of(R, G, B, L, mode) << 1) | ((G >> 4) << 6) | (R << 10) | (B << 20) |
+         ((G & 0xFu) << 28);
 }
 
 // Packs row y of image d with threads tid, tid+nthr, ...
@@ -253,17 +273,21 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
   const uint8_t *src = d.in + static_cast<size_t>(y) * d.stride;
   uint32_t *dst = d.packed + static_cast<size_t>(y) * d.ppitch;
   const uint32_t L = d.L, mode = d.mode, w = d.w;
+  const bool fmt1 = d.kcols > 1;
+  auto word = [&](uint32_t R, uint32_t G, uint32_t B) {
+    return fmt1 ? pack_word_delta(R, G, B, L, mode) : pack_word(R, G, B, L, mode);
+  };
   if (d.bpp == 4 && (reinterpret_cast<uintptr_t>(src) & 3u) == 0) {
     const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
     for (uint32_t x = tid; x < w; x += nthr) {
       const uint32_t p = __ldg(s4 + x);
-      dst[x] = pack_word(p & 0xFFu, (p >> 8) & 0xFFu, (p >> 16) & 0xFFu, L, mode);
+      dst[x] = word(p & 0xFFu, (p >> 8) & 0xFFu, (p >> 16) & 0xFFu);
     }
   } else {
     const uint32_t bpp = d.bpp;
     for (uint32_t x = tid; x < w; x += nthr) {
       const uint8_t *p = src + x * bpp;
-      dst[x] = pack_word(__ldg(p), __ldg(p + 1), __ldg(p + 2), L, mode);
+      dst[x] = word(__ldg(p), __ldg(p + 1), __ldg(p + 2));
     }
   }
 }
@@ -282,10 +306,11 @@ __device__ __forceinline__ void delta_b(uint32_t w, uint32_t &lo, uint32_t &hi) 
   hi = (w >> 6) & 0x0003FC00u;
 }
 
-// One histogram owned by one thread: level l of thread t lives at
-// sums + l * NT * 8 (+ cnts + l * NT * 4 for variant B), so the 32 lanes of a
-// warp always touch 32 consecutive bins whatever their levels.  Level L is a
-// scratch bin that absorbs the no-op half of a paired update.
+// One histogram owned by one thread (one output column per thread, word
+// format 0): level l of thread t lives at sums + l * NT * 8 (+ cnts + l * NT
+// * 4 for variant B), so the 32 lanes of a warp always touch 32 consecutive
+// bins whatever their levels.  Level L is a scratch bin that absorbs the
+// no-op half of a paired update.
 template <int NT, int VAR>
 struct Hist {
   static constexpr uint32_t kStride64 = NT * 8u;
@@ -352,16 +377,7 @@ struct Hist {
   }
 };
 
-// Sum of two disjoint histograms' count keys.  For variant A the high words
-// are added without the carry out of the low words: that carry could only
-// reach the top bits of the G field, which stay below 2^4 for any window of
-// at most 961 pixels, so the count bits are exact.
-template <int VAR>
-__device__ __forceinline__ uint32_t key_sum(uint32_t a, uint32_t b) {
-  return VAR == kVarA ? ((a + b) & 0xFFC00000u) : a + b;
-}
-
-// Channel sums and count of a (possibly combined) 64-bit bin.
+// Channel sums and count of a word-format-0 bin.
 template <int VAR>
 __device__ __forceinline__ void unpack_bin(uint32_t lo, uint32_t hi, uint32_t cnt_b,
                                            uint32_t &cnt, uint32_t &R, uint32_t &G,
@@ -379,13 +395,69 @@ __device__ __forceinline__ void unpack_bin(uint32_t lo, uint32_t hi, uint32_t cn
   }
 }
 
+// ------------------------------------------- difference-histogram bins
+//
+// Word format 1 bins (64 bits): count:10 @0 | R:18 @10 | G:18 @28 | B:18 @46.
+// The count sits at the bottom of the LOW word, so the low word of a sum of
+// bins is the sum of their low words: adding the low words of a window
+// histogram and of difference histograms gives an exact count without
+// touching the high words.  A pixel's delta is one mask of its word (low
+// word, with the valid bit landing on the count) and one shift and mask
+// (high word); zero words (outside the image) have a zero delta.
+
+__device__ __forceinline__ void dh_delta(uint32_t w, uint32_t &lo, uint32_t &hi) {
+  lo = w & 0xF003FC01u;
+  hi = (w >> 6) & 0x003FC00Fu;
+}
+
+// Address of w's bin in a histogram whose level 0 is at `base` (levels NT*8
+// bytes apart): the level field sits at bits 1..5, so (w & 0x3E) * NT * 4.
+template <int NT>
+__device__ __forceinline__ uint32_t dh_addr(uint32_t base, uint32_t w) {
+  return base + (w & 0x3Eu) * (NT * 4u);
+}
+
+template <int NT>
+__device__ __forceinline__ void dh_add(uint32_t base, uint32_t w) {
+  uint32_t lo, hi;
+  dh_delta(w, lo, hi);
+  bin_add64(dh_addr<NT>(base, w), lo, hi);
+}
+
+template <int NT>
+__device__ __forceinline__ void dh_sub(uint32_t base, uint32_t w) {
+  uint32_t lo, hi;
+  dh_delta(w, lo, hi);
+  bin_sub64(dh_addr<NT>(base, w), lo, hi);
+}
+
+// +win -wout as one two-deep update (same-level pairs fold into one delta,
+// the other half goes to the scratch bin at base + scratch_off).
+template <int NT>
+__device__ __forceinline__ void dh_addsub(uint32_t base, uint32_t win, uint32_t wout,
+                                          uint32_t scratch_off) {
+  uint32_t alo, ahi, blo, bhi;
+  dh_delta(win, alo, ahi);
+  dh_delta(wout, blo, bhi);
+  const uint32_t aa = dh_addr<NT>(base, win);
+  uint32_t ab = dh_addr<NT>(base, wout);
+  if (aa == ab) {
+    const uint64_t net =
+        (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
+    alo = static_cast<uint32_t>(net);
+    ahi = static_cast<uint32_t>(net >> 32);
+    ab = base + scratch_off;
+  }
+  bin_addsub64(aa, alo, ahi, ab, blo, bhi);
+}
+
 // ------------------------------------------------------------ division
 
-// Truncating n / d for the channel means.  Variant A (n < 2^18, d <= 961):
+// Truncating n / d for the channel means.  r <= 15 (n < 2^18, d <= 961):
 // Granlund and Montgomery's multiply-high by m = ceil(2^31 / d) from a
 // per-CTA table, q = floor(2n * m / 2^32); with e = m*d - 2^31 < d the error
-// term n*e / 2^31 stays below 2^28 / 2^31 < 1, so q is exact.  Variant B
-// uses integer division.
+// term n*e / 2^31 stays below 2^28 / 2^31 < 1, so q is exact.  Larger radii
+// use integer division.
 constexpr uint32_t kRcpEntries = 962;  // d = 0..961 (entry 0 unused)
 
 __device__ __forceinline__ void fill_rcp_table(uint32_t *rcp) {
@@ -401,14 +473,14 @@ __device__ __forceinline__ uint32_t div_mean(uint32_t n, uint32_t d, uint32_t m)
 
 // ----------------------------------------------------------------- tiles
 
-// Shared-memory carve-up common to both kernels.  `smem` is the dynamic
+// Shared-memory carve-up common to all kernels.  `smem` is the dynamic
 // shared memory base; every region starts on a 128-byte boundary.
 struct SmemMap {
   uint32_t bars;  // nslot mbarriers
   uint32_t ring;  // nslot * slot_bytes
   uint32_t rcp;   // kRcpEntries reciprocals
-  uint32_t sums;  // nhist * (L + 1) * NT * 8
-  uint32_t cnts;  // nhist * (L + 1) * NT * 4 (variant B)
+  uint32_t sums;  // histogram bins
+  uint32_t cnts;  // variant B counts
   uint8_t *ring_ptr;
   uint32_t *rcp_ptr;
 };
@@ -455,105 +527,32 @@ __device__ __forceinline__ uint32_t load_alpha(const ImgDesc &d, int x, int y) {
   return __ldg(d.in + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * 4u + 3u);
 }
 
-// CPT = 2, interior thread: one step's updates over the 2r+2 ring words of
-// columns xa-r .. xa+r+1 (EL, the 2r core columns, ER) of the entering row pe
-// (ADD) and/or the leaving row pl (RM).  Words are read in 8-byte pairs from
-// even ring indices (ring rows are 16-byte aligned): with an even start the
-// pairs are (EL, core), (core, core)..., (core, ER); with an odd start EL
-// and ER are single words around core pairs.
-template <int NT, int VAR, bool ADD, bool RM>
-__device__ __forceinline__ void window2_update(const Hist<NT, VAR> *hs, const uint32_t *pe,
-                                               const uint32_t *pl, int r, bool odd) {
-  auto upd = [&](const Hist<NT, VAR> &h, uint32_t a, uint32_t b) {
-    if (ADD && RM)
-      h.addsub(a, b);
-    else if (ADD)
-      h.add(a);
-    else
-      h.sub(b);
-  };
-  auto pair = [&](int j, const Hist<NT, VAR> &hx, const Hist<NT, VAR> &hy) {
-    uint2 a = make_uint2(0u, 0u), b = make_uint2(0u, 0u);
-    if (ADD) a = *reinterpret_cast<const uint2 *>(pe + j);
-    if (RM) b = *reinterpret_cast<const uint2 *>(pl + j);
-    upd(hx, a.x, b.x);
-    upd(hy, a.y, b.y);
-  };
-  auto single = [&](int j, const Hist<NT, VAR> &h) {
-    upd(h, ADD ? pe[j] : 0u, RM ? pl[j] : 0u);
-  };
-  if (!odd) {
-    pair(0, hs[1], r ? hs[0] : hs[2]);
-#pragma unroll 2
-    for (int j = 2; j <= 2 * r - 2; j += 2) pair(j, hs[0], hs[0]);
-    if (r) pair(2 * r, hs[0], hs[2]);
-  } else {
-    single(0, hs[1]);
-#pragma unroll 2
-    for (int j = 1; j <= 2 * r - 1; j += 2) pair(j, hs[0], hs[0]);
-    single(2 * r + 1, hs[2]);
-  }
-}
-
-// Output tile [x0, x0 + NT*CPT) x [y0, y1) of image d; thread t owns the CPT
-// output columns x0 + CPT*t ...
-//
-// CPT = 1: one histogram per thread, the window's 2r+1 columns.
-// CPT = 2: outputs x and x+1 share the 2r columns x-r+1 .. x+r.  The thread
-//   keeps a "core" histogram of those columns and two one-column histograms,
-//   EL of column x-r and ER of column x+r+1; output x is core + EL, output x+1
-//   core + ER.  A step then costs 2(2r+2) bin updates for two outputs instead
-//   of 2 * 2(2r+1).
-//
-// Step s of the tile adds entering row y0 - r + s and removes leaving row
-// y0 - r + s - (2r+1).  Chunk k covers steps [k*ch, (k+1)*ch): its entering
-// and leaving rows arrive by two TMA copies in ring slot (chunk_ctr + k) %
-// nslot, whose mbarrier completes its phase ((chunk_ctr + k) / nslot) & 1.
-// chunk_ctr counts the chunks this CTA has consumed and is advanced by the
-// tile.  Returns false if a halo copy did not arrive within timeout_ns (error
-// recorded in *err).
-//
-// diag (may be null): 16 words that receive, on the first timeout only, where
-// the wait gave up -- see kDiagWords.
-//
+// The halo-ring protocol of one tile.  Step s = 0 .. nsteps-1 adds entering
+// row E0 + s and removes leaving row E0 + s - (2r+1).  Chunk k covers steps
+// [k*ch, (k+1)*ch): its entering and leaving rows arrive by two TMA copies of
+// d.boxw columns from image column xs (a multiple of 4) into ring slot
+// (chunk_ctr + k) % nslot, whose mbarrier completes its phase
+// ((chunk_ctr + k) / nslot) & 1.  chunk_ctr counts the chunks this CTA has
+// consumed and is advanced by the tile.  For each step, step(s, e, l) gets
+// the ring rows of the entering and leaving row, column 0 = image column xs.
+// Returns false if a copy did not arrive within timeout_ns: the error bit is
+// set, the first such event is described in diag (16 words, may be null),
+// and the copies still in flight are waited for (bounded) before returning.
 // tmap_global: the tensor map lives in global memory (batch path) and may
 // have been rewritten since an earlier launch; it is fenced before use.
-template <int NT, int CPT, int VAR>
-__device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
-                         const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
-                         uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
-                         bool tmap_global = false) {
-  static_assert(CPT == 1 || CPT == 2, "one or two output columns per thread");
+template <class Step>
+__device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *tmap, int xs,
+                                          int E0, int nsteps, const RingCfg &rc,
+                                          const SmemMap &sm, uint32_t &chunk_ctr,
+                                          uint32_t *err, uint64_t timeout_ns, uint32_t *diag,
+                                          bool tmap_global, int x0, int y0, int y1,
+                                          Step &&step) {
   const int t = threadIdx.x;
   const int r = d.r;
-  const int W = static_cast<int>(d.w), H = static_cast<int>(d.h);
-  const uint32_t L = d.L;
-  const int xa = x0 + CPT * t;   // first output column of this thread
-  const int xs = (x0 - r) & ~3;  // box start, rounded down to 16 bytes
-  const int cl = xa - r;            // leftmost window column touched
-  const int cr = xa + CPT - 1 + r;  // rightmost window column touched
-  const bool active = xa < W;
-  const bool interior = cl >= 0 && cr < W;
-  const int jl = cl - xs;  // ring index of column cl (>= 0)
-  const int E0 = y0 - r;   // first entering row
-  const int nsteps = (y1 - y0) + 2 * r;
   const int ch = static_cast<int>(rc.ch);
   const int nchunks = (nsteps + ch - 1) / ch;
   const uint32_t box_bytes = d.boxw * rc.ch * 4u;
   const uint32_t boxw = d.boxw;
-  const uint32_t *rcp = sm.rcp_ptr;
-
-  // histograms: [0] the window (CPT 1) or the core (CPT 2), [1] EL, [2] ER;
-  // each has L + 1 levels (the last one is the scratch bin)
-  const uint32_t lvl_bins = (L + 1u) * NT;
-  Hist<NT, VAR> hs[CPT == 1 ? 1 : 3];
-#pragma unroll
-  for (int i = 0; i < (CPT == 1 ? 1 : 3); ++i) {
-    hs[i].sums = sm.sums + (i * lvl_bins + t) * 8u;
-    hs[i].cnts = sm.cnts + (i * lvl_bins + t) * 4u;
-    hs[i].scratch = L;
-    hs[i].clear(L);
-  }
 
   auto issue = [&](int k) {
     const uint32_t g = chunk_ctr + static_cast<uint32_t>(k);
@@ -594,7 +593,7 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
                                     static_cast<uint32_t>(y0), static_cast<uint32_t>(y1),
                                     static_cast<uint32_t>(k), static_cast<uint32_t>(nchunks), g,
                                     rc.nslot, (g / rc.nslot) & 1u, static_cast<uint32_t>(issued),
-                                    blo, bhi, static_cast<uint32_t>(r) | (L << 16),
+                                    blo, bhi, static_cast<uint32_t>(r) | (d.L << 16),
                                     d.boxw | (rc.ch << 16)};
           for (int i = 0; i < 15; ++i) diag[1 + i] = rec[i];
           __threadfence();
@@ -616,27 +615,60 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
       }
       ++issued;
     }
-    const uint32_t *base_e = ring + (g % rc.nslot) * slot_words + jl;
+    const uint32_t *base_e = ring + (g % rc.nslot) * slot_words;
     const uint32_t *base_l = base_e + half_words;
     const int s_end = min((k + 1) * ch, nsteps);
     for (int s = k * ch; s < s_end; ++s) {
-      const int e = E0 + s;         // entering row
-      const int l = e - 2 * r - 1;  // leaving row
-      const bool do_add = e >= 0 && e < H;
-      const bool do_rm = l >= 0 && l >= E0 && l < H;
-      const bool out_now = s >= 2 * r && active;  // output row e - r is complete after this step
-      const uint32_t *pe = base_e + (s - k * ch) * boxw;
-      const uint32_t *pl = base_l + (s - k * ch) * boxw;
-      // the alpha bytes are fetched before the updates so their latency is hidden
-      uint32_t alpha0 = 0, alpha1 = 0;
-      if (out_now && d.bpp == 4) {
-        alpha0 = load_alpha(d, xa, e - r);
-        if (CPT == 2 && xa + 1 < W) alpha1 = load_alpha(d, xa + 1, e - r);
-      }
-      if (CPT == 1) {
-        const Hist<NT, VAR> &h = hs[0];
-        const int j0 = interior ? 0 : max(cl, 0) - cl;
-        const int j1 = interior ? 2 * r + 1 : (active ? min(cr, W - 1) - cl + 1 : 0);
+      const uint32_t off = static_cast<uint32_t>(s - k * ch) * boxw;
+      step(s, base_e + off, base_l + off);
+    }
+  }
+  chunk_ctr += static_cast<uint32_t>(nchunks);
+  return true;
+}
+
+// One output column per thread: tile [x0, x0 + NT) x [y0, y1), thread t owns
+// column x0 + t and a running histogram of its window (2(2r+1) updates per
+// output pixel); border threads clip their windows to the image.
+template <int NT, int VAR>
+__device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
+                         const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
+                         uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
+                         bool tmap_global = false) {
+  const int t = threadIdx.x;
+  const int r = d.r;
+  const int W = static_cast<int>(d.w), H = static_cast<int>(d.h);
+  const uint32_t L = d.L;
+  const int xa = x0 + t;
+  const int xs = (x0 - r) & ~3;  // box start, rounded down to 16 bytes
+  const int cl = xa - r, cr = xa + r;
+  const bool active = xa < W;
+  const bool interior = cl >= 0 && cr < W;
+  const int jl = cl - xs;  // ring index of column cl (>= 0)
+  const int E0 = y0 - r;
+  const int nsteps = (y1 - y0) + 2 * r;
+  const uint32_t *rcp = sm.rcp_ptr;
+  const int j0 = interior ? 0 : max(cl, 0) - cl;
+  const int j1 = interior ? 2 * r + 1 : (active ? min(cr, W - 1) - cl + 1 : 0);
+
+  Hist<NT, VAR> h;
+  h.sums = sm.sums + static_cast<uint32_t>(t) * 8u;
+  h.cnts = sm.cnts + static_cast<uint32_t>(t) * 4u;
+  h.scratch = L;
+  h.clear(L);
+
+  return ring_pass(
+      d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
+      y1, [&](int s, const uint32_t *rowe, const uint32_t *rowl) {
+        const int e = E0 + s;         // entering row
+        const int l = e - 2 * r - 1;  // leaving row
+        const bool do_add = e >= 0 && e < H;
+        const bool do_rm = l >= 0 && l >= E0 && l < H;
+        const bool out_now = s >= 2 * r && active;  // output row e - r is complete
+        const uint32_t *pe = rowe + jl;
+        const uint32_t *pl = rowl + jl;
+        // the alpha byte is fetched before the updates so its latency is hidden
+        const uint32_t alpha = (out_now && d.bpp == 4) ? load_alpha(d, xa, e - r) : 0u;
         if (do_add && do_rm) {
           int j = j0;
           for (; j + 4 <= j1; j += 4) {
@@ -653,86 +685,186 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
         } else if (do_rm) {
           for (int j = j0; j < j1; ++j) h.sub(pl[j]);
         }
-      } else if (interior && do_add && do_rm) {
-        window2_update<NT, VAR, true, true>(hs, pe, pl, r, (jl & 1) != 0);
-      } else if (interior && do_add) {
-        window2_update<NT, VAR, true, false>(hs, pe, pl, r, (jl & 1) != 0);
-      } else if (interior && do_rm) {
-        window2_update<NT, VAR, false, true>(hs, pe, pl, r, (jl & 1) != 0);
-      } else if (active && (do_add || do_rm)) {
-        // border thread: EL and ER only when inside the image, the core
-        // clipped to it; same paired updates, no per-column branches
-        const int last = 2 * r + 1;
-        const bool el_ok = cl >= 0, er_ok = cr < W;
-        const int j0 = max(cl + 1, 0) - cl, j1 = min(cr - 1, W - 1) - cl;
-        if (do_add && do_rm) {
-          if (el_ok) hs[1].addsub(pe[0], pl[0]);
-          for (int j = j0; j <= j1; ++j) hs[0].addsub(pe[j], pl[j]);
-          if (er_ok) hs[2].addsub(pe[last], pl[last]);
-        } else if (do_add) {
-          if (el_ok) hs[1].add(pe[0]);
-          for (int j = j0; j <= j1; ++j) hs[0].add(pe[j]);
-          if (er_ok) hs[2].add(pe[last]);
-        } else {
-          if (el_ok) hs[1].sub(pl[0]);
-          for (int j = j0; j <= j1; ++j) hs[0].sub(pl[j]);
-          if (er_ok) hs[2].sub(pl[last]);
-        }
-      }
-      if (out_now) {
-        const int y = e - r;
-        if (CPT == 1) {
+        if (out_now) {
           uint32_t m = 0, best = 0;
           for (uint32_t lv = 0; lv < L; ++lv) {
-            const uint32_t kk = hs[0].count_key(lv);
+            const uint32_t kk = h.count_key(lv);
             if (kk > best) {
               best = kk;
               m = lv;
             }
           }
           uint32_t lo, hi, cnt, R, G, B;
-          hs[0].bin(m, lo, hi);
+          h.bin(m, lo, hi);
           unpack_bin<VAR>(lo, hi, VAR == kVarB ? best : 0u, cnt, R, G, B);
           const uint32_t mul = VAR == kVarA ? rcp[cnt] : 0u;
-          store_pixel(d, xa, y, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
-                      div_mean<VAR>(B, cnt, mul), alpha0);
-        } else {
-          uint32_t m0 = 0, m1 = 0, b0 = 0, b1 = 0;
-          for (uint32_t lv = 0; lv < L; ++lv) {
-            const uint32_t kc = hs[0].count_key(lv);
-            const uint32_t k0 = key_sum<VAR>(kc, hs[1].count_key(lv));
-            const uint32_t k1 = key_sum<VAR>(kc, hs[2].count_key(lv));
-            if (k0 > b0) {
-              b0 = k0;
-              m0 = lv;
-            }
-            if (k1 > b1) {
-              b1 = k1;
-              m1 = lv;
-            }
-          }
+          store_pixel(d, xa, e - r, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
+                      div_mean<VAR>(B, cnt, mul), alpha);
+        }
+      });
+}
+
+// K-word vector load from a ring row (K-aligned index, rows 16-byte aligned).
+template <int K>
+struct VecOf;
+template <>
+struct VecOf<2> {
+  using T = uint2;
+  static __device__ __forceinline__ uint32_t at(const uint2 &v, int q) { return q ? v.y : v.x; }
+};
+template <>
+struct VecOf<4> {
+  using T = uint4;
+  static __device__ __forceinline__ uint32_t at(const uint4 &v, int q) {
+    return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+  }
+};
+
+// One step's updates of the K histograms of a difference-histogram thread
+// (see run_tile_delta) from the ring words 0 .. 2r+K-1 of its entering row pe
+// and, when RM, its leaving row pl.  Word j (image column xa - r + j) feeds
+//   the window histogram H when j <= 2r,
+//   D_{j+1} negatively (its left column leaves) when j <= K-2,
+//   D_{j-2r} positively (its right column) when j >= 2r+1.
+// Groups of K words are loaded as one vector; the groups that only feed H
+// skip the tests.
+template <int NT, int K, bool RM>
+__device__ __forceinline__ void delta_step(const uint32_t *pe, const uint32_t *pl, int r,
+                                           uint32_t h0, uint32_t hstride, uint32_t scratch_off) {
+  using V = typename VecOf<K>::T;
+  const int last = 2 * r + K - 1;
+  const int ngroups = last / K + 1;
+  auto upd = [&](uint32_t base, uint32_t e, uint32_t l) {
+    if (RM)
+      dh_addsub<NT>(base, e, l, scratch_off);
+    else
+      dh_add<NT>(base, e);
+  };
+  auto updneg = [&](uint32_t base, uint32_t e, uint32_t l) {
+    if (RM)
+      dh_addsub<NT>(base, l, e, scratch_off);
+    else
+      dh_sub<NT>(base, e);
+  };
+  auto word = [&](int j, uint32_t e, uint32_t l) {
+    if (j <= 2 * r) upd(h0, e, l);
+    if (j <= K - 2) updneg(h0 + static_cast<uint32_t>(j + 1) * hstride, e, l);
+    if (j >= 2 * r + 1 && j <= last) upd(h0 + static_cast<uint32_t>(j - 2 * r) * hstride, e, l);
+  };
+  auto load = [&](const uint32_t *p) { return *reinterpret_cast<const V *>(p); };
+  V a = load(pe), b = V{};
+  if (RM) b = load(pl);
 #pragma unroll
-          for (int i = 0; i < 2; ++i) {
-            if (i == 1 && xa + 1 >= W) break;
-            const uint32_t m = i ? m1 : m0;
-            uint32_t clo, chi, elo, ehi, cnt, R, G, B;
-            hs[0].bin(m, clo, chi);
-            hs[1 + i].bin(m, elo, ehi);
-            // 64-bit sum of the core and edge bins
-            const uint64_t v = (static_cast<uint64_t>(chi) << 32 | clo) +
-                               (static_cast<uint64_t>(ehi) << 32 | elo);
-            unpack_bin<VAR>(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32),
-                            VAR == kVarB ? (i ? b1 : b0) : 0u, cnt, R, G, B);
-            const uint32_t mul = VAR == kVarA ? rcp[cnt] : 0u;
-            store_pixel(d, xa + i, y, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
-                        div_mean<VAR>(B, cnt, mul), i ? alpha1 : alpha0);
+  for (int q = 0; q < K; ++q) word(q, VecOf<K>::at(a, q), VecOf<K>::at(b, q));
+  int g = 1;
+#pragma unroll 2
+  for (; (g + 1) * K - 1 <= 2 * r; ++g) {
+    a = load(pe + g * K);
+    if (RM) b = load(pl + g * K);
+#pragma unroll
+    for (int q = 0; q < K; ++q) upd(h0, VecOf<K>::at(a, q), VecOf<K>::at(b, q));
+  }
+  for (; g < ngroups; ++g) {
+    a = load(pe + g * K);
+    if (RM) b = load(pl + g * K);
+#pragma unroll
+    for (int q = 0; q < K; ++q) word(g * K + q, VecOf<K>::at(a, q), VecOf<K>::at(b, q));
+  }
+}
+
+// K output columns per thread through difference histograms (word format 1,
+// r <= 15, L <= 32).  Thread t owns columns xa .. xa+K-1 with xa = x0 + K*t;
+// x0 - r is a multiple of 4 (tiles start at d.xshift), so every thread's
+// window starts on a 16-byte boundary of the ring.  It keeps
+//   H    the histogram of the window of column xa (2r+1 columns),
+//   D_i  (i = 1..K-1) the histogram of column xa+i+r minus that of column
+//        xa+i-1-r, so that the window histogram of column xa+i is
+//        H + D_1 + ... + D_i.
+// A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  The argmax runs
+// over the running sums of the histograms' low words, whose bottom 10 bits
+// are the counts; a key (count << 5) | (31 - level) makes the lowest level
+// win ties under max.  Pixels outside the image are TMA zero fill whose
+// delta is zero, so no thread clips its window.
+template <int NT, int K>
+__device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0,
+                               int y1, const RingCfg &rc, const SmemMap &sm,
+                               uint32_t &chunk_ctr, uint32_t *err, uint64_t timeout_ns,
+                               uint32_t *diag = nullptr, bool tmap_global = false) {
+  static_assert(K == 2 || K == 4, "two or four columns per thread");
+  const int t = threadIdx.x;
+  const int r = d.r;
+  const int W = static_cast<int>(d.w);
+  const uint32_t L = d.L;
+  const int xa = x0 + K * t;
+  const int xs = x0 - r;  // a multiple of 4 by the choice of d.xshift
+  const int jl = K * t;
+  const int E0 = y0 - r;
+  const int nsteps = (y1 - y0) + 2 * r;
+  const uint32_t *rcp = sm.rcp_ptr;
+  const uint32_t lstride = NT * 8u;                 // between levels of one histogram
+  const uint32_t hstride = (L + 1u) * NT * 8u;      // between the K histograms
+  const uint32_t h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
+  const uint32_t scratch_off = L * lstride;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+    for (uint32_t lv = 0; lv < L; ++lv) sts_zero64(h0 + i * hstride + lv * lstride);
+
+  return ring_pass(
+      d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
+      y1, [&](int s, const uint32_t *rowe, const uint32_t *rowl) {
+        const bool rm = s >= 2 * r + 1;  // the leaving row was added by this tile
+        const bool out_now = s >= 2 * r;
+        const int y = E0 + s - r;
+        const uint32_t *pe = rowe + jl;
+        const uint32_t *pl = rowl + jl;
+        uint32_t alpha[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const int x = xa + i;
+          alpha[i] = (out_now && d.bpp == 4 && x >= 0 && x < W) ? load_alpha(d, x, y) : 0u;
+        }
+        if (rm)
+          delta_step<NT, K, true>(pe, pl, r, h0, hstride, scratch_off);
+        else
+          delta_step<NT, K, false>(pe, pl, r, h0, hstride, scratch_off);
+        if (!out_now) return;
+        uint32_t best[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) best[i] = 0u;
+        for (uint32_t lv = 0; lv < L; ++lv) {
+          const uint32_t tag = 31u - lv;
+          uint32_t acc = lds_u32(h0 + lv * lstride);
+          best[0] = max(best[0], ((acc << 5) & 0x7FE0u) | tag);
+#pragma unroll
+          for (int i = 1; i < K; ++i) {
+            acc += lds_u32(h0 + i * hstride + lv * lstride);
+            best[i] = max(best[i], ((acc << 5) & 0x7FE0u) | tag);
           }
         }
-      }
-    }
-  }
-  chunk_ctr += static_cast<uint32_t>(nchunks);
-  return true;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const int x = xa + i;
+          if (x < 0 || x >= W) continue;
+          const uint32_t m = 31u - (best[i] & 31u);
+          const uint32_t cnt = best[i] >> 5;
+          uint32_t lo, hi;
+          lds_v2(h0 + m * lstride, lo, hi);
+          uint64_t v = static_cast<uint64_t>(hi) << 32 | lo;
+#pragma unroll
+          for (int j = 1; j <= i; ++j) {
+            lds_v2(h0 + j * hstride + m * lstride, lo, hi);
+            v += static_cast<uint64_t>(hi) << 32 | lo;
+          }
+          lo = static_cast<uint32_t>(v);
+          hi = static_cast<uint32_t>(v >> 32);
+          const uint32_t R = (lo >> 10) & 0x3FFFFu;
+          const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
+          const uint32_t B = hi >> 14;
+          const uint32_t mul = rcp[cnt];
+          store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul),
+                      __umulhi(B << 1, mul), alpha[i]);
+        }
+      });
 }
 
 // Barrier init and the reciprocal table; ends with a CTA barrier.

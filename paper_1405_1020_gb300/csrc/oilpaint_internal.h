@@ -42,26 +42,77 @@ inline uint32_t box_width(uint32_t tw, int r) {
   return (off + tw + 2u * static_cast<uint32_t>(r) + 3u) & ~3u;
 }
 
-// Dynamic shared memory of a filter CTA of nt threads with cpt output columns
-// per thread (plus 128 bytes of alignment slack).
-inline size_t tile_smem_bytes(uint32_t nt, int cpt, uint32_t lmax, int variant_max,
-                              const RingCfg &rc) {
-  const size_t nhist = cpt == 1 ? 1u : 3u;
-  // L levels plus one scratch level per histogram
+inline bool delta_eligible(int r, uint32_t L) {
+  return r >= 0 && r <= kDeltaMaxRadius && L >= 1 && L <= kDeltaMaxLevels;
+}
+
+// Box width (words) of a difference-histogram tile: thread t reads K-word
+// groups from ring index K*t up to the group holding word 2r+K-1.
+inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
+  const uint32_t ng = (2u * static_cast<uint32_t>(r) + static_cast<uint32_t>(k) - 1u) /
+                          static_cast<uint32_t>(k) + 1u;
+  const uint32_t w = static_cast<uint32_t>(k) * (nt - 1u + ng);
+  return (w + 3u) & ~3u;
+}
+
+// Launch geometry of one image: threads per CTA, columns per thread (2 or 4
+// only where the difference-histogram path applies), tile width, the x of
+// the first tile, tiles per row and the halo box width.
+struct Geometry {
+  uint32_t nt;
+  int kcols;
+  uint32_t tile_w;
+  int32_t xshift;
+  uint32_t tiles_x;
+  uint32_t boxw;
+  int variant;
+};
+
+inline Geometry image_geometry(uint32_t nt, int kcols_wanted, int r, uint32_t L, uint32_t w) {
+  Geometry g;
+  g.nt = nt;
+  g.kcols = (kcols_wanted > 1 && delta_eligible(r, L)) ? kcols_wanted : 1;
+  g.tile_w = nt * static_cast<uint32_t>(g.kcols);
+  g.variant = variant_for_radius(r);
+  if (g.kcols > 1) {
+    // first tile at x0 = xshift with x0 - r a multiple of 4
+    g.xshift = (r & 3) ? (r & 3) - 4 : 0;
+    g.boxw = delta_box_width(nt, g.kcols, r);
+  } else {
+    g.xshift = 0;
+    g.boxw = box_width(nt, r);
+  }
+  g.tiles_x = static_cast<uint32_t>((static_cast<int64_t>(w) - g.xshift + g.tile_w - 1) /
+                                    g.tile_w);
+  return g;
+}
+
+// Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
+// per thread, bins of the variant's size; 2 or 4: that many 64-bit
+// histograms of L + 1 levels per thread).
+inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
+  if (kcols > 1) return static_cast<size_t>(kcols) * (L + 1u) * nt * 8u;
+  return static_cast<size_t>(L + 1u) * nt * bin_bytes(variant);
+}
+
+// Dynamic shared memory of a filter CTA given its histogram bytes (plus 128
+// bytes of alignment slack).
+inline size_t tile_smem_bytes(size_t hist, const RingCfg &rc) {
   return 128u + ((rc.nslot * 8u + 127u) & ~127u) + static_cast<size_t>(rc.nslot) * rc.slot_bytes +
-         kRcpBytes + nhist * (lmax + 1u) * nt * bin_bytes(variant_max);
+         kRcpBytes + hist;
 }
 
 // Launchers; each returns cudaSuccess or the launch error.
 cudaError_t launch_pack_single(const ImgDesc &d, int grid, cudaStream_t s);
-// nt threads per CTA (32, 64, 96, 128), cpt output columns per thread (1, 2)
-cudaError_t launch_tile_plain(uint32_t nt, int cpt, int variant, const ImgDesc &d,
-                              const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
-                              uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
+// nt threads per CTA (32, 64, 96, 128); kcols 1 (one column per thread,
+// histogram variant `variant`) or 2 / 4 (difference histograms)
+cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
+                        const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
+                        uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
 // d_n: device pointer to the number of images (the batch tables are device-resident).
 cudaError_t launch_pack_batch(const ImgDesc *d_descs, const uint32_t *d_row_prefix,
                               const uint32_t *d_n, uint32_t *d_queue, int grid, cudaStream_t s);
-cudaError_t launch_persistent(uint32_t nt, int cpt, const ImgDesc *d_descs,
+cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
                               const uint32_t *d_tile_prefix, const uint32_t *d_n,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
@@ -70,7 +121,8 @@ cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStrea
 // Raise the dynamic shared-memory limit of every filter kernel instance to
 // `bytes`; returns the error of the first failing call.
 cudaError_t set_tile_smem_limit(size_t bytes);
-// Resident CTAs per SM of the plain (variant) or persistent (variant < 0) kernel.
-int tile_occupancy(uint32_t nt, int cpt, int variant, size_t smem);
+// Resident CTAs per SM of the plain (kcols 1: variant), difference-histogram
+// (kcols 2, 4) or persistent kernel.
+int tile_occupancy(uint32_t nt, bool persistent, int kcols, int variant, size_t smem);
 
 }  // namespace opk

@@ -3,9 +3,12 @@
 //   pack_single_kernel / pack_batch_kernel  the pack prepass (one image / a
 //                                           batch; the batch form also resets
 //                                           the tile-queue counter)
-//   tile_plain_kernel<NT, CPT, VAR>         one CTA per output tile (NT threads,
-//                                           CPT output columns per thread)
-//   persistent_kernel<NT, CPT>              grid-sized CTAs pulling
+//   tile_plain_kernel<NT, VAR>              one CTA per output tile, one output
+//                                           column per thread (NT threads)
+//   tile_delta_kernel<NT, K>                one CTA per output tile, K output
+//                                           columns per thread through
+//                                           difference histograms
+//   persistent_kernel<NT, K>                grid-sized CTAs pulling
 //                                           (image, tile) tickets from a
 //                                           device atomic until the queue of a
 //                                           whole batch is empty
@@ -46,39 +49,53 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Histogram bins per CTA: nhist histograms of L levels plus a scratch level
-// for each of NT threads.
-__device__ __forceinline__ uint32_t hist_bins(int cpt, uint32_t L, uint32_t nt) {
-  return (cpt == 1 ? 1u : 3u) * (L + 1u) * nt;
-}
-
-template <int NT, int CPT, int VAR>
+template <int NT, int VAR>
 __global__ void __launch_bounds__(NT, 1)
     tile_plain_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d, const RingCfg rc,
                       uint32_t *err, uint64_t timeout_ns) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const SmemMap sm = carve_smem(smem, rc, hist_bins(CPT, d.L, NT));
+  const SmemMap sm = carve_smem(smem, rc, (d.L + 1u) * NT);
   init_cta(sm, rc);
   uint32_t ctr = 0;
-  const int x0 = static_cast<int>(blockIdx.x) * NT * CPT;
+  const int x0 = static_cast<int>(blockIdx.x) * NT;
   const int y0 = static_cast<int>(blockIdx.y * d.tile_h);
   const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
-  run_tile<NT, CPT, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+  run_tile<NT, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
-template <int NT, int CPT>
+template <int NT, int K>
+__global__ void __launch_bounds__(NT, 1)
+    tile_delta_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d, const RingCfg rc,
+                      uint32_t *err, uint64_t timeout_ns) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const SmemMap sm = carve_smem(smem, rc, K * (d.L + 1u) * NT);
+  init_cta(sm, rc);
+  uint32_t ctr = 0;
+  const int x0 = d.xshift + static_cast<int>(blockIdx.x) * NT * K;
+  const int y0 = static_cast<int>(blockIdx.y * d.tile_h);
+  const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
+  run_tile_delta<NT, K>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+}
+
+// K = 1: every image on the one-column path; K = 2 or 4: images with
+// d.kcols == K on the difference-histogram path, the others on the
+// one-column path.  Shared memory is sized by the host for the largest.
+template <int NT, int K>
 __global__ void __launch_bounds__(NT, 1)
     persistent_kernel(const ImgDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
                       const uint32_t *__restrict__ d_n, uint32_t *queue, const RingCfg rc,
                       uint32_t lmax, uint32_t *err, uint64_t timeout_ns) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_job[2];
-  const SmemMap sm = carve_smem(smem, rc, hist_bins(CPT, lmax, NT));
+  const SmemMap sm = carve_smem(smem, rc, (lmax + 1u) * NT);
   init_cta(sm, rc);
   const uint32_t n = __ldg(d_n);
   if (n == 0) return;
   const uint32_t total = __ldg(tile_prefix + n);
   uint32_t ctr = 0;
+  // the batch's control block keeps a timeout diagnostic record 8 words
+  // after the error word
+  uint32_t *diag = err + 7;
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t ticket = atomicAdd(queue, 1u);
@@ -94,20 +111,23 @@ __global__ void __launch_bounds__(NT, 1)
     const uint32_t img = s_job[0], local = s_job[1];
     if (img == 0xFFFFFFFFu) break;
     const ImgDesc d = descs[img];
-    // this image's histograms are laid out for its own L inside the region
-    SmemMap smi = sm;
-    smi.cnts = sm.sums + hist_bins(CPT, d.L, NT) * 8u;
-    const int x0 = static_cast<int>(local % d.tiles_x) * NT * CPT;
+    const int tw = NT * static_cast<int>(d.kcols);
+    const int x0 = d.xshift + static_cast<int>(local % d.tiles_x) * tw;
     const int y0 = static_cast<int>((local / d.tiles_x) * d.tile_h);
     const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
-    // the batch's control block keeps a timeout diagnostic record 8 words
-    // after the error word
-    uint32_t *diag = err + 7;
-    const bool ok = d.variant == kVarA
-                        ? run_tile<NT, CPT, kVarA>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
-                                                   timeout_ns, diag, true)
-                        : run_tile<NT, CPT, kVarB>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
-                                                   timeout_ns, diag, true);
+    bool ok;
+    if (K > 1 && d.kcols == static_cast<uint32_t>(K)) {
+      ok = run_tile_delta<NT, (K > 1 ? K : 2)>(d, d.tmap, x0, y0, y1, rc, sm, ctr, err,
+                                               timeout_ns, diag, true);
+    } else {
+      // this image's counts follow its own L + 1 levels of sums
+      SmemMap smi = sm;
+      smi.cnts = sm.sums + (d.L + 1u) * NT * 8u;
+      ok = d.variant == kVarA ? run_tile<NT, kVarA>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
+                                                    timeout_ns, diag, true)
+                              : run_tile<NT, kVarB>(d, d.tmap, x0, y0, y1, rc, smi, ctr, err,
+                                                    timeout_ns, diag, true);
+    }
     if (!ok) break;
   }
 }
@@ -138,44 +158,59 @@ cudaError_t launch_pack_batch(const ImgDesc *d_descs, const uint32_t *d_row_pref
   return cudaGetLastError();
 }
 
-template <int NT, int CPT>
-static void plain_nc(int variant, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
-                     dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+template <int NT>
+static void plain_n(int variant, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
+                    dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
   if (variant == kVarA)
-    tile_plain_kernel<NT, CPT, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+    tile_plain_kernel<NT, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
   else
-    tile_plain_kernel<NT, CPT, kVarB><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+    tile_plain_kernel<NT, kVarB><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
 }
 
 template <int NT>
-static void plain_n(int cpt, int variant, const ImgDesc &d, const CUtensorMap &map,
-                    const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
-                    uint64_t timeout_ns, cudaStream_t s) {
-  if (cpt == 2)
-    plain_nc<NT, 2>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
+static void delta_n(int k, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
+                    dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  if (k == 4)
+    tile_delta_kernel<NT, 4><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
   else
-    plain_nc<NT, 1>(variant, d, map, rc, grid, smem, err, timeout_ns, s);
+    tile_delta_kernel<NT, 2><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
 }
 
-cudaError_t launch_tile_plain(uint32_t nt, int cpt, int variant, const ImgDesc &d,
-                              const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
-                              uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
+                        const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
+                        uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
   switch (nt) {
-    case 32: plain_n<32>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
-    case 64: plain_n<64>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
-    case 96: plain_n<96>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
-    case 128: plain_n<128>(cpt, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+    case 32:
+      kcols == 1 ? plain_n<32>(variant, d, map, rc, grid, smem, err, timeout_ns, s)
+                 : delta_n<32>(kcols, d, map, rc, grid, smem, err, timeout_ns, s);
+      break;
+    case 64:
+      kcols == 1 ? plain_n<64>(variant, d, map, rc, grid, smem, err, timeout_ns, s)
+                 : delta_n<64>(kcols, d, map, rc, grid, smem, err, timeout_ns, s);
+      break;
+    case 96:
+      kcols == 1 ? plain_n<96>(variant, d, map, rc, grid, smem, err, timeout_ns, s)
+                 : delta_n<96>(kcols, d, map, rc, grid, smem, err, timeout_ns, s);
+      break;
+    case 128:
+      kcols == 1 ? plain_n<128>(variant, d, map, rc, grid, smem, err, timeout_ns, s)
+                 : delta_n<128>(kcols, d, map, rc, grid, smem, err, timeout_ns, s);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template <int NT>
-static void persistent_n(int cpt, const ImgDesc *d_descs, const uint32_t *d_tile_prefix,
+static void persistent_n(int k, const ImgDesc *d_descs, const uint32_t *d_tile_prefix,
                          const uint32_t *d_n, uint32_t *d_queue, const RingCfg &rc,
                          uint32_t lmax, int grid, size_t smem, uint32_t *err,
                          uint64_t timeout_ns, cudaStream_t s) {
-  if (cpt == 2)
+  if (k == 4)
+    persistent_kernel<NT, 4><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
+                                                    lmax, err, timeout_ns);
+  else if (k == 2)
     persistent_kernel<NT, 2><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
                                                     lmax, err, timeout_ns);
   else
@@ -183,25 +218,26 @@ static void persistent_n(int cpt, const ImgDesc *d_descs, const uint32_t *d_tile
                                                     lmax, err, timeout_ns);
 }
 
-cudaError_t launch_persistent(uint32_t nt, int cpt, const ImgDesc *d_descs,
+cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
                               const uint32_t *d_tile_prefix, const uint32_t *d_n,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
   switch (nt) {
     case 32:
-      persistent_n<32>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<32>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
                        timeout_ns, s);
       break;
     case 64:
-      persistent_n<64>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<64>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
                        timeout_ns, s);
       break;
     case 96:
-      persistent_n<96>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<96>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
                        timeout_ns, s);
       break;
     case 128:
-      persistent_n<128>(cpt, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<128>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
                         timeout_ns, s);
       break;
     default: return cudaErrorInvalidValue;
@@ -214,19 +250,17 @@ cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStrea
   return cudaGetLastError();
 }
 
-template <int NT, int CPT>
-static cudaError_t set_limit_nc(int b) {
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, CPT, kVarA>, a, b)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, CPT, kVarB>, a, b)) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(persistent_kernel<NT, CPT>, a, b);
-}
-
 template <int NT>
 static cudaError_t set_limit_n(int b) {
-  const cudaError_t e = set_limit_nc<NT, 1>(b);
-  return e != cudaSuccess ? e : set_limit_nc<NT, 2>(b);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, kVarA>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, kVarB>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 2>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 1>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 2>, a, b)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(persistent_kernel<NT, 4>, a, b);
 }
 
 cudaError_t set_tile_smem_limit(size_t bytes) {
@@ -238,32 +272,31 @@ cudaError_t set_tile_smem_limit(size_t bytes) {
   return set_limit_n<128>(b);
 }
 
-template <int NT, int CPT>
-static int occupancy_nc(int variant, size_t smem) {
+template <class F>
+static int occ_of(F f, int nt, size_t smem) {
   int n = 0;
-  cudaError_t e;
-  if (variant == kVarA)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tile_plain_kernel<NT, CPT, kVarA>, NT,
-                                                      smem);
-  else if (variant == kVarB)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tile_plain_kernel<NT, CPT, kVarB>, NT,
-                                                      smem);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<NT, CPT>, NT, smem);
-  return e == cudaSuccess ? n : 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, nt, smem) == cudaSuccess ? n : 0;
 }
 
 template <int NT>
-static int occupancy_n(int cpt, int variant, size_t smem) {
-  return cpt == 2 ? occupancy_nc<NT, 2>(variant, smem) : occupancy_nc<NT, 1>(variant, smem);
+static int occupancy_n(bool persistent, int kcols, int variant, size_t smem) {
+  if (persistent) {
+    if (kcols == 4) return occ_of(persistent_kernel<NT, 4>, NT, smem);
+    if (kcols == 2) return occ_of(persistent_kernel<NT, 2>, NT, smem);
+    return occ_of(persistent_kernel<NT, 1>, NT, smem);
+  }
+  if (kcols == 4) return occ_of(tile_delta_kernel<NT, 4>, NT, smem);
+  if (kcols == 2) return occ_of(tile_delta_kernel<NT, 2>, NT, smem);
+  return variant == kVarA ? occ_of(tile_plain_kernel<NT, kVarA>, NT, smem)
+                          : occ_of(tile_plain_kernel<NT, kVarB>, NT, smem);
 }
 
-int tile_occupancy(uint32_t nt, int cpt, int variant, size_t smem) {
+int tile_occupancy(uint32_t nt, bool persistent, int kcols, int variant, size_t smem) {
   switch (nt) {
-    case 32: return occupancy_n<32>(cpt, variant, smem);
-    case 64: return occupancy_n<64>(cpt, variant, smem);
-    case 96: return occupancy_n<96>(cpt, variant, smem);
-    case 128: return occupancy_n<128>(cpt, variant, smem);
+    case 32: return occupancy_n<32>(persistent, kcols, variant, smem);
+    case 64: return occupancy_n<64>(persistent, kcols, variant, smem);
+    case 96: return occupancy_n<96>(persistent, kcols, variant, smem);
+    case 128: return occupancy_n<128>(persistent, kcols, variant, smem);
     default: return 0;
   }
 }

@@ -125,12 +125,14 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return OP_E_CUDA;
 
-  const int cpt = cfg.cols_per_thread == 2 ? 2 : 1;
-  const uint32_t nt = cfg.tile_w / static_cast<uint32_t>(cpt);
-  const int variant = opk::variant_for_radius(radius);
-  const uint32_t boxw = opk::box_width(cfg.tile_w, radius);
+  const int cpt = (cfg.cols_per_thread == 2 || cfg.cols_per_thread == 4)
+                      ? static_cast<int>(cfg.cols_per_thread)
+                      : 1;
+  const opk::Geometry g = opk::image_geometry(cfg.tile_w / static_cast<uint32_t>(cpt), cpt,
+                                              radius, levels, width);
+  const uint32_t boxw = g.boxw;
   const opk::RingCfg rc = opk::make_ring(radius, cfg.chunk_rows, cfg.prefetch, boxw);
-  const size_t smem = opk::tile_smem_bytes(nt, cpt, levels, variant, rc);
+  const size_t smem = opk::tile_smem_bytes(opk::hist_bytes(g.nt, g.kcols, levels, g.variant), rc);
 
   opk::ImgDesc d{};
   d.in = d_in;
@@ -146,15 +148,17 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   d.L = levels;
   d.mode = flags;
   d.ppitch = ppitch;
-  d.tiles_x = (width + cfg.tile_w - 1) / cfg.tile_w;
+  d.tiles_x = g.tiles_x;
   if (cfg.tile_h) {
     d.tile_h = std::min(cfg.tile_h, height);
   } else {
-    const int occ = std::max(1, opk::tile_occupancy(nt, cpt, variant, smem));
+    const int occ = std::max(1, opk::tile_occupancy(g.nt, false, g.kcols, g.variant, smem));
     d.tile_h = pick_tile_h(height, d.tiles_x, radius, static_cast<uint64_t>(occ) * sms);
   }
   d.boxw = boxw;
-  d.variant = static_cast<uint32_t>(variant);
+  d.variant = static_cast<uint32_t>(g.variant);
+  d.kcols = static_cast<uint32_t>(g.kcols);
+  d.xshift = g.xshift;
 
   auto fn = encode_fn();
   if (!fn) return OP_E_CUDA;
@@ -173,8 +177,8 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   const int pack_grid = static_cast<int>(std::min<uint32_t>(height, 8u * static_cast<uint32_t>(sms)));
   if (opk::launch_pack_single(d, pack_grid, s) != cudaSuccess) return OP_E_CUDA;
   const dim3 grid(d.tiles_x, (height + d.tile_h - 1) / d.tile_h);
-  if (opk::launch_tile_plain(nt, cpt, variant, d, map, rc, grid, smem, sc.err, kWaitTimeoutNs,
-                             s) != cudaSuccess)
+  if (opk::launch_tile(g.nt, g.kcols, g.variant, d, map, rc, grid, smem, sc.err, kWaitTimeoutNs,
+                       s) != cudaSuccess)
     return OP_E_CUDA;
   uint32_t err = 0;
   if (cudaMemcpyAsync(&err, sc.err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -103,7 +103,9 @@ def test_mixed_batch_eager_and_graph():
 @pytest.mark.parametrize("cfg", [None,
                                  {"tile_w": 64, "chunk_rows": 4, "prefetch": 2},
                                  {"tile_w": 128, "chunk_rows": 16, "prefetch": 1,
-                                  "cols_per_thread": 2}])
+                                  "cols_per_thread": 2},
+                                 {"tile_w": 128, "chunk_rows": 8, "prefetch": 2,
+                                  "cols_per_thread": 4}])
 def test_batch_equals_solo_runs(cfg):
     images = make_images(12, seed=3, max_r=20, levels=(16, 20, 32))
     descs = to_device(images)

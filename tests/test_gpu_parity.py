@@ -130,7 +130,7 @@ def _fuzz_cases(n=48, seed=7):
         pad = int(rng.choice([0, 1, 4, 13]))
         mode = int(rng.integers(0, 2))
         nt = int(rng.choice([32, 64, 96, 128]))
-        cpt = int(rng.choice([1, 2]))
+        cpt = int(rng.choice([1, 2, 4]))
         cfg = {"tile_w": nt * cpt, "tile_h": int(rng.choice([0, 1, 5, 16, 64])),
                "chunk_rows": int(rng.choice([1, 2, 3, 8, 16, 32])),
                "prefetch": int(rng.integers(1, 5)), "cols_per_thread": cpt}
@@ -147,6 +147,47 @@ def test_fuzz(k, w, h, r, L, bpp, pad, mode, cfg):
     except B.OilPaintError as e:
         # the only acceptable refusal: a tile too wide for the radius or shared memory
         assert e.status == B.OP_E_UNSUPPORTED, e
+
+
+def _delta_fuzz_cases(n=40, seed=11):
+    """Cases the difference-histogram path takes (r <= 15, L <= 32, 2 or 4
+    columns per thread): every r mod 4 (the tile's x shift), widths around
+    the tile width, one-column and one-row images."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n):
+        w = int(rng.choice([1, 2, 3, 4, 5, 7, 31, 61, 64, 67, 127, 128, 131, 190, 256, 259, 400]))
+        h = int(rng.choice([1, 2, 3, 9, 16, 33, 100, 211]))
+        r = int(rng.integers(0, 16))
+        L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32]))
+        bpp = int(rng.choice([3, 4]))
+        pad = int(rng.choice([0, 1, 4, 13]))
+        mode = int(rng.integers(0, 2))
+        cpt = int(rng.choice([2, 4]))
+        nt = int(rng.choice([32, 64] if cpt == 4 else [32, 64, 96, 128]))
+        cfg = {"tile_w": nt * cpt, "tile_h": int(rng.choice([0, 1, 3, 16, 64])),
+               "chunk_rows": int(rng.choice([1, 2, 3, 8, 16, 32])),
+               "prefetch": int(rng.integers(1, 5)), "cols_per_thread": cpt}
+        cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
+    return cases
+
+
+@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _delta_fuzz_cases())
+def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
+    img = synth.camera_like(h, w, seed=900 + k, npoly=12, rad_range=(1, 60)) if k % 2 else \
+        synth.uniform_rgb(h, w, seed=900 + k)
+    try:
+        check_case(img, r, L, bpp, pad, mode, cfg)
+    except B.OilPaintError as e:
+        # refused only when the halo box is wider than 256 columns or the
+        # ring of halo copies plus K histograms exceeds a CTA's shared memory
+        assert e.status == B.OP_E_UNSUPPORTED, e
+        K, nt = cfg["cols_per_thread"], cfg["tile_w"] // cfg["cols_per_thread"]
+        ng = (2 * r + K - 1) // K + 1
+        boxw = -(-K * (nt - 1 + ng) // 4) * 4
+        half = -(-boxw * cfg["chunk_rows"] * 4 // 128) * 128
+        smem = 2 * half * (cfg["prefetch"] + 1) + K * (L + 1) * nt * 8 + 4096 + 256
+        assert boxw > 256 or smem > 200 * 1024, (cfg, r, L)
 
 
 # ---- edge cases --------------------------------------------------------------
@@ -174,27 +215,35 @@ def test_every_config_gives_the_same_bytes():
     h, w = img.shape[:2]
     buf, stride = synth.to_strided(img, bpp=3, stride=w * 3 + 2)
     want = cpu_filter(buf, w, h, stride, 3, 9, 20)
+    ran = 0
     for nt in (32, 64, 96, 128):
-        for cpt in (1, 2):
+        for cpt in (1, 2, 4):
             for ch in (1, 4, 8, 16):
                 for pf in (1, 2, 4):
                     for th in (0, 1, 23, 233):
                         cfg = {"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch,
                                "prefetch": pf, "cols_per_thread": cpt}
-                        if nt * cpt + 2 * 9 + 3 > 256:
-                            continue  # halo wider than one TMA box: refused by the library
-                        got = gpu_filter(buf, w, h, stride, 3, 9, 20, config=cfg)
+                        try:
+                            got = gpu_filter(buf, w, h, stride, 3, 9, 20, config=cfg)
+                        except B.OilPaintError as e:
+                            # halo wider than one TMA box
+                            assert e.status == B.OP_E_UNSUPPORTED, e
+                            continue
                         assert_same(got, want, w, h, stride, 3, str(cfg))
+                        ran += 1
+    # r = 9: boxes of 32..96 threads x 1, 32..96 x 2 and 32 x 4 columns fit
+    assert ran == (4 + 3 + 1) * 4 * 3 * 4
 
 
-@pytest.mark.parametrize("cpt", [1, 2])
-@pytest.mark.parametrize("r,L", [(0, 20), (1, 7), (2, 20), (14, 20), (15, 20), (16, 20),
-                                 (20, 32), (15, 256), (44, 64), (13, 3)])
+@pytest.mark.parametrize("cpt", [1, 2, 4])
+@pytest.mark.parametrize("r,L", [(0, 20), (1, 7), (2, 20), (3, 32), (14, 20), (15, 20),
+                                 (16, 20), (20, 32), (15, 256), (44, 64), (13, 3), (15, 33)])
 def test_columns_per_thread_both_variants(cpt, r, L):
-    """Both histogram variants and both column-per-thread layouts, with odd
-    and even halo offsets (r mod 4), on images whose width is not a tile
-    multiple.  Configurations the library refuses (shared memory) are
-    skipped; at least one must run."""
+    """Both histogram variants, one column per thread and both difference-
+    histogram widths, with every halo offset (r mod 4), on images whose
+    width is not a tile multiple.  Two or four columns per thread are
+    refused exactly when r > 15 or L > 32; with one column per thread,
+    configurations beyond shared memory are skipped and one must run."""
     img = synth.camera_like(190, 270, seed=r * L + 1, npoly=25, rad_range=(3, 100))
     ran = 0
     for bpp, pad, nt, ch in ((4, 4, 64, 8), (3, 1, 32, 3)):
@@ -204,15 +253,21 @@ def test_columns_per_thread_both_variants(cpt, r, L):
             ran += 1
         except B.OilPaintError as e:
             assert e.status == B.OP_E_UNSUPPORTED, e
-    assert ran
+    if cpt > 1 and (r > 15 or L > 32):
+        assert ran == 0
+    elif cpt == 4:
+        assert ran >= 1  # 64 threads x 4 columns: a 256+ box at r >= 1
+    else:
+        assert ran == 2 or cpt == 1 and ran >= 1
 
 
 @pytest.mark.parametrize("w,h,r,L", [(300, 40, 15, 20), (301, 41, 14, 20), (97, 50, 13, 16)])
-def test_border_threads_two_columns(w, h, r, L):
-    """Images narrower than two tiles: most threads clip their windows."""
+def test_border_threads_several_columns(w, h, r, L):
+    """Images narrower than two tiles: most windows reach past an image
+    edge into the zero words of the halo copy."""
     img = synth.uniform_rgb(h, w, seed=w + r)
-    for nt in (32, 64):
-        check_case(img, r, L, bpp=3, config={"tile_w": 2 * nt, "cols_per_thread": 2})
+    for nt, k in ((32, 2), (64, 2), (32, 4)):
+        check_case(img, r, L, bpp=3, config={"tile_w": k * nt, "cols_per_thread": k})
 
 
 def test_tile_w_256_only_without_halo():
