@@ -288,9 +288,12 @@ def run_ours(args):
             tr = json.load(f)
         if tr.get("workload") == WORKLOAD and tr.get("kernel_source_hash") == _kernel_hash():
             traffic = tr.get("bytes_per_launch")
+    launch = op.config()
+    kernel = ("tile_delta_kernel" if launch["cols_per_thread"] > 1 and RADIUS <= 15 and LEVELS <= 32
+              else "tile_plain_kernel")
     roofline = {"bound": "alu", "achieved": round(ach_tops, 3), "peak": round(peak_tops, 3),
                 "unit": "Tops/s", "frac": round(ach_tops / peak_tops, 4), "traffic": traffic,
-                "kernel": "tile_plain_kernel", "kernel_ms": round(f_ms, 4),
+                "kernel": kernel, "kernel_ms": round(f_ms, 4),
                 "pack_ms": round(statistics.mean(pack_ms), 4),
                 "ops_per_pixel": ops_per_pixel(RADIUS, LEVELS),
                 "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz"}

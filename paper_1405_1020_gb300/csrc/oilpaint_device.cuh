@@ -226,6 +226,51 @@ __device__ __forceinline__ void bin_addsub64(uint32_t addr_a, uint32_t alo, uint
       "r"(alo), "r"(ahi), "r"(addr_b), "r"(blo), "r"(bhi));
 }
 
+// Two 64-bit additions issued together (addr_a != addr_b).
+__device__ __forceinline__ void bin_add64x2(uint32_t addr_a, uint32_t alo, uint32_t ahi,
+                                            uint32_t addr_b, uint32_t blo, uint32_t bhi) {
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
+      "add.cc.u32 a0, a0, %1;\n\t"
+      "addc.u32 a1, a1, %2;\n\t"
+      "add.cc.u32 b0, b0, %4;\n\t"
+      "addc.u32 b1, b1, %5;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(addr_a),
+      "r"(alo), "r"(ahi), "r"(addr_b), "r"(blo), "r"(bhi));
+}
+
+// Two bin_addsub64 issued together: +a at A, -b at B, +c at C, -d at D, all
+// four loads before any add.  A, B, C, D are distinct, except that B and D
+// may both be the scratch bin, whose contents are never read.
+__device__ __forceinline__ void bin_addsub64x2(uint32_t A, uint32_t alo, uint32_t ahi, uint32_t B,
+                                               uint32_t blo, uint32_t bhi, uint32_t C,
+                                               uint32_t clo, uint32_t chi, uint32_t D,
+                                               uint32_t dlo, uint32_t dhi) {
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
+      "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"
+      "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"
+      "add.cc.u32 a0, a0, %1;\n\t"
+      "addc.u32 a1, a1, %2;\n\t"
+      "sub.cc.u32 b0, b0, %4;\n\t"
+      "subc.u32 b1, b1, %5;\n\t"
+      "add.cc.u32 c0, c0, %7;\n\t"
+      "addc.u32 c1, c1, %8;\n\t"
+      "sub.cc.u32 d0, d0, %10;\n\t"
+      "subc.u32 d1, d1, %11;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.v2.u32 [%3], {b0, b1};\n\t"
+      "st.shared.v2.u32 [%6], {c0, c1};\n\t"
+      "st.shared.v2.u32 [%9], {d0, d1};\n\t}" ::"r"(A),
+      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi), "r"(D),
+      "r"(dlo), "r"(dhi));
+}
+
 // The same for two 32-bit counts: +da at addr_a, -db at addr_b.
 __device__ __forceinline__ void cnt_addsub(uint32_t addr_a, uint32_t da, uint32_t addr_b,
                                            uint32_t db) {
@@ -431,39 +476,93 @@ __device__ __forceinline__ void dh_sub(uint32_t base, uint32_t w) {
   bin_sub64(dh_addr<NT>(base, w), lo, hi);
 }
 
-// +win -wout as one two-deep update (same-level pairs fold into one delta,
-// the other half goes to the scratch bin at base + scratch_off).
+// Delta of +win - wout at histogram `base`: the bin of win gets (alo, ahi)
+// added and the bin ab gets (blo, bhi) subtracted.  When both words have the
+// same level the two fold into one delta and ab becomes the scratch bin.
 template <int NT>
-__device__ __forceinline__ void dh_addsub(uint32_t base, uint32_t win, uint32_t wout,
-                                          uint32_t scratch_off) {
-  uint32_t alo, ahi, blo, bhi;
+__device__ __forceinline__ void dh_pair(uint32_t base, uint32_t win, uint32_t wout,
+                                        uint32_t scratch, uint32_t &aa, uint32_t &alo,
+                                        uint32_t &ahi, uint32_t &ab, uint32_t &blo,
+                                        uint32_t &bhi) {
   dh_delta(win, alo, ahi);
   dh_delta(wout, blo, bhi);
-  const uint32_t aa = dh_addr<NT>(base, win);
-  uint32_t ab = dh_addr<NT>(base, wout);
+  aa = dh_addr<NT>(base, win);
+  ab = dh_addr<NT>(base, wout);
   if (aa == ab) {
     const uint64_t net =
         (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
     alo = static_cast<uint32_t>(net);
     ahi = static_cast<uint32_t>(net >> 32);
-    ab = base + scratch_off;
+    ab = scratch;
   }
+}
+
+// +win -wout in one histogram as one two-deep update.
+template <int NT>
+__device__ __forceinline__ void dh_addsub(uint32_t base, uint32_t win, uint32_t wout,
+                                          uint32_t scratch) {
+  uint32_t aa, alo, ahi, ab, blo, bhi;
+  dh_pair<NT>(base, win, wout, scratch, aa, alo, ahi, ab, blo, bhi);
   bin_addsub64(aa, alo, ahi, ab, blo, bhi);
+}
+
+// +win_p -wout_p in histogram p and +win_q -wout_q in histogram q != p as
+// one four-deep update.
+template <int NT>
+__device__ __forceinline__ void dh_addsub_x2(uint32_t p, uint32_t win_p, uint32_t wout_p,
+                                             uint32_t q, uint32_t win_q, uint32_t wout_q,
+                                             uint32_t scratch) {
+  uint32_t A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi;
+  dh_pair<NT>(p, win_p, wout_p, scratch, A, alo, ahi, B, blo, bhi);
+  dh_pair<NT>(q, win_q, wout_q, scratch, C, clo, chi, D, dlo, dhi);
+  bin_addsub64x2(A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi);
+}
+
+// Signed additions of single words to two histograms p != q: (+/-)wp at p,
+// (+/-)wq at q.
+template <int NT, bool NEG_P, bool NEG_Q>
+__device__ __forceinline__ void dh_pm_x2(uint32_t p, uint32_t wp, uint32_t q, uint32_t wq) {
+  uint32_t plo, phi, qlo, qhi;
+  dh_delta(wp, plo, phi);
+  dh_delta(wq, qlo, qhi);
+  if (NEG_P) {
+    const uint64_t v = 0ull - (static_cast<uint64_t>(phi) << 32 | plo);
+    plo = static_cast<uint32_t>(v);
+    phi = static_cast<uint32_t>(v >> 32);
+  }
+  if (NEG_Q) {
+    const uint64_t v = 0ull - (static_cast<uint64_t>(qhi) << 32 | qlo);
+    qlo = static_cast<uint32_t>(v);
+    qhi = static_cast<uint32_t>(v >> 32);
+  }
+  bin_add64x2(dh_addr<NT>(p, wp), plo, phi, dh_addr<NT>(q, wq), qlo, qhi);
 }
 
 // ------------------------------------------------------------ division
 
 // Truncating n / d for the channel means.  r <= 15 (n < 2^18, d <= 961):
-// Granlund and Montgomery's multiply-high by m = ceil(2^31 / d) from a
-// per-CTA table, q = floor(2n * m / 2^32); with e = m*d - 2^31 < d the error
-// term n*e / 2^31 stays below 2^28 / 2^31 < 1, so q is exact.  Larger radii
-// use integer division.
+// Granlund and Montgomery's multiply-high by m = ceil(2^31 / d), looked up
+// in a table built at compile time, q = floor(2n * m / 2^32); with
+// e = m*d - 2^31 < d the error term n*e / 2^31 stays below 2^28 / 2^31 < 1,
+// so q is exact.  Larger radii use integer division.  The table lives in
+// global memory (read through the L1 cache) rather than in each CTA's
+// shared memory, which the histograms need.
 constexpr uint32_t kRcpEntries = 962;  // d = 0..961 (entry 0 unused)
 
-__device__ __forceinline__ void fill_rcp_table(uint32_t *rcp) {
-  for (uint32_t d = threadIdx.x; d < kRcpEntries; d += blockDim.x)
-    rcp[d] = d ? static_cast<uint32_t>(((1ull << 31) + d - 1u) / d) : 0u;
+struct RcpTable {
+  uint32_t m[kRcpEntries];
+};
+
+constexpr RcpTable make_rcp_table() {
+  RcpTable t{};
+  for (uint32_t d = 1; d < kRcpEntries; ++d)
+    t.m[d] = static_cast<uint32_t>(((1ull << 31) + d - 1u) / d);
+  return t;
 }
+
+__device__ const RcpTable g_rcp = make_rcp_table();
+
+__device__ __forceinline__ uint32_t rcp_of(uint32_t d) { return __ldg(&g_rcp.m[d]); }
 
 template <int VAR>
 __device__ __forceinline__ uint32_t div_mean(uint32_t n, uint32_t d, uint32_t m) {
@@ -478,14 +577,10 @@ __device__ __forceinline__ uint32_t div_mean(uint32_t n, uint32_t d, uint32_t m)
 struct SmemMap {
   uint32_t bars;  // nslot mbarriers
   uint32_t ring;  // nslot * slot_bytes
-  uint32_t rcp;   // kRcpEntries reciprocals
   uint32_t sums;  // histogram bins
   uint32_t cnts;  // variant B counts
   uint8_t *ring_ptr;
-  uint32_t *rcp_ptr;
 };
-
-constexpr uint32_t kRcpBytes = (kRcpEntries * 4u + 127u) & ~127u;
 
 __device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc,
                                               uint32_t nhist_bins) {
@@ -494,11 +589,9 @@ __device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc,
   const uint32_t a = (base + 127u) & ~127u;
   s.bars = a;
   s.ring = a + ((rc.nslot * 8u + 127u) & ~127u);
-  s.rcp = s.ring + rc.nslot * rc.slot_bytes;
-  s.sums = s.rcp + kRcpBytes;
+  s.sums = s.ring + rc.nslot * rc.slot_bytes;
   s.cnts = s.sums + nhist_bins * 8u;
   s.ring_ptr = smem + (s.ring - base);
-  s.rcp_ptr = reinterpret_cast<uint32_t *>(smem + (s.rcp - base));
   return s;
 }
 
@@ -647,7 +740,6 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
   const int jl = cl - xs;  // ring index of column cl (>= 0)
   const int E0 = y0 - r;
   const int nsteps = (y1 - y0) + 2 * r;
-  const uint32_t *rcp = sm.rcp_ptr;
   const int j0 = interior ? 0 : max(cl, 0) - cl;
   const int j1 = interior ? 2 * r + 1 : (active ? min(cr, W - 1) - cl + 1 : 0);
 
@@ -697,7 +789,7 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
           uint32_t lo, hi, cnt, R, G, B;
           h.bin(m, lo, hi);
           unpack_bin<VAR>(lo, hi, VAR == kVarB ? best : 0u, cnt, R, G, B);
-          const uint32_t mul = VAR == kVarA ? rcp[cnt] : 0u;
+          const uint32_t mul = VAR == kVarA ? rcp_of(cnt) : 0u;
           store_pixel(d, xa, e - r, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
                       div_mean<VAR>(B, cnt, mul), alpha);
         }
@@ -720,9 +812,10 @@ struct VecOf<4> {
   }
 };
 
-// One step's updates of the K histograms of a difference-histogram thread
-// (see run_tile_delta) from the ring words 0 .. 2r+K-1 of its entering row pe
-// and, when RM, its leaving row pl.  Word j (image column xa - r + j) feeds
+// One step's updates of a difference-histogram thread with one window
+// histogram H at h0 and D_i at h0 + i*hstride (see run_tile_delta), from the
+// ring words 0 .. 2r+K-1 of its entering row pe and, when RM, its leaving
+// row pl.  Word j (image column xa - r + j) feeds
 //   the window histogram H when j <= 2r,
 //   D_{j+1} negatively (its left column leaves) when j <= K-2,
 //   D_{j-2r} positively (its right column) when j >= 2r+1.
@@ -730,19 +823,19 @@ struct VecOf<4> {
 // skip the tests.
 template <int NT, int K, bool RM>
 __device__ __forceinline__ void delta_step(const uint32_t *pe, const uint32_t *pl, int r,
-                                           uint32_t h0, uint32_t hstride, uint32_t scratch_off) {
+                                           uint32_t h0, uint32_t hstride, uint32_t scratch) {
   using V = typename VecOf<K>::T;
   const int last = 2 * r + K - 1;
   const int ngroups = last / K + 1;
   auto upd = [&](uint32_t base, uint32_t e, uint32_t l) {
     if (RM)
-      dh_addsub<NT>(base, e, l, scratch_off);
+      dh_addsub<NT>(base, e, l, scratch);
     else
       dh_add<NT>(base, e);
   };
   auto updneg = [&](uint32_t base, uint32_t e, uint32_t l) {
     if (RM)
-      dh_addsub<NT>(base, l, e, scratch_off);
+      dh_addsub<NT>(base, l, e, scratch);
     else
       dh_sub<NT>(base, e);
   };
@@ -772,25 +865,124 @@ __device__ __forceinline__ void delta_step(const uint32_t *pe, const uint32_t *p
   }
 }
 
+// The same step with the window histogram split by word parity: H_even at
+// h0 (words 0, 2, .., 2r), H_odd at h0 + hstride (words 1, 3, .., 2r-1) and
+// D_i at h0 + (1+i)*hstride.  The two halves are independent, so each
+// update of an even word is issued together with one of an odd word (four
+// bins in flight instead of two); the last even word pairs with the first
+// D update and the D updates pair among themselves.
+template <int NT, int K, bool RM>
+__device__ __forceinline__ void delta_step_split(const uint32_t *pe, const uint32_t *pl, int r,
+                                                 uint32_t h0, uint32_t hstride,
+                                                 uint32_t scratch) {
+  using V = typename VecOf<K>::T;
+  const uint32_t hev = h0, hod = h0 + hstride;
+  auto dh = [&](int i) { return h0 + static_cast<uint32_t>(1 + i) * hstride; };
+  auto at = [](const V &v, int q) { return VecOf<K>::at(v, q); };
+  auto load = [&](const uint32_t *p) { return *reinterpret_cast<const V *>(p); };
+  // +e -l in histograms p and q (p != q)
+  auto both = [&](uint32_t p, uint32_t ep, uint32_t lp, uint32_t q, uint32_t eq, uint32_t lq) {
+    if (RM)
+      dh_addsub_x2<NT>(p, ep, lp, q, eq, lq, scratch);
+    else
+      dh_pm_x2<NT, false, false>(p, ep, q, eq);
+  };
+  // +e -l in histogram p and the column leaving D_i: +l -e in histogram q
+  auto with_leaving = [&](uint32_t p, uint32_t ep, uint32_t lp, uint32_t q, uint32_t eq,
+                          uint32_t lq) {
+    if (RM)
+      dh_addsub_x2<NT>(p, ep, lp, q, lq, eq, scratch);
+    else
+      dh_pm_x2<NT, false, true>(p, ep, q, eq);
+  };
+  const int nfull = (2 * r + 1) / K;  // groups made only of window words
+  const V a0 = load(pe);
+  V b0 = V{};
+  if (RM) b0 = load(pl);
+  int g = 0;
+  if (nfull > 0) {
+#pragma unroll
+    for (int q = 0; q < K; q += 2) both(hev, at(a0, q), at(b0, q), hod, at(a0, q + 1), at(b0, q + 1));
+    g = 1;
+  }
+#pragma unroll 2
+  for (; g < nfull; ++g) {
+    const V a = load(pe + g * K);
+    V b = V{};
+    if (RM) b = load(pl + g * K);
+#pragma unroll
+    for (int q = 0; q < K; q += 2) both(hev, at(a, q), at(b, q), hod, at(a, q + 1), at(b, q + 1));
+  }
+  // the c = 2r + 1 - nfull*K remaining window words (c odd, 1 <= c < K);
+  // the last is even and goes to H_even together with D_1's leaving word 0
+  V ta = a0, tb = b0;
+  if (nfull > 0) {
+    ta = load(pe + nfull * K);
+    if (RM) tb = load(pl + nfull * K);
+  }
+  uint32_t es = at(ta, 0), ls = at(tb, 0);
+  if (K == 4 && 2 * r + 1 - nfull * K == 3) {
+    both(hev, at(ta, 0), at(tb, 0), hod, at(ta, 1), at(tb, 1));
+    es = at(ta, 2);
+    ls = at(tb, 2);
+  }
+  with_leaving(hev, es, ls, dh(1), at(a0, 0), at(b0, 0));
+  const uint32_t *pe2 = pe + 2 * r + 1, *pl2 = pl + 2 * r + 1;
+  if (K == 2) {
+    const uint32_t e = pe2[0], l = RM ? pl2[0] : 0u;
+    if (RM)
+      dh_addsub<NT>(dh(1), e, l, scratch);
+    else
+      dh_add<NT>(dh(1), e);
+  } else {
+    // D_2, D_3 lose words 1, 2; D_1, D_2, D_3 gain words 2r+1, 2r+2, 2r+3
+    if (RM)
+      dh_addsub_x2<NT>(dh(2), at(b0, 1), at(a0, 1), dh(3), at(b0, 2), at(a0, 2), scratch);
+    else
+      dh_pm_x2<NT, true, true>(dh(2), at(a0, 1), dh(3), at(a0, 2));
+    const uint32_t e1 = pe2[0], e2 = pe2[1], e3 = pe2[2];
+    const uint32_t l1 = RM ? pl2[0] : 0u, l2 = RM ? pl2[1] : 0u, l3 = RM ? pl2[2] : 0u;
+    both(dh(1), e1, l1, dh(2), e2, l2);
+    if (RM)
+      dh_addsub<NT>(dh(3), e3, l3, scratch);
+    else
+      dh_add<NT>(dh(3), e3);
+  }
+}
+
+// Whether the K-column path splits the window histogram by column parity:
+// with four columns per thread the histograms already limit a CTA to few
+// resident warps, and the extra independent update chain pays for the
+// extra histogram; with two columns the extra histogram costs more
+// occupancy than the chain gains.
+constexpr bool kSplit2 = false;
+constexpr bool kSplit4 = true;
+__host__ __device__ constexpr bool split_for(int k) { return k == 4 ? kSplit4 : kSplit2; }
+
 // K output columns per thread through difference histograms (word format 1,
 // r <= 15, L <= 32).  Thread t owns columns xa .. xa+K-1 with xa = x0 + K*t;
 // x0 - r is a multiple of 4 (tiles start at d.xshift), so every thread's
 // window starts on a 16-byte boundary of the ring.  It keeps
-//   H    the histogram of the window of column xa (2r+1 columns),
+//   H    the histogram of the window of column xa (2r+1 columns; with SPLIT
+//        two histograms over its even and odd columns),
 //   D_i  (i = 1..K-1) the histogram of column xa+i+r minus that of column
 //        xa+i-1-r, so that the window histogram of column xa+i is
 //        H + D_1 + ... + D_i.
-// A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  The argmax runs
-// over the running sums of the histograms' low words, whose bottom 10 bits
-// are the counts; a key (count << 5) | (31 - level) makes the lowest level
-// win ties under max.  Pixels outside the image are TMA zero fill whose
-// delta is zero, so no thread clips its window.
-template <int NT, int K>
+// A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  Histograms are
+// L levels of NT 64-bit bins (level-major, thread-minor), followed by one
+// scratch bin per thread.  The argmax runs over the running sums of the
+// histograms' low words, whose bottom 10 bits are the counts; a key
+// (count << 22) | (31 - level) makes the lowest level win ties under max.
+// Pixels outside the image are TMA zero fill whose delta is zero, so no
+// thread clips its window.
+template <int NT, int K, bool SPLIT>
 __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0,
                                int y1, const RingCfg &rc, const SmemMap &sm,
                                uint32_t &chunk_ctr, uint32_t *err, uint64_t timeout_ns,
                                uint32_t *diag = nullptr, bool tmap_global = false) {
   static_assert(K == 2 || K == 4, "two or four columns per thread");
+  constexpr int NB = SPLIT ? 2 : 1;  // histograms making up H
+  constexpr int NH = NB + K - 1;
   const int t = threadIdx.x;
   const int r = d.r;
   const int W = static_cast<int>(d.w);
@@ -800,14 +992,14 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
   const int jl = K * t;
   const int E0 = y0 - r;
   const int nsteps = (y1 - y0) + 2 * r;
-  const uint32_t *rcp = sm.rcp_ptr;
-  const uint32_t lstride = NT * 8u;                 // between levels of one histogram
-  const uint32_t hstride = (L + 1u) * NT * 8u;      // between the K histograms
+  const uint32_t lstride = NT * 8u;    // between levels of one histogram
+  const uint32_t hstride = L * lstride;  // between histograms
   const uint32_t h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
-  const uint32_t scratch_off = L * lstride;
+  const uint32_t scratch = h0 + NH * hstride;
+  auto hist = [&](int i) { return h0 + static_cast<uint32_t>(i) * hstride; };
 #pragma unroll
-  for (int i = 0; i < K; ++i)
-    for (uint32_t lv = 0; lv < L; ++lv) sts_zero64(h0 + i * hstride + lv * lstride);
+  for (int i = 0; i < NH; ++i)
+    for (uint32_t lv = 0; lv < L; ++lv) sts_zero64(hist(i) + lv * lstride);
 
   return ring_pass(
       d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
@@ -823,22 +1015,30 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
           const int x = xa + i;
           alpha[i] = (out_now && d.bpp == 4 && x >= 0 && x < W) ? load_alpha(d, x, y) : 0u;
         }
-        if (rm)
-          delta_step<NT, K, true>(pe, pl, r, h0, hstride, scratch_off);
-        else
-          delta_step<NT, K, false>(pe, pl, r, h0, hstride, scratch_off);
+        if (SPLIT) {
+          if (rm)
+            delta_step_split<NT, K, true>(pe, pl, r, h0, hstride, scratch);
+          else
+            delta_step_split<NT, K, false>(pe, pl, r, h0, hstride, scratch);
+        } else {
+          if (rm)
+            delta_step<NT, K, true>(pe, pl, r, h0, hstride, scratch);
+          else
+            delta_step<NT, K, false>(pe, pl, r, h0, hstride, scratch);
+        }
         if (!out_now) return;
         uint32_t best[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) best[i] = 0u;
         for (uint32_t lv = 0; lv < L; ++lv) {
           const uint32_t tag = 31u - lv;
-          uint32_t acc = lds_u32(h0 + lv * lstride);
-          best[0] = max(best[0], ((acc << 5) & 0x7FE0u) | tag);
+          uint32_t acc = lds_u32(hist(0) + lv * lstride);
+          if (SPLIT) acc += lds_u32(hist(1) + lv * lstride);
+          best[0] = max(best[0], (acc << 22) | tag);
 #pragma unroll
           for (int i = 1; i < K; ++i) {
-            acc += lds_u32(h0 + i * hstride + lv * lstride);
-            best[i] = max(best[i], ((acc << 5) & 0x7FE0u) | tag);
+            acc += lds_u32(hist(NB - 1 + i) + lv * lstride);
+            best[i] = max(best[i], (acc << 22) | tag);
           }
         }
 #pragma unroll
@@ -846,34 +1046,32 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
           const int x = xa + i;
           if (x < 0 || x >= W) continue;
           const uint32_t m = 31u - (best[i] & 31u);
-          const uint32_t cnt = best[i] >> 5;
-          uint32_t lo, hi;
-          lds_v2(h0 + m * lstride, lo, hi);
-          uint64_t v = static_cast<uint64_t>(hi) << 32 | lo;
+          const uint32_t cnt = best[i] >> 22;
+          uint64_t v = 0;
 #pragma unroll
-          for (int j = 1; j <= i; ++j) {
-            lds_v2(h0 + j * hstride + m * lstride, lo, hi);
+          for (int j = 0; j < NB + i; ++j) {
+            uint32_t lo, hi;
+            lds_v2(hist(j) + m * lstride, lo, hi);
             v += static_cast<uint64_t>(hi) << 32 | lo;
           }
-          lo = static_cast<uint32_t>(v);
-          hi = static_cast<uint32_t>(v >> 32);
+          const uint32_t lo = static_cast<uint32_t>(v);
+          const uint32_t hi = static_cast<uint32_t>(v >> 32);
           const uint32_t R = (lo >> 10) & 0x3FFFFu;
           const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
           const uint32_t B = hi >> 14;
-          const uint32_t mul = rcp[cnt];
+          const uint32_t mul = rcp_of(cnt);
           store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul),
                       __umulhi(B << 1, mul), alpha[i]);
         }
       });
 }
 
-// Barrier init and the reciprocal table; ends with a CTA barrier.
+// Barrier init; ends with a CTA barrier.
 __device__ __forceinline__ void init_cta(const SmemMap &sm, const RingCfg &rc) {
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < rc.nslot; ++s) mbar_init(sm.bars + s * 8u, 1u);
     mbar_fence_init();
   }
-  fill_rcp_table(sm.rcp_ptr);
   __syncthreads();
 }
 

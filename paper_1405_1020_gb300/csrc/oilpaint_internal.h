@@ -88,10 +88,14 @@ inline Geometry image_geometry(uint32_t nt, int kcols_wanted, int r, uint32_t L,
 }
 
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
-// per thread, bins of the variant's size; 2 or 4: that many 64-bit
-// histograms of L + 1 levels per thread).
+// per thread, bins of the variant's size; 2 or 4: kcols histograms, one
+// more where the window histogram is split, of L 64-bit levels per thread,
+// plus one scratch bin).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
-  if (kcols > 1) return static_cast<size_t>(kcols) * (L + 1u) * nt * 8u;
+  if (kcols > 1) {
+    const size_t nh = static_cast<size_t>(kcols) + (split_for(kcols) ? 1u : 0u);
+    return (nh * L + 1u) * nt * 8u;
+  }
   return static_cast<size_t>(L + 1u) * nt * bin_bytes(variant);
 }
 
@@ -99,7 +103,7 @@ inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
 // bytes of alignment slack).
 inline size_t tile_smem_bytes(size_t hist, const RingCfg &rc) {
   return 128u + ((rc.nslot * 8u + 127u) & ~127u) + static_cast<size_t>(rc.nslot) * rc.slot_bytes +
-         kRcpBytes + hist;
+         hist;
 }
 
 // Launchers; each returns cudaSuccess or the launch error.
