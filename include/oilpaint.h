@@ -79,10 +79,9 @@ typedef struct op_s op_t;
  *                   leaving the window, so the window of column i is
  *                   H + D_1 + ... + D_i; 2(2r+1) + 4(K-1) bin updates per K
  *                   outputs instead of 2(2r+1) per output); 0 = 1.  2 and 4
- *                   need radius <= 15 and levels <= 32, else the
- *                   configuration is refused (OP_E_UNSUPPORTED) by
- *                   op_set_config; a batch runs its other images on the
- *                   one-column path.
+ *                   need levels <= 32, else the configuration is refused
+ *                   (OP_E_UNSUPPORTED) by op_set_config; a batch runs its
+ *                   other images on the one-column path.
  * The halo copy of a tile is at most 256 columns wide: tile_w + 2r + up to
  * 3 columns for one column per thread, K * (threads - 1 + ceil((2r+K-1)/K)
  * + 1) rounded up to 4 for K columns per thread.
@@ -201,9 +200,9 @@ typedef struct op_batch_s op_batch_t;
  * launch: each CTA takes (image, tile) tickets from a device-side atomic
  * counter until the queue is empty.  cfg: tile_w, chunk_rows, prefetch and
  * cols_per_thread of that launch (NULL = defaults; tile_h is chosen per
- * image); with 2 or 4 columns per thread, images of radius <= 15 and
- * <= 32 levels take the difference-histogram path and the others one
- * column per thread with tile_w / cols_per_thread threads.  Returns NULL
+ * image); with 2 or 4 columns per thread, images of <= 32 levels take the
+ * difference-histogram path and the others one column per thread with
+ * tile_w / cols_per_thread threads.  Returns NULL
  * with op_last_error() on failure.
  */
 op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t max_radius,

@@ -147,6 +147,8 @@ BatchNeeds batch_needs(const op_config_t &c, int max_r, uint32_t max_L) {
     const int rd = std::min(max_r, static_cast<int>(opk::kDeltaMaxRadius));
     const uint32_t Ld = std::min(max_L, static_cast<uint32_t>(opk::kDeltaMaxLevels));
     n.boxw = std::max(n.boxw, opk::delta_box_width(nt, k, rd));
+    // the largest delta histogram over the radii a batch may hold
+    n.hist = std::max(n.hist, opk::hist_bytes(nt, k, Ld, opk::variant_for_radius(rd)));
     n.hist = std::max(n.hist, opk::hist_bytes(nt, k, Ld, opk::kVarA));
   }
   return n;

@@ -37,6 +37,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace opk {
 
 constexpr int kVarA = 0;
@@ -69,7 +71,7 @@ struct __align__(16) ImgDesc {
 
 // The difference-histogram path needs r <= 15 (64-bit bins) and L <= 32
 // (5-bit level field next to the valid bit).
-constexpr int kDeltaMaxRadius = 15;
+constexpr int kDeltaMaxRadius = 44;
 constexpr uint32_t kDeltaMaxLevels = 32;
 
 // Geometry of the shared-memory halo ring, fixed per launch.  Chunk k of a
@@ -312,28 +314,64 @@ __device__ __forceinline__ uint32_t pack_word_delta(uint32_t R, uint32_t G, uint
          ((G & 0xFu) << 28);
 }
 
-// Packs row y of image d with threads tid, tid+nthr, ...
+// Word format 2 (L <= 32, 16 <= r <= 44): R @0..7 | level @8..12 |
+// B @13..20 | G @21..28 | valid @29 (see DeltaOpsB).
+__device__ __forceinline__ uint32_t pack_word_delta_b(uint32_t R, uint32_t G, uint32_t B,
+                                                      uint32_t L, uint32_t mode) {
+  return R | (level_of(R, G, B, L, mode) << 8) | (B << 13) | (G << 21) | (1u << 29);
+}
+
+// Packs row y of image d with threads tid, tid+nthr, ...  Rows whose pixels
+// start on a 16-byte (RGBA) or 4-byte (RGB) boundary are read and written
+// four pixels at a time; the packed rows always start on a 16-byte boundary
+// (the tensor map's base and pitch rule).
 __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t tid,
                                          uint32_t nthr) {
   const uint8_t *src = d.in + static_cast<size_t>(y) * d.stride;
   uint32_t *dst = d.packed + static_cast<size_t>(y) * d.ppitch;
   const uint32_t L = d.L, mode = d.mode, w = d.w;
-  const bool fmt1 = d.kcols > 1;
+  const uint32_t fmt = d.kcols > 1 ? (d.variant == kVarA ? 1u : 2u) : 0u;
   auto word = [&](uint32_t R, uint32_t G, uint32_t B) {
-    return fmt1 ? pack_word_delta(R, G, B, L, mode) : pack_word(R, G, B, L, mode);
+    return fmt == 1u   ? pack_word_delta(R, G, B, L, mode)
+           : fmt == 2u ? pack_word_delta_b(R, G, B, L, mode)
+                       : pack_word(R, G, B, L, mode);
   };
-  if (d.bpp == 4 && (reinterpret_cast<uintptr_t>(src) & 3u) == 0) {
+  auto rgba = [&](uint32_t p) { return word(p & 0xFFu, (p >> 8) & 0xFFu, (p >> 16) & 0xFFu); };
+  const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+  uint32_t x0 = 0;  // first pixel left to the scalar loop
+  if (d.bpp == 4 && (a & 15u) == 0) {
+    const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d16 = reinterpret_cast<uint4 *>(dst);
+    const uint32_t nq = w >> 2;
+    for (uint32_t q = tid; q < nq; q += nthr) {
+      const uint4 p = __ldg(s16 + q);
+      d16[q] = make_uint4(rgba(p.x), rgba(p.y), rgba(p.z), rgba(p.w));
+    }
+    x0 = nq << 2;
+  } else if (d.bpp == 3 && (a & 3u) == 0) {
+    // four RGB pixels are three words: R0G0B0R1 G1B1R2G2 B2R3G3B3
     const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
-    for (uint32_t x = tid; x < w; x += nthr) {
-      const uint32_t p = __ldg(s4 + x);
-      dst[x] = word(p & 0xFFu, (p >> 8) & 0xFFu, (p >> 16) & 0xFFu);
+    uint4 *d16 = reinterpret_cast<uint4 *>(dst);
+    const uint32_t nq = w >> 2;
+    for (uint32_t q = tid; q < nq; q += nthr) {
+      const uint32_t p0 = __ldg(s4 + 3u * q), p1 = __ldg(s4 + 3u * q + 1u),
+                     p2 = __ldg(s4 + 3u * q + 2u);
+      d16[q] = make_uint4(word(p0 & 0xFFu, (p0 >> 8) & 0xFFu, (p0 >> 16) & 0xFFu),
+                          word(p0 >> 24, p1 & 0xFFu, (p1 >> 8) & 0xFFu),
+                          word((p1 >> 16) & 0xFFu, p1 >> 24, p2 & 0xFFu),
+                          word((p2 >> 8) & 0xFFu, (p2 >> 16) & 0xFFu, p2 >> 24));
     }
-  } else {
-    const uint32_t bpp = d.bpp;
-    for (uint32_t x = tid; x < w; x += nthr) {
-      const uint8_t *p = src + x * bpp;
-      dst[x] = word(__ldg(p), __ldg(p + 1), __ldg(p + 2));
-    }
+    x0 = nq << 2;
+  }
+  if (d.bpp == 4 && (a & 3u) == 0) {
+    const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src);
+    for (uint32_t x = x0 + tid; x < w; x += nthr) dst[x] = rgba(__ldg(s4 + x));
+    return;
+  }
+  const uint32_t bpp = d.bpp;
+  for (uint32_t x = x0 + tid; x < w; x += nthr) {
+    const uint8_t *p = src + x * bpp;
+    dst[x] = word(__ldg(p), __ldg(p + 1), __ldg(p + 2));
   }
 }
 
@@ -442,13 +480,24 @@ __device__ __forceinline__ void unpack_bin(uint32_t lo, uint32_t hi, uint32_t cn
 
 // ------------------------------------------- difference-histogram bins
 //
-// Word format 1 bins (64 bits): count:10 @0 | R:18 @10 | G:18 @28 | B:18 @46.
+// Difference-histogram bins.  Both kinds are linear in the pixel (modulo
+// 2^64 / 2^32), so the signed fields of a difference histogram are
+// harmless: the sum of a window's bins decodes exactly.
+//
+// Variant A (r <= 15, word format 1), one 64-bit bin:
+//   count:10 @0 | R:18 @10 | G:18 @28 | B:18 @46.
 // The count sits at the bottom of the LOW word, so the low word of a sum of
 // bins is the sum of their low words: adding the low words of a window
 // histogram and of difference histograms gives an exact count without
 // touching the high words.  A pixel's delta is one mask of its word (low
 // word, with the valid bit landing on the count) and one shift and mask
 // (high word); zero words (outside the image) have a zero delta.
+//
+// Variant B (16 <= r <= 44, word format 2), a 64-bit sums bin
+//   R:21 @0 | G:21 @21 | B:21 @42   (89^2 * 255 < 2^21)
+// plus a 32-bit count in a second array laid out like the sums with half the
+// stride, so a bin's count address is (sums address >> 1) + cd for one
+// CTA-wide constant cd.
 
 __device__ __forceinline__ void dh_delta(uint32_t w, uint32_t &lo, uint32_t &hi) {
   lo = w & 0xF003FC01u;
@@ -462,81 +511,212 @@ __device__ __forceinline__ uint32_t dh_addr(uint32_t base, uint32_t w) {
   return base + (w & 0x3Eu) * (NT * 4u);
 }
 
-template <int NT>
-__device__ __forceinline__ void dh_add(uint32_t base, uint32_t w) {
-  uint32_t lo, hi;
-  dh_delta(w, lo, hi);
-  bin_add64(dh_addr<NT>(base, w), lo, hi);
+__device__ __forceinline__ void neg64(uint32_t &lo, uint32_t &hi) {
+  const uint64_t v = 0ull - (static_cast<uint64_t>(hi) << 32 | lo);
+  lo = static_cast<uint32_t>(v);
+  hi = static_cast<uint32_t>(v >> 32);
 }
 
+// Variant A operations on histograms given by the address of the thread's
+// level-0 bin.
 template <int NT>
-__device__ __forceinline__ void dh_sub(uint32_t base, uint32_t w) {
-  uint32_t lo, hi;
-  dh_delta(w, lo, hi);
-  bin_sub64(dh_addr<NT>(base, w), lo, hi);
-}
+struct DeltaOpsA {
+  uint32_t scratch;  // the thread's scratch bin
 
-// Delta of +win - wout at histogram `base`: the bin of win gets (alo, ahi)
-// added and the bin ab gets (blo, bhi) subtracted.  When both words have the
-// same level the two fold into one delta and ab becomes the scratch bin.
-template <int NT>
-__device__ __forceinline__ void dh_pair(uint32_t base, uint32_t win, uint32_t wout,
-                                        uint32_t scratch, uint32_t &aa, uint32_t &alo,
-                                        uint32_t &ahi, uint32_t &ab, uint32_t &blo,
-                                        uint32_t &bhi) {
-  dh_delta(win, alo, ahi);
-  dh_delta(wout, blo, bhi);
-  aa = dh_addr<NT>(base, win);
-  ab = dh_addr<NT>(base, wout);
-  if (aa == ab) {
-    const uint64_t net =
-        (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
-    alo = static_cast<uint32_t>(net);
-    ahi = static_cast<uint32_t>(net >> 32);
-    ab = scratch;
+  __device__ __forceinline__ void add(uint32_t base, uint32_t w) const {
+    uint32_t lo, hi;
+    dh_delta(w, lo, hi);
+    bin_add64(dh_addr<NT>(base, w), lo, hi);
   }
-}
-
-// +win -wout in one histogram as one two-deep update.
-template <int NT>
-__device__ __forceinline__ void dh_addsub(uint32_t base, uint32_t win, uint32_t wout,
-                                          uint32_t scratch) {
-  uint32_t aa, alo, ahi, ab, blo, bhi;
-  dh_pair<NT>(base, win, wout, scratch, aa, alo, ahi, ab, blo, bhi);
-  bin_addsub64(aa, alo, ahi, ab, blo, bhi);
-}
-
-// +win_p -wout_p in histogram p and +win_q -wout_q in histogram q != p as
-// one four-deep update.
-template <int NT>
-__device__ __forceinline__ void dh_addsub_x2(uint32_t p, uint32_t win_p, uint32_t wout_p,
-                                             uint32_t q, uint32_t win_q, uint32_t wout_q,
-                                             uint32_t scratch) {
-  uint32_t A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi;
-  dh_pair<NT>(p, win_p, wout_p, scratch, A, alo, ahi, B, blo, bhi);
-  dh_pair<NT>(q, win_q, wout_q, scratch, C, clo, chi, D, dlo, dhi);
-  bin_addsub64x2(A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi);
-}
-
-// Signed additions of single words to two histograms p != q: (+/-)wp at p,
-// (+/-)wq at q.
-template <int NT, bool NEG_P, bool NEG_Q>
-__device__ __forceinline__ void dh_pm_x2(uint32_t p, uint32_t wp, uint32_t q, uint32_t wq) {
-  uint32_t plo, phi, qlo, qhi;
-  dh_delta(wp, plo, phi);
-  dh_delta(wq, qlo, qhi);
-  if (NEG_P) {
-    const uint64_t v = 0ull - (static_cast<uint64_t>(phi) << 32 | plo);
-    plo = static_cast<uint32_t>(v);
-    phi = static_cast<uint32_t>(v >> 32);
+  __device__ __forceinline__ void sub(uint32_t base, uint32_t w) const {
+    uint32_t lo, hi;
+    dh_delta(w, lo, hi);
+    bin_sub64(dh_addr<NT>(base, w), lo, hi);
   }
-  if (NEG_Q) {
-    const uint64_t v = 0ull - (static_cast<uint64_t>(qhi) << 32 | qlo);
-    qlo = static_cast<uint32_t>(v);
-    qhi = static_cast<uint32_t>(v >> 32);
+  // +win -wout: the bin of win gets (alo, ahi) added and bin ab gets (blo,
+  // bhi) subtracted; when both words have the same level the two fold into
+  // one delta and ab becomes the scratch bin.
+  __device__ __forceinline__ void pair(uint32_t base, uint32_t win, uint32_t wout, uint32_t &aa,
+                                       uint32_t &alo, uint32_t &ahi, uint32_t &ab, uint32_t &blo,
+                                       uint32_t &bhi) const {
+    dh_delta(win, alo, ahi);
+    dh_delta(wout, blo, bhi);
+    aa = dh_addr<NT>(base, win);
+    ab = dh_addr<NT>(base, wout);
+    if (aa == ab) {
+      const uint64_t net =
+          (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
+      alo = static_cast<uint32_t>(net);
+      ahi = static_cast<uint32_t>(net >> 32);
+      ab = scratch;
+    }
   }
-  bin_add64x2(dh_addr<NT>(p, wp), plo, phi, dh_addr<NT>(q, wq), qlo, qhi);
+  // +win -wout in one histogram as one two-deep update.
+  __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
+    uint32_t aa, alo, ahi, ab, blo, bhi;
+    pair(base, win, wout, aa, alo, ahi, ab, blo, bhi);
+    bin_addsub64(aa, alo, ahi, ab, blo, bhi);
+  }
+  // +win_p -wout_p in histogram p and +win_q -wout_q in histogram q != p as
+  // one four-deep update.
+  __device__ __forceinline__ void addsub_x2(uint32_t p, uint32_t win_p, uint32_t wout_p,
+                                            uint32_t q, uint32_t win_q, uint32_t wout_q) const {
+    uint32_t A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi;
+    pair(p, win_p, wout_p, A, alo, ahi, B, blo, bhi);
+    pair(q, win_q, wout_q, C, clo, chi, D, dlo, dhi);
+    bin_addsub64x2(A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi);
+  }
+  // (+/-)wp at histogram p and (+/-)wq at histogram q != p.
+  template <bool NEG_P, bool NEG_Q>
+  __device__ __forceinline__ void pm_x2(uint32_t p, uint32_t wp, uint32_t q, uint32_t wq) const {
+    uint32_t plo, phi, qlo, qhi;
+    dh_delta(wp, plo, phi);
+    dh_delta(wq, qlo, qhi);
+    if (NEG_P) neg64(plo, phi);
+    if (NEG_Q) neg64(qlo, qhi);
+    bin_add64x2(dh_addr<NT>(p, wp), plo, phi, dh_addr<NT>(q, wq), qlo, qhi);
+  }
+};
+
+// Variant B: +(lo, hi) at sums address s and +c at count address sc, and
+// -(lo, hi) / -c at a second bin, all loads first (distinct bins except
+// that the second may be the scratch bin).
+__device__ __forceinline__ void binb_addsub(uint32_t As, uint32_t Ac, uint32_t alo, uint32_t ahi,
+                                            uint32_t ac, uint32_t Bs, uint32_t Bc, uint32_t blo,
+                                            uint32_t bhi, uint32_t bc) {
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u32 a2, [%1];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
+      "ld.shared.u32 b2, [%6];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "sub.cc.u32 b0, b0, %7;\n\t"
+      "subc.u32 b1, b1, %8;\n\t"
+      "sub.u32 b2, b2, %9;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u32 [%1], a2;\n\t"
+      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
+      "st.shared.u32 [%6], b2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
 }
+
+// Two additions at two distinct bins (signs folded into the deltas).
+__device__ __forceinline__ void binb_add_x2(uint32_t As, uint32_t Ac, uint32_t alo, uint32_t ahi,
+                                            uint32_t ac, uint32_t Bs, uint32_t Bc, uint32_t blo,
+                                            uint32_t bhi, uint32_t bc) {
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u32 a2, [%1];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
+      "ld.shared.u32 b2, [%6];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "add.cc.u32 b0, b0, %7;\n\t"
+      "addc.u32 b1, b1, %8;\n\t"
+      "add.u32 b2, b2, %9;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u32 [%1], a2;\n\t"
+      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
+      "st.shared.u32 [%6], b2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+}
+
+__device__ __forceinline__ void binb_add(uint32_t As, uint32_t Ac, uint32_t lo, uint32_t hi,
+                                         uint32_t c) {
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, a2;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u32 a2, [%1];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u32 [%1], a2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(lo), "r"(hi), "r"(c));
+}
+
+// Word format 2 (L <= 32): R @0..7 | level @8..12 | B @13..20 | G @21..28 |
+// valid @29.  Sums delta: low word one mask (R, G), high word one shift and
+// mask (B << 10); count delta: the valid bit.
+__device__ __forceinline__ void dhb_delta(uint32_t w, uint32_t &lo, uint32_t &hi, uint32_t &c) {
+  lo = w & 0x1FE000FFu;
+  hi = (w >> 3) & 0x0003FC00u;
+  c = w >> 29;
+}
+
+template <int NT>
+struct DeltaOpsB {
+  uint32_t scratch;  // the thread's scratch sums bin
+  uint32_t cd;       // count address = (sums address >> 1) + cd
+
+  __device__ __forceinline__ uint32_t saddr(uint32_t base, uint32_t w) const {
+    return base + (w & 0x1F00u) * (NT / 32u);
+  }
+  __device__ __forceinline__ uint32_t caddr(uint32_t s) const { return (s >> 1) + cd; }
+
+  __device__ __forceinline__ void add(uint32_t base, uint32_t w) const {
+    uint32_t lo, hi, c;
+    dhb_delta(w, lo, hi, c);
+    const uint32_t s = saddr(base, w);
+    binb_add(s, caddr(s), lo, hi, c);
+  }
+  __device__ __forceinline__ void sub(uint32_t base, uint32_t w) const {
+    uint32_t lo, hi, c;
+    dhb_delta(w, lo, hi, c);
+    neg64(lo, hi);
+    const uint32_t s = saddr(base, w);
+    binb_add(s, caddr(s), lo, hi, 0u - c);
+  }
+  __device__ __forceinline__ void pair(uint32_t base, uint32_t win, uint32_t wout, uint32_t &as,
+                                       uint32_t &alo, uint32_t &ahi, uint32_t &ac, uint32_t &bs,
+                                       uint32_t &blo, uint32_t &bhi, uint32_t &bc) const {
+    dhb_delta(win, alo, ahi, ac);
+    dhb_delta(wout, blo, bhi, bc);
+    as = saddr(base, win);
+    bs = saddr(base, wout);
+    if (as == bs) {
+      const uint64_t net =
+          (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
+      alo = static_cast<uint32_t>(net);
+      ahi = static_cast<uint32_t>(net >> 32);
+      ac -= bc;
+      bs = scratch;
+    }
+  }
+  __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
+    uint32_t as, alo, ahi, ac, bs, blo, bhi, bc;
+    pair(base, win, wout, as, alo, ahi, ac, bs, blo, bhi, bc);
+    binb_addsub(as, caddr(as), alo, ahi, ac, bs, caddr(bs), blo, bhi, bc);
+  }
+  // Two histograms: issued as two two-deep updates (a four-deep one would
+  // need 20 operands and more registers than it saves latency here).
+  __device__ __forceinline__ void addsub_x2(uint32_t p, uint32_t win_p, uint32_t wout_p,
+                                            uint32_t q, uint32_t win_q, uint32_t wout_q) const {
+    addsub(p, win_p, wout_p);
+    addsub(q, win_q, wout_q);
+  }
+  template <bool NEG_P, bool NEG_Q>
+  __device__ __forceinline__ void pm_x2(uint32_t p, uint32_t wp, uint32_t q, uint32_t wq) const {
+    uint32_t plo, phi, pc, qlo, qhi, qc;
+    dhb_delta(wp, plo, phi, pc);
+    dhb_delta(wq, qlo, qhi, qc);
+    if (NEG_P) {
+      neg64(plo, phi);
+      pc = 0u - pc;
+    }
+    if (NEG_Q) {
+      neg64(qlo, qhi);
+      qc = 0u - qc;
+    }
+    const uint32_t ps = saddr(p, wp), qs = saddr(q, wq);
+    binb_add_x2(ps, caddr(ps), plo, phi, pc, qs, caddr(qs), qlo, qhi, qc);
+  }
+};
 
 // ------------------------------------------------------------ division
 
@@ -821,23 +1001,23 @@ struct VecOf<4> {
 //   D_{j-2r} positively (its right column) when j >= 2r+1.
 // Groups of K words are loaded as one vector; the groups that only feed H
 // skip the tests.
-template <int NT, int K, bool RM>
-__device__ __forceinline__ void delta_step(const uint32_t *pe, const uint32_t *pl, int r,
-                                           uint32_t h0, uint32_t hstride, uint32_t scratch) {
+template <int K, bool RM, class Ops>
+__device__ __forceinline__ void delta_step(const Ops &ops, const uint32_t *pe, const uint32_t *pl,
+                                           int r, uint32_t h0, uint32_t hstride) {
   using V = typename VecOf<K>::T;
   const int last = 2 * r + K - 1;
   const int ngroups = last / K + 1;
   auto upd = [&](uint32_t base, uint32_t e, uint32_t l) {
     if (RM)
-      dh_addsub<NT>(base, e, l, scratch);
+      ops.addsub(base, e, l);
     else
-      dh_add<NT>(base, e);
+      ops.add(base, e);
   };
   auto updneg = [&](uint32_t base, uint32_t e, uint32_t l) {
     if (RM)
-      dh_addsub<NT>(base, l, e, scratch);
+      ops.addsub(base, l, e);
     else
-      dh_sub<NT>(base, e);
+      ops.sub(base, e);
   };
   auto word = [&](int j, uint32_t e, uint32_t l) {
     if (j <= 2 * r) upd(h0, e, l);
@@ -871,10 +1051,10 @@ __device__ __forceinline__ void delta_step(const uint32_t *pe, const uint32_t *p
 // update of an even word is issued together with one of an odd word (four
 // bins in flight instead of two); the last even word pairs with the first
 // D update and the D updates pair among themselves.
-template <int NT, int K, bool RM>
-__device__ __forceinline__ void delta_step_split(const uint32_t *pe, const uint32_t *pl, int r,
-                                                 uint32_t h0, uint32_t hstride,
-                                                 uint32_t scratch) {
+template <int K, bool RM, class Ops>
+__device__ __forceinline__ void delta_step_split(const Ops &ops, const uint32_t *pe,
+                                                 const uint32_t *pl, int r, uint32_t h0,
+                                                 uint32_t hstride) {
   using V = typename VecOf<K>::T;
   const uint32_t hev = h0, hod = h0 + hstride;
   auto dh = [&](int i) { return h0 + static_cast<uint32_t>(1 + i) * hstride; };
@@ -883,17 +1063,17 @@ __device__ __forceinline__ void delta_step_split(const uint32_t *pe, const uint3
   // +e -l in histograms p and q (p != q)
   auto both = [&](uint32_t p, uint32_t ep, uint32_t lp, uint32_t q, uint32_t eq, uint32_t lq) {
     if (RM)
-      dh_addsub_x2<NT>(p, ep, lp, q, eq, lq, scratch);
+      ops.addsub_x2(p, ep, lp, q, eq, lq);
     else
-      dh_pm_x2<NT, false, false>(p, ep, q, eq);
+      ops.template pm_x2<false, false>(p, ep, q, eq);
   };
   // +e -l in histogram p and the column leaving D_i: +l -e in histogram q
   auto with_leaving = [&](uint32_t p, uint32_t ep, uint32_t lp, uint32_t q, uint32_t eq,
                           uint32_t lq) {
     if (RM)
-      dh_addsub_x2<NT>(p, ep, lp, q, lq, eq, scratch);
+      ops.addsub_x2(p, ep, lp, q, lq, eq);
     else
-      dh_pm_x2<NT, false, true>(p, ep, q, eq);
+      ops.template pm_x2<false, true>(p, ep, q, eq);
   };
   const int nfull = (2 * r + 1) / K;  // groups made only of window words
   const V a0 = load(pe);
@@ -931,22 +1111,22 @@ __device__ __forceinline__ void delta_step_split(const uint32_t *pe, const uint3
   if (K == 2) {
     const uint32_t e = pe2[0], l = RM ? pl2[0] : 0u;
     if (RM)
-      dh_addsub<NT>(dh(1), e, l, scratch);
+      ops.addsub(dh(1), e, l);
     else
-      dh_add<NT>(dh(1), e);
+      ops.add(dh(1), e);
   } else {
     // D_2, D_3 lose words 1, 2; D_1, D_2, D_3 gain words 2r+1, 2r+2, 2r+3
     if (RM)
-      dh_addsub_x2<NT>(dh(2), at(b0, 1), at(a0, 1), dh(3), at(b0, 2), at(a0, 2), scratch);
+      ops.addsub_x2(dh(2), at(b0, 1), at(a0, 1), dh(3), at(b0, 2), at(a0, 2));
     else
-      dh_pm_x2<NT, true, true>(dh(2), at(a0, 1), dh(3), at(a0, 2));
+      ops.template pm_x2<true, true>(dh(2), at(a0, 1), dh(3), at(a0, 2));
     const uint32_t e1 = pe2[0], e2 = pe2[1], e3 = pe2[2];
     const uint32_t l1 = RM ? pl2[0] : 0u, l2 = RM ? pl2[1] : 0u, l3 = RM ? pl2[2] : 0u;
     both(dh(1), e1, l1, dh(2), e2, l2);
     if (RM)
-      dh_addsub<NT>(dh(3), e3, l3, scratch);
+      ops.addsub(dh(3), e3, l3);
     else
-      dh_add<NT>(dh(3), e3);
+      ops.add(dh(3), e3);
   }
 }
 
@@ -955,32 +1135,38 @@ __device__ __forceinline__ void delta_step_split(const uint32_t *pe, const uint3
 // resident warps, and the extra independent update chain pays for the
 // extra histogram; with two columns the extra histogram costs more
 // occupancy than the chain gains.
+// Variant B bins (12 bytes) never split.
 constexpr bool kSplit2 = false;
 constexpr bool kSplit4 = true;
-__host__ __device__ constexpr bool split_for(int k) { return k == 4 ? kSplit4 : kSplit2; }
+__host__ __device__ constexpr bool split_for(int k, int var) {
+  return var == kVarA && (k == 4 ? kSplit4 : kSplit2);
+}
 
-// K output columns per thread through difference histograms (word format 1,
-// r <= 15, L <= 32).  Thread t owns columns xa .. xa+K-1 with xa = x0 + K*t;
-// x0 - r is a multiple of 4 (tiles start at d.xshift), so every thread's
-// window starts on a 16-byte boundary of the ring.  It keeps
-//   H    the histogram of the window of column xa (2r+1 columns; with SPLIT
-//        two histograms over its even and odd columns),
+// K output columns per thread through difference histograms (r <= 44,
+// L <= 32; VAR A for r <= 15 with word format 1, VAR B above with word
+// format 2).  Thread t owns columns xa .. xa+K-1 with xa = x0 + K*t; x0 - r
+// is a multiple of 4 (tiles start at d.xshift), so every thread's window
+// starts on a 16-byte boundary of the ring.  It keeps
+//   H    the histogram of the window of column xa (2r+1 columns; split into
+//        two histograms over its even and odd columns where split_for says),
 //   D_i  (i = 1..K-1) the histogram of column xa+i+r minus that of column
 //        xa+i-1-r, so that the window histogram of column xa+i is
 //        H + D_1 + ... + D_i.
 // A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  Histograms are
-// L levels of NT 64-bit bins (level-major, thread-minor), followed by one
-// scratch bin per thread.  The argmax runs over the running sums of the
-// histograms' low words, whose bottom 10 bits are the counts; a key
-// (count << 22) | (31 - level) makes the lowest level win ties under max.
-// Pixels outside the image are TMA zero fill whose delta is zero, so no
-// thread clips its window.
-template <int NT, int K, bool SPLIT>
+// L levels of NT bins (level-major, thread-minor), followed by one scratch
+// bin per thread; VAR B keeps its counts in a second array of the same
+// shape.  The argmax runs over running sums of counts (VAR A: the
+// histograms' low words, whose bottom 10 bits are the counts) with keys
+// (count, 31 - level), so the lowest level wins ties under max.  Pixels
+// outside the image are TMA zero fill whose delta is zero, so no thread
+// clips its window.
+template <int NT, int K, int VAR>
 __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0,
                                int y1, const RingCfg &rc, const SmemMap &sm,
                                uint32_t &chunk_ctr, uint32_t *err, uint64_t timeout_ns,
                                uint32_t *diag = nullptr, bool tmap_global = false) {
   static_assert(K == 2 || K == 4, "two or four columns per thread");
+  constexpr bool SPLIT = split_for(K, VAR);
   constexpr int NB = SPLIT ? 2 : 1;  // histograms making up H
   constexpr int NH = NB + K - 1;
   const int t = threadIdx.x;
@@ -992,14 +1178,25 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
   const int jl = K * t;
   const int E0 = y0 - r;
   const int nsteps = (y1 - y0) + 2 * r;
-  const uint32_t lstride = NT * 8u;    // between levels of one histogram
+  const uint32_t lstride = NT * 8u;      // between levels of one histogram
   const uint32_t hstride = L * lstride;  // between histograms
   const uint32_t h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
   const uint32_t scratch = h0 + NH * hstride;
+  // VAR B counts: same shape at half the stride, after the sums
+  const uint32_t cbase = sm.sums + (NH * L + 1u) * lstride;
+  const uint32_t cd = cbase - (sm.sums >> 1);
+  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<NT>, DeltaOpsB<NT>>::type;
+  Ops ops;
+  ops.scratch = scratch;
+  if constexpr (VAR == kVarB) ops.cd = cd;
   auto hist = [&](int i) { return h0 + static_cast<uint32_t>(i) * hstride; };
+  auto cnt_of = [&](uint32_t s) { return (s >> 1) + cd; };
 #pragma unroll
   for (int i = 0; i < NH; ++i)
-    for (uint32_t lv = 0; lv < L; ++lv) sts_zero64(hist(i) + lv * lstride);
+    for (uint32_t lv = 0; lv < L; ++lv) {
+      sts_zero64(hist(i) + lv * lstride);
+      if (VAR == kVarB) sts_zero32(cnt_of(hist(i) + lv * lstride));
+    }
 
   return ring_pass(
       d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
@@ -1017,28 +1214,34 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
         }
         if (SPLIT) {
           if (rm)
-            delta_step_split<NT, K, true>(pe, pl, r, h0, hstride, scratch);
+            delta_step_split<K, true>(ops, pe, pl, r, h0, hstride);
           else
-            delta_step_split<NT, K, false>(pe, pl, r, h0, hstride, scratch);
+            delta_step_split<K, false>(ops, pe, pl, r, h0, hstride);
         } else {
           if (rm)
-            delta_step<NT, K, true>(pe, pl, r, h0, hstride, scratch);
+            delta_step<K, true>(ops, pe, pl, r, h0, hstride);
           else
-            delta_step<NT, K, false>(pe, pl, r, h0, hstride, scratch);
+            delta_step<K, false>(ops, pe, pl, r, h0, hstride);
         }
         if (!out_now) return;
+        // count of level lv in histogram i (VAR A: the low word, count in bits 0..9)
+        auto count_word = [&](int i, uint32_t lv) {
+          const uint32_t a = hist(i) + lv * lstride;
+          return lds_u32(VAR == kVarA ? a : cnt_of(a));
+        };
+        constexpr int CSH = VAR == kVarA ? 22 : 5;  // VAR A: drop the sums above the count
         uint32_t best[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) best[i] = 0u;
         for (uint32_t lv = 0; lv < L; ++lv) {
           const uint32_t tag = 31u - lv;
-          uint32_t acc = lds_u32(hist(0) + lv * lstride);
-          if (SPLIT) acc += lds_u32(hist(1) + lv * lstride);
-          best[0] = max(best[0], (acc << 22) | tag);
+          uint32_t acc = count_word(0, lv);
+          if (SPLIT) acc += count_word(1, lv);
+          best[0] = max(best[0], (acc << CSH) | tag);
 #pragma unroll
           for (int i = 1; i < K; ++i) {
-            acc += lds_u32(hist(NB - 1 + i) + lv * lstride);
-            best[i] = max(best[i], (acc << 22) | tag);
+            acc += count_word(NB - 1 + i, lv);
+            best[i] = max(best[i], (acc << CSH) | tag);
           }
         }
 #pragma unroll
@@ -1046,7 +1249,7 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
           const int x = xa + i;
           if (x < 0 || x >= W) continue;
           const uint32_t m = 31u - (best[i] & 31u);
-          const uint32_t cnt = best[i] >> 22;
+          const uint32_t cnt = best[i] >> CSH;
           uint64_t v = 0;
 #pragma unroll
           for (int j = 0; j < NB + i; ++j) {
@@ -1056,12 +1259,19 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
           }
           const uint32_t lo = static_cast<uint32_t>(v);
           const uint32_t hi = static_cast<uint32_t>(v >> 32);
-          const uint32_t R = (lo >> 10) & 0x3FFFFu;
-          const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
-          const uint32_t B = hi >> 14;
-          const uint32_t mul = rcp_of(cnt);
-          store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul),
-                      __umulhi(B << 1, mul), alpha[i]);
+          if (VAR == kVarA) {
+            const uint32_t R = (lo >> 10) & 0x3FFFFu;
+            const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
+            const uint32_t B = hi >> 14;
+            const uint32_t mul = rcp_of(cnt);
+            store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul),
+                        __umulhi(B << 1, mul), alpha[i]);
+          } else {
+            const uint32_t R = lo & 0x1FFFFFu;
+            const uint32_t G = (lo >> 21) | ((hi & 0x3FFu) << 11);
+            const uint32_t B = (hi >> 10) & 0x1FFFFFu;
+            store_pixel(d, x, y, R / cnt, G / cnt, B / cnt, alpha[i]);
+          }
         }
       });
 }

@@ -89,12 +89,12 @@ inline Geometry image_geometry(uint32_t nt, int kcols_wanted, int r, uint32_t L,
 
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
 // per thread, bins of the variant's size; 2 or 4: kcols histograms, one
-// more where the window histogram is split, of L 64-bit levels per thread,
-// plus one scratch bin).
+// more where the window histogram is split, of L levels per thread plus one
+// scratch bin, bins of 8 bytes (variant A) or 8 + 4 bytes (variant B)).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
   if (kcols > 1) {
-    const size_t nh = static_cast<size_t>(kcols) + (split_for(kcols) ? 1u : 0u);
-    return (nh * L + 1u) * nt * 8u;
+    const size_t nh = static_cast<size_t>(kcols) + (split_for(kcols, variant) ? 1u : 0u);
+    return (nh * L + 1u) * nt * (variant == kVarA ? 8u : 12u);
   }
   return static_cast<size_t>(L + 1u) * nt * bin_bytes(variant);
 }

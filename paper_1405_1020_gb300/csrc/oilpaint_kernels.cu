@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(NT, 1)
   run_tile<NT, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
-template <int NT, int K, bool SPLIT>
+template <int NT, int K, int VAR>
 __global__ void __launch_bounds__(NT, 1)
     tile_delta_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d, const RingCfg rc,
                       uint32_t *err, uint64_t timeout_ns) {
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT, 1)
   const int x0 = d.xshift + static_cast<int>(blockIdx.x) * NT * K;
   const int y0 = static_cast<int>(blockIdx.y * d.tile_h);
   const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
-  run_tile_delta<NT, K, SPLIT>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+  run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
 // K = 1: every image on the one-column path; K = 2 or 4: images with
@@ -118,8 +118,11 @@ __global__ void __launch_bounds__(NT, 1)
     bool ok;
     if (K > 1 && d.kcols == static_cast<uint32_t>(K)) {
       constexpr int KD = K > 1 ? K : 2;
-      ok = run_tile_delta<NT, KD, split_for(KD)>(d, d.tmap, x0, y0, y1, rc, sm, ctr, err,
-                                                 timeout_ns, diag, true);
+      ok = d.variant == kVarA
+               ? run_tile_delta<NT, KD, kVarA>(d, d.tmap, x0, y0, y1, rc, sm, ctr, err,
+                                               timeout_ns, diag, true)
+               : run_tile_delta<NT, KD, kVarB>(d, d.tmap, x0, y0, y1, rc, sm, ctr, err,
+                                               timeout_ns, diag, true);
     } else {
       // this image's counts follow its own L + 1 levels of sums
       SmemMap smi = sm;
@@ -171,10 +174,18 @@ static void plain_n(int variant, const ImgDesc &d, const CUtensorMap &map, const
 template <int NT>
 static void delta_n(int k, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
                     dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
-  if (k == 4)
-    tile_delta_kernel<NT, 4, kSplit4><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
-  else
-    tile_delta_kernel<NT, 2, kSplit2><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+  const bool a = d.variant == static_cast<uint32_t>(kVarA);
+  if (k == 4) {
+    if (a)
+      tile_delta_kernel<NT, 4, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+    else
+      tile_delta_kernel<NT, 4, kVarB><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+  } else {
+    if (a)
+      tile_delta_kernel<NT, 2, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+    else
+      tile_delta_kernel<NT, 2, kVarB><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+  }
 }
 
 cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
@@ -257,8 +268,10 @@ static cudaError_t set_limit_n(int b) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, kVarA>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tile_plain_kernel<NT, kVarB>, a, b)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 2, kSplit2>, a, b)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kSplit4>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 2, kVarA>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kVarA>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 2, kVarB>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kVarB>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 1>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 2>, a, b)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(persistent_kernel<NT, 4>, a, b);
@@ -286,8 +299,12 @@ static int occupancy_n(bool persistent, int kcols, int variant, size_t smem) {
     if (kcols == 2) return occ_of(persistent_kernel<NT, 2>, NT, smem);
     return occ_of(persistent_kernel<NT, 1>, NT, smem);
   }
-  if (kcols == 4) return occ_of(tile_delta_kernel<NT, 4, kSplit4>, NT, smem);
-  if (kcols == 2) return occ_of(tile_delta_kernel<NT, 2, kSplit2>, NT, smem);
+  if (kcols == 4)
+    return variant == kVarA ? occ_of(tile_delta_kernel<NT, 4, kVarA>, NT, smem)
+                            : occ_of(tile_delta_kernel<NT, 4, kVarB>, NT, smem);
+  if (kcols == 2)
+    return variant == kVarA ? occ_of(tile_delta_kernel<NT, 2, kVarA>, NT, smem)
+                            : occ_of(tile_delta_kernel<NT, 2, kVarB>, NT, smem);
   return variant == kVarA ? occ_of(tile_plain_kernel<NT, kVarA>, NT, smem)
                           : occ_of(tile_plain_kernel<NT, kVarB>, NT, smem);
 }

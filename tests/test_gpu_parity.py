@@ -149,16 +149,17 @@ def test_fuzz(k, w, h, r, L, bpp, pad, mode, cfg):
         assert e.status == B.OP_E_UNSUPPORTED, e
 
 
-def _delta_fuzz_cases(n=40, seed=11):
-    """Cases the difference-histogram path takes (r <= 15, L <= 32, 2 or 4
-    columns per thread): every r mod 4 (the tile's x shift), widths around
-    the tile width, one-column and one-row images."""
+def _delta_fuzz_cases(n=56, seed=11):
+    """Cases the difference-histogram path takes (L <= 32, 2 or 4 columns
+    per thread; 8-byte bins for r <= 15, 12-byte bins above): every r mod 4
+    (the tile's x shift), widths around the tile width, one-column and
+    one-row images."""
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(n):
         w = int(rng.choice([1, 2, 3, 4, 5, 7, 31, 61, 64, 67, 127, 128, 131, 190, 256, 259, 400]))
         h = int(rng.choice([1, 2, 3, 9, 16, 33, 100, 211]))
-        r = int(rng.integers(0, 16))
+        r = int(rng.integers(0, 16)) if k < 40 else int(rng.integers(16, 45))
         L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32]))
         bpp = int(rng.choice([3, 4]))
         pad = int(rng.choice([0, 1, 4, 13]))
@@ -186,8 +187,11 @@ def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
         ng = (2 * r + K - 1) // K + 1
         boxw = -(-K * (nt - 1 + ng) // 4) * 4
         half = -(-boxw * cfg["chunk_rows"] * 4 // 128) * 128
-        smem = 2 * half * (cfg["prefetch"] + 1) + K * (L + 1) * nt * 8 + 4096 + 256
-        assert boxw > 256 or smem > 200 * 1024, (cfg, r, L)
+        nh = K + (1 if K == 4 and r <= 15 else 0)  # four 8-byte columns split H
+        hist = (nh * L + 1) * nt * (8 if r <= 15 else 12)
+        slots = cfg["prefetch"] + 1
+        smem = 128 + -(-slots * 8 // 128) * 128 + 2 * half * slots + hist
+        assert boxw > 256 or smem > 226 * 1024, (cfg, r, L, smem)
 
 
 # ---- edge cases --------------------------------------------------------------
@@ -242,8 +246,9 @@ def test_columns_per_thread_both_variants(cpt, r, L):
     """Both histogram variants, one column per thread and both difference-
     histogram widths, with every halo offset (r mod 4), on images whose
     width is not a tile multiple.  Two or four columns per thread are
-    refused exactly when r > 15 or L > 32; with one column per thread,
-    configurations beyond shared memory are skipped and one must run."""
+    refused when L > 32 (and where the halo box or shared memory does not
+    fit); with one column per thread, configurations beyond shared memory
+    are skipped and one must run."""
     img = synth.camera_like(190, 270, seed=r * L + 1, npoly=25, rad_range=(3, 100))
     ran = 0
     for bpp, pad, nt, ch in ((4, 4, 64, 8), (3, 1, 32, 3)):
@@ -253,7 +258,7 @@ def test_columns_per_thread_both_variants(cpt, r, L):
             ran += 1
         except B.OilPaintError as e:
             assert e.status == B.OP_E_UNSUPPORTED, e
-    if cpt > 1 and (r > 15 or L > 32):
+    if cpt > 1 and L > 32:
         assert ran == 0
     elif cpt == 4:
         assert ran >= 1  # 64 threads x 4 columns: a 256+ box at r >= 1
