@@ -298,18 +298,38 @@ def run_ours(args):
                 "ops_per_pixel": ops_per_pixel(RADIUS, LEVELS),
                 "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz"}
 
-    # end to end through the host-buffer entry point
+    # end to end through the host-buffer entry points: every step copies its
+    # input from pinned host memory and its result back.  op_run_host_async
+    # lets consecutive steps overlap (copy in / filter / copy out on the op's
+    # own streams); op_run_host is the synchronous, one-at-a-time form.
     h_in = torch.from_numpy(buf).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
-    op.run_host(h_in, h_out)
-    e2e_times = []
-    for _ in range(max(3, args.steps // 2)):
+    e2e_stream = torch.cuda.Stream()
+    n_e2e = max(10, args.steps)
+    for _ in range(3):
+        op.run_host_async(h_in, h_out, e2e_stream)
+    e2e_stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    for _ in range(n_e2e):
+        op.run_host_async(h_in, h_out, e2e_stream)
+    e2e_stream.synchronize()
+    e2e_s = reduce_max((time.perf_counter() - t) / n_e2e)
+    if op.sync_status(e2e_stream) != B.OP_OK:
+        raise RuntimeError("device error in the host-buffer steps")
+    sync_times = []
+    for _ in range(max(3, args.steps // 4)):
         t = time.perf_counter()
         op.run_host(h_in, h_out)
-        e2e_times.append(time.perf_counter() - t)
-    e2e_s = statistics.mean(e2e_times)
+        sync_times.append(time.perf_counter() - t)
+    sync_s = reduce_max(statistics.mean(sync_times))
     e2e = {"value": round(world * W * H / e2e_s / 1e6, 3), "unit": "Mpix/s",
-           "h2d_bytes_per_step": H * STRIDE, "d2h_bytes_per_step": H * W * BPP}
+           "h2d_bytes_per_step": H * STRIDE, "d2h_bytes_per_step": H * W * BPP,
+           "steps": n_e2e, "ms_per_step": round(e2e_s * 1e3, 4),
+           "api": "op_run_host_async (consecutive steps overlap copies and filter)",
+           "sync_value": round(world * W * H / sync_s / 1e6, 3),
+           "sync_api": "op_run_host (one step at a time)"}
     if not np.array_equal(h_out.numpy(), dst.cpu().numpy()):
         raise RuntimeError("op_run_host output differs from op_run output")
 

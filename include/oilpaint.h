@@ -152,12 +152,27 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream);
 /*
  * op_run_host -- the same filter on host buffers: copies h_in to device
  * memory owned by `op`, runs, copies the result to h_out and synchronises
- * `stream` before returning.  h_in, h_out: host pointers to height*stride
- * bytes (page-locked memory makes the copies faster).  Only pixel bytes of
- * h_out are written; its row padding is left untouched.  Device staging
- * memory is allocated on the first call and freed by op_destroy.
+ * `stream` before returning (op_run_host_async followed by op_sync_status).
+ * h_in, h_out: host pointers to height*stride bytes (page-locked memory makes
+ * the copies faster and lets them overlap).  Only pixel bytes of h_out are
+ * written; its row padding is left untouched.  Device staging memory and
+ * three internal streams are created on the first call and freed by
+ * op_destroy.
  */
 int op_run_host(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream);
+
+/*
+ * op_run_host_async -- enqueue the host-buffer filter and return.  The copy
+ * of h_in, the filter and the copy to h_out run on the op's own streams
+ * through one of two staging slots, so consecutive calls pipeline: one
+ * image's copies in and out overlap another's filter.  `stream` is made to
+ * wait for this call's copy to h_out, so synchronising it (or
+ * op_sync_status) waits for the result; h_in is read without waiting for
+ * `stream` (host data is ready when the call is made).  h_in and h_out must
+ * stay valid, and h_in unchanged, until then; page-locked memory is needed
+ * for the copies to be asynchronous.  Not thread-safe per op.
+ */
+int op_run_host_async(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream);
 
 /* Profiling hook: when `event` (a cudaEvent_t passed as void*) is not NULL,
  * every later op_run records it on the run's stream between the pack prepass

@@ -35,7 +35,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboilpaint
 EXPORTS = (
     "op_create", "op_create_ex", "op_last_error", "op_status_string", "op_get_config",
     "op_set_config", "op_default_config", "op_tune_table_set", "op_workspace_size",
-    "op_set_workspace", "op_run", "op_run_host", "op_set_profile_event", "op_sync_status",
+    "op_set_workspace", "op_run", "op_run_host", "op_run_host_async", "op_set_profile_event",
+    "op_sync_status",
     "op_destroy",
     "op_batch_create", "op_batch_get_config", "op_batch_workspace_size",
     "op_batch_set_workspace", "op_batch_set",
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "op_set_workspace": (ci, [vp, vp, sz]),
         "op_run": (ci, [vp, vp, vp, vp]),
         "op_run_host": (ci, [vp, vp, vp, vp]),
+        "op_run_host_async": (ci, [vp, vp, vp, vp]),
         "op_set_profile_event": (ci, [vp, vp]),
         "op_sync_status": (ci, [vp, vp]),
         "op_destroy": (ci, [vp]),
@@ -184,6 +186,10 @@ def op_run(op, d_in, d_out, stream=None):
 
 def op_run_host(op, h_in, h_out, stream=None):
     return load().op_run_host(op, h_in, h_out, stream)
+
+
+def op_run_host_async(op, h_in, h_out, stream=None):
+    return load().op_run_host_async(op, h_in, h_out, stream)
 
 
 def op_set_profile_event(op, event):

@@ -268,9 +268,62 @@ struct op_s {
   CUtensorMap map;
   bool map_valid = false;
   uint32_t *d_err = nullptr;
-  uint8_t *d_stage_in = nullptr, *d_stage_out = nullptr;
   cudaEvent_t prof_ev = nullptr;
+  // host-buffer path: two staging slots, each an input and an output image,
+  // and three internal streams (copy in, filter, copy out) so that
+  // consecutive calls overlap one image's copies with another's filter
+  struct HostPipe {
+    bool ready = false;
+    cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+    uint8_t *d_in[2] = {nullptr, nullptr}, *d_out[2] = {nullptr, nullptr};
+    cudaEvent_t in_done[2] = {nullptr, nullptr}, run_done[2] = {nullptr, nullptr},
+                out_done[2] = {nullptr, nullptr};
+    uint32_t next = 0;  // slot of the next call
+  } hp;
 };
+
+namespace {
+
+void host_pipe_free(op_s::HostPipe &hp) {
+  cudaStream_t ss[3] = {hp.s_in, hp.s_run, hp.s_out};
+  for (cudaStream_t x : ss)
+    if (x) cudaStreamSynchronize(x);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(hp.d_in[b]);
+    cudaFree(hp.d_out[b]);
+    if (hp.in_done[b]) cudaEventDestroy(hp.in_done[b]);
+    if (hp.run_done[b]) cudaEventDestroy(hp.run_done[b]);
+    if (hp.out_done[b]) cudaEventDestroy(hp.out_done[b]);
+  }
+  for (cudaStream_t x : ss)
+    if (x) cudaStreamDestroy(x);
+  hp = op_s::HostPipe();
+}
+
+int host_pipe_init(op_s::HostPipe &hp, size_t bytes) {
+  if (hp.ready) return OP_OK;
+  cudaError_t e = cudaSuccess;
+  const unsigned sf = cudaStreamNonBlocking;
+  const unsigned ef = cudaEventDisableTiming;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp.s_in, sf);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp.s_run, sf);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp.s_out, sf);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMalloc(&hp.d_in[b], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&hp.d_out[b], bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.in_done[b], ef);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.run_done[b], ef);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp.out_done[b], ef);
+  }
+  if (e != cudaSuccess) {
+    host_pipe_free(hp);
+    return cuda_status(e);
+  }
+  hp.ready = true;
+  return OP_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -457,29 +510,41 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   return e == cudaSuccess ? OP_OK : OP_E_CUDA;
 }
 
-int op_run_host(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream) {
+int op_run_host_async(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream) {
   if (!op || !h_in || !h_out) return OP_E_INVALID;
   const size_t bytes = static_cast<size_t>(op->h) * op->stride;
   if (ranges_overlap(h_in, h_out, bytes)) return OP_E_INVALID;
-  if (!op->d_stage_in) {
-    cudaError_t e = cudaMalloc(&op->d_stage_in, bytes);
-    if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMalloc(&op->d_stage_out, bytes);
-    if (e != cudaSuccess) {
-      cudaFree(op->d_stage_in);
-      op->d_stage_in = nullptr;
-      return cuda_status(e);
-    }
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(op->d_stage_in, h_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return OP_E_CUDA;
-  int st = op_run(op, op->d_stage_in, op->d_stage_out, stream);
+  op_s::HostPipe &hp = op->hp;
+  int st = host_pipe_init(hp, bytes);
   if (st != OP_OK) return st;
+  const uint32_t b = hp.next;
+  hp.next ^= 1u;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t row = static_cast<size_t>(op->w) * op->bpp;
-  if (cudaMemcpy2DAsync(h_out, op->stride, op->d_stage_out, op->stride, row, op->h,
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  // slot b's input may be overwritten once the filter that read it is done,
+  // its output once the copy that read it is done; events never recorded
+  // yet are complete
+  if (cudaStreamWaitEvent(hp.s_in, hp.run_done[b], 0) != cudaSuccess ||
+      cudaMemcpyAsync(hp.d_in[b], h_in, bytes, cudaMemcpyHostToDevice, hp.s_in) != cudaSuccess ||
+      cudaEventRecord(hp.in_done[b], hp.s_in) != cudaSuccess ||
+      cudaStreamWaitEvent(hp.s_run, hp.in_done[b], 0) != cudaSuccess ||
+      cudaStreamWaitEvent(hp.s_run, hp.out_done[b], 0) != cudaSuccess)
     return OP_E_CUDA;
+  st = op_run(op, hp.d_in[b], hp.d_out[b], hp.s_run);
+  if (st != OP_OK) return st;
+  if (cudaEventRecord(hp.run_done[b], hp.s_run) != cudaSuccess ||
+      cudaStreamWaitEvent(hp.s_out, hp.run_done[b], 0) != cudaSuccess ||
+      cudaMemcpy2DAsync(h_out, op->stride, hp.d_out[b], op->stride, row, op->h,
+                        cudaMemcpyDeviceToHost, hp.s_out) != cudaSuccess ||
+      cudaEventRecord(hp.out_done[b], hp.s_out) != cudaSuccess ||
+      cudaStreamWaitEvent(s, hp.out_done[b], 0) != cudaSuccess)
+    return OP_E_CUDA;
+  return OP_OK;
+}
+
+int op_run_host(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream) {
+  const int st = op_run_host_async(op, h_in, h_out, stream);
+  if (st != OP_OK) return st;
   return op_sync_status(op, stream);
 }
 
@@ -506,9 +571,8 @@ int op_sync_status(op_t *op, void *stream) {
 int op_destroy(op_t *op) {
   if (!op) return OP_OK;
   if (op->ws_owned) cudaFree(op->ws);
+  host_pipe_free(op->hp);
   cudaFree(op->d_err);
-  cudaFree(op->d_stage_in);
-  cudaFree(op->d_stage_out);
   delete op;
   return OP_OK;
 }

@@ -123,22 +123,30 @@ class OilPaint:
         self.run(src, dst, stream)
         return dst
 
+    def _host_ptr(self, a) -> int:
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.uint8 or not a.is_contiguous():
+                raise B.OilPaintError("host buffers must be contiguous uint8 CPU tensors")
+            if a.numel() < self.nbytes:
+                raise B.OilPaintError("host buffer too small")
+            return a.data_ptr()
+        a = np.asarray(a)
+        if a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"] or a.size < self.nbytes:
+            raise B.OilPaintError("host buffers must be contiguous uint8 arrays")
+        return a.ctypes.data
+
     def run_host(self, h_in, h_out, stream=None) -> None:
         """Host buffers in and out (numpy arrays or CPU tensors, ideally pinned);
         synchronous."""
-        def ptr(a):
-            if isinstance(a, torch.Tensor):
-                if a.is_cuda or a.dtype != torch.uint8 or not a.is_contiguous():
-                    raise B.OilPaintError("host buffers must be contiguous uint8 CPU tensors")
-                if a.numel() < self.nbytes:
-                    raise B.OilPaintError("host buffer too small")
-                return a.data_ptr()
-            a = np.asarray(a)
-            if a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"] or a.size < self.nbytes:
-                raise B.OilPaintError("host buffers must be contiguous uint8 arrays")
-            return a.ctypes.data
-        B.check(B.op_run_host(self._h, ptr(h_in), ptr(h_out), _stream_handle(stream)),
-                "op_run_host")
+        B.check(B.op_run_host(self._h, self._host_ptr(h_in), self._host_ptr(h_out),
+                              _stream_handle(stream)), "op_run_host")
+
+    def run_host_async(self, h_in, h_out, stream=None) -> None:
+        """Enqueue the host-buffer filter; consecutive calls overlap one image's
+        copies with another's filter.  `stream` waits for the result: keep both
+        buffers alive (and pinned) until it is synchronised or sync_status()."""
+        B.check(B.op_run_host_async(self._h, self._host_ptr(h_in), self._host_ptr(h_out),
+                                    _stream_handle(stream)), "op_run_host_async")
 
     def sync_status(self, stream=None) -> int:
         return B.op_sync_status(self._h, _stream_handle(stream))

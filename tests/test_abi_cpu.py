@@ -61,6 +61,7 @@ def test_null_handles(lib):
     assert B.op_batch_destroy(None) == B.OP_OK
     assert B.op_run(None, 1, 2, None) == B.OP_E_INVALID
     assert B.op_run_host(None, 1, 2, None) == B.OP_E_INVALID
+    assert B.op_run_host_async(None, 1, 2, None) == B.OP_E_INVALID
     assert B.op_sync_status(None, None) == B.OP_E_INVALID
     assert B.op_workspace_size(None) == 0
     assert B.op_batch_workspace_size(None) == 0
