@@ -22,6 +22,10 @@ import numpy as np
 from . import build as _build
 from . import oilpaint_np  # noqa: F401  (the NumPy oracle module)
 from .oilpaint_np import LEVEL_INTDIV3, LEVEL_PAPER, level_map  # noqa: F401
+
+# mode bit of the C oracle: the section-4 listing as printed (interior pixels
+# only, white excluded from the argmax, no write when no level below L occurs)
+LITERAL = 2
 from .oilpaint_np import oilpaint_buffer as oilpaint_numpy  # noqa: F401
 
 _lib = None
@@ -114,6 +118,6 @@ def view_pixels(buf: np.ndarray, width: int, height: int, stride: int, bpp: int)
 
 
 __all__ = [
-    "LEVEL_PAPER", "LEVEL_INTDIV3", "level_map", "level_of_sum", "num_cpus", "oilpaint",
+    "LEVEL_PAPER", "LEVEL_INTDIV3", "LITERAL", "level_map", "level_of_sum", "num_cpus", "oilpaint",
     "oilpaint_rows", "oilpaint_pixels", "oilpaint_numpy", "oilpaint_np", "view_pixels",
 ]

@@ -80,6 +80,8 @@ def oilpaint_buffer(buf: np.ndarray, width: int, height: int, stride: int, bpp: 
     Only pixel bytes are written; with bpp == 4 the alpha byte is copied from
     the input.  `out` (same size as `buf`) keeps its row padding.
     """
+    if mode not in (LEVEL_PAPER, LEVEL_INTDIV3):
+        raise ValueError("the NumPy oracle implements the two level modes only")
     flat = np.ascontiguousarray(buf).reshape(-1)
     if flat.size < height * stride:
         raise ValueError("buffer too small")

@@ -35,6 +35,23 @@
  * and copied from the input's centre pixel.  Bytes past width*bpp in a row
  * (row padding) are never written.
  *
+ * Literal mode (mode bit ORC_LITERAL) follows the section-4 listing as
+ * printed instead of the readings above:
+ *   - only pixels with r <= x < w-r and r <= y < h-r are visited (the
+ *     listing's loops start at radius and stop radius short of each edge),
+ *     so every window lies inside the image; nothing else is written, and
+ *     nothing at all when w <= 2r or h <= 2r;
+ *   - the level is not clamped: pure white lands on level L, which the
+ *     listing counts (its arrays hold 255 levels, so L <= 254) but whose
+ *     count its argmax, running over levels 0..L-1, never reads;
+ *   - the argmax starts from level 0's count and keeps the first strictly
+ *     larger count, as in step 5; when every level below L is empty (a
+ *     window of white pixels only) the listing's guard skips the write;
+ *   - only the three colour bytes are written.
+ * The listing clears only the first 255 bytes of each 255-entry int array
+ * per pixel; its prose asks for a fresh histogram per pixel, which both
+ * modes use (the two agree whenever L <= 63: levels 0..62 are cleared).
+ *
  * Threads: rows are independent, so they are split across worker threads the
  * way section 5 splits them across parallel_for tasks; every thread owns its
  * histogram and the output does not depend on the thread count.
@@ -47,6 +64,7 @@
 
 #define ORC_LEVEL_PAPER 0u
 #define ORC_LEVEL_INTDIV3 1u
+#define ORC_LITERAL 2u /* mode bit: the listing as printed (see above) */
 
 typedef struct {
   const uint8_t *in;
@@ -59,27 +77,30 @@ typedef struct {
   int status;
 } orc_job_t;
 
-/* Step 3 above. */
+/* Step 3 above (literal mode: not clamped, so white reaches level L). */
 static uint32_t orc_level(uint32_t R, uint32_t G, uint32_t B, uint32_t L, uint32_t mode) {
   uint32_t s = R + G + B;
   uint32_t l;
-  if (mode == ORC_LEVEL_INTDIV3)
+  if (mode & ORC_LEVEL_INTDIV3)
     l = ((s / 3u) * L) / 255u;
   else
     l = (s * L) / 765u;
+  if (mode & ORC_LITERAL) return l;
   return l < L ? l : L - 1u;
 }
 
-/* Steps 1-6 for one output pixel; writes rgb[0..2]. */
-static void orc_pixel(const uint8_t *in, uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp,
-                      int32_t r, uint32_t L, uint32_t mode, uint32_t x, uint32_t y,
-                      uint32_t *count, uint32_t *sumR, uint32_t *sumG, uint32_t *sumB,
-                      uint8_t rgb[3]) {
+/* Steps 1-6 for one output pixel; writes rgb[0..2] and returns 1, or returns
+ * 0 (literal mode, no level below L in the window) without writing.  The
+ * arrays hold L + 1 levels. */
+static int orc_pixel(const uint8_t *in, uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp,
+                     int32_t r, uint32_t L, uint32_t mode, uint32_t x, uint32_t y,
+                     uint32_t *count, uint32_t *sumR, uint32_t *sumG, uint32_t *sumB,
+                     uint8_t rgb[3]) {
   /* step 1 */
-  memset(count, 0, L * sizeof(uint32_t));
-  memset(sumR, 0, L * sizeof(uint32_t));
-  memset(sumG, 0, L * sizeof(uint32_t));
-  memset(sumB, 0, L * sizeof(uint32_t));
+  memset(count, 0, (L + 1u) * sizeof(uint32_t));
+  memset(sumR, 0, (L + 1u) * sizeof(uint32_t));
+  memset(sumG, 0, (L + 1u) * sizeof(uint32_t));
+  memset(sumB, 0, (L + 1u) * sizeof(uint32_t));
   /* step 2 */
   for (int32_t dy = -r; dy <= r; ++dy) {
     for (int32_t dx = -r; dx <= r; ++dx) {
@@ -98,30 +119,41 @@ static void orc_pixel(const uint8_t *in, uint32_t w, uint32_t h, uint32_t stride
   uint32_t best = 0;
   for (uint32_t l = 1; l < L; ++l)
     if (count[l] > count[best]) best = l;
+  if (count[best] == 0) return 0; /* literal mode only: the listing's guard */
   /* step 6 */
   rgb[0] = (uint8_t)(sumR[best] / count[best]);
   rgb[1] = (uint8_t)(sumG[best] / count[best]);
   rgb[2] = (uint8_t)(sumB[best] / count[best]);
+  return 1;
 }
 
 static void *orc_worker(void *arg) {
   orc_job_t *j = (orc_job_t *)arg;
-  uint32_t *bins = (uint32_t *)malloc((size_t)4 * j->L * sizeof(uint32_t));
+  const uint32_t n = j->L + 1u;
+  uint32_t *bins = (uint32_t *)malloc((size_t)4 * n * sizeof(uint32_t));
   if (!bins) {
     j->status = -3;
     return NULL;
   }
-  uint32_t *count = bins, *sumR = bins + j->L, *sumG = bins + 2 * j->L, *sumB = bins + 3 * j->L;
+  uint32_t *count = bins, *sumR = bins + n, *sumG = bins + 2 * n, *sumB = bins + 3 * n;
+  const int literal = (j->mode & ORC_LITERAL) != 0;
+  /* literal mode: the listing's loop bounds, radius .. size-radius-1 */
+  const int64_t r = j->r;
+  const int64_t x_lo = literal ? r : 0, x_hi = literal ? (int64_t)j->w - r : (int64_t)j->w;
+  const int64_t y_lo = literal ? r : 0, y_hi = literal ? (int64_t)j->h - r : (int64_t)j->h;
   for (uint32_t y = j->y_begin; y < j->y_end; y += j->y_step) {
-    for (uint32_t x = 0; x < j->w; ++x) {
+    if ((int64_t)y < y_lo || (int64_t)y >= y_hi) continue;
+    for (int64_t xi = x_lo; xi < x_hi; ++xi) {
+      const uint32_t x = (uint32_t)xi;
       uint8_t rgb[3];
-      orc_pixel(j->in, j->w, j->h, j->stride, j->bpp, j->r, j->L, j->mode, x, y, count, sumR,
-                sumG, sumB, rgb);
+      if (!orc_pixel(j->in, j->w, j->h, j->stride, j->bpp, j->r, j->L, j->mode, x, y, count,
+                     sumR, sumG, sumB, rgb))
+        continue;
       uint8_t *o = j->out + (size_t)y * j->stride + (size_t)x * j->bpp;
       o[0] = rgb[0];
       o[1] = rgb[1];
       o[2] = rgb[2];
-      if (j->bpp == 4) o[3] = j->in[(size_t)y * j->stride + (size_t)x * 4 + 3];
+      if (j->bpp == 4 && !literal) o[3] = j->in[(size_t)y * j->stride + (size_t)x * 4 + 3];
     }
   }
   free(bins);
@@ -135,7 +167,8 @@ static int orc_check(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int3
   if ((uint64_t)stride < (uint64_t)w * bpp) return -1;
   if (r < 0 || r > 1000) return -1;
   if (L < 1 || L > 256) return -1;
-  if (mode != ORC_LEVEL_PAPER && mode != ORC_LEVEL_INTDIV3) return -1;
+  if (mode & ~(ORC_LEVEL_INTDIV3 | ORC_LITERAL)) return -1;
+  if ((mode & ORC_LITERAL) && L > 254) return -1; /* level L must index a 255-entry array */
   return 0;
 }
 
@@ -204,15 +237,17 @@ int orc_oilpaint_pixels(const uint8_t *in, uint32_t w, uint32_t h, uint32_t stri
                         const uint32_t *ys, uint32_t n, uint8_t *rgb) {
   if (!in || (n && (!xs || !ys || !rgb))) return -1;
   if (orc_check(w, h, stride, bpp, r, L, mode)) return -1;
-  uint32_t *bins = (uint32_t *)malloc((size_t)4 * L * sizeof(uint32_t));
+  if (mode & ORC_LITERAL) return -1; /* sampled pixels: the default readings only */
+  const uint32_t nb = L + 1u;
+  uint32_t *bins = (uint32_t *)malloc((size_t)4 * nb * sizeof(uint32_t));
   if (!bins) return -3;
   for (uint32_t k = 0; k < n; ++k) {
     if (xs[k] >= w || ys[k] >= h) {
       free(bins);
       return -1;
     }
-    orc_pixel(in, w, h, stride, bpp, r, L, mode, xs[k], ys[k], bins, bins + L, bins + 2 * L,
-              bins + 3 * L, rgb + 3 * (size_t)k);
+    orc_pixel(in, w, h, stride, bpp, r, L, mode, xs[k], ys[k], bins, bins + nb, bins + 2 * nb,
+              bins + 3 * nb, rgb + 3 * (size_t)k);
   }
   free(bins);
   return 0;
