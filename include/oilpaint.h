@@ -54,6 +54,18 @@ extern "C" {
 /* ---- flags for op_create_ex / op_image_t.flags -------------------------- */
 #define OP_LEVEL_PAPER 0u   /* level = min(floor((R+G+B)*L/765), L-1)        (section 4) */
 #define OP_LEVEL_INTDIV3 1u /* level = min(floor(floor((R+G+B)/3)*L/255), L-1)          */
+/*
+ * OP_LITERAL (flag bit, with either level mode): the section-4 listing as
+ * printed instead of the default readings.  Only pixels at least `radius`
+ * from every edge are written (none when width or height <= 2*radius); the
+ * level is not clamped, so pure white (R+G+B = 765) lands on level L, which
+ * the argmax (levels 0..L-1) never reads; a pixel whose window has no level
+ * below L is not written; only the three colour bytes are written (alpha and
+ * the border keep whatever the output buffer held).  Needs
+ * levels <= OP_LITERAL_MAX_LEVELS (the listing's arrays hold 255 levels).
+ */
+#define OP_LITERAL 2u
+#define OP_LITERAL_MAX_LEVELS 254u
 
 /* ---- limits ------------------------------------------------------------- */
 #define OP_MAX_RADIUS 44   /* 255*(2r+1)^2 must fit the 21-bit per-level channel sums */
@@ -105,7 +117,8 @@ typedef struct {
 op_t *op_create(uint32_t width, uint32_t height, uint32_t stride, int32_t radius, uint32_t levels);
 
 /* op_create_ex -- explicit bytes per pixel (3 or 4, stride >= width*bpp) and
- * flags (OP_LEVEL_PAPER or OP_LEVEL_INTDIV3).  Otherwise as op_create. */
+ * flags (OP_LEVEL_PAPER or OP_LEVEL_INTDIV3, optionally | OP_LITERAL).  Otherwise
+ * as op_create. */
 op_t *op_create_ex(uint32_t width, uint32_t height, uint32_t stride, uint32_t bpp, int32_t radius,
                    uint32_t levels, uint32_t flags);
 

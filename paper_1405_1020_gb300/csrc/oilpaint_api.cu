@@ -233,7 +233,8 @@ bool valid_image(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int32_t 
   if (static_cast<uint64_t>(stride) < static_cast<uint64_t>(w) * bpp) return false;
   if (r < 0 || r > OP_MAX_RADIUS) return false;
   if (L < 1 || L > OP_MAX_LEVELS) return false;
-  if (flags != OP_LEVEL_PAPER && flags != OP_LEVEL_INTDIV3) return false;
+  if (flags & ~(OP_LEVEL_INTDIV3 | OP_LITERAL)) return false;
+  if ((flags & OP_LITERAL) && L > OP_LITERAL_MAX_LEVELS) return false;
   return true;
 }
 
@@ -379,7 +380,9 @@ op_t *op_create_ex(uint32_t width, uint32_t height, uint32_t stride, uint32_t bp
   op->device = dev;
   op->di = di;
   op->cfg = cfg;
-  op->tile_h = effective_tile_h(op->cfg, width, height, radius, levels, di);
+  op->tile_h = effective_tile_h(op->cfg, width,
+                                std::max(1u, opk::output_window(width, height, radius, flags).rows()),
+                                radius, levels, di);
   op->ppitch = packed_pitch(width);
   if (cudaMalloc(&op->d_err, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(op->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
@@ -410,7 +413,9 @@ int op_set_config(op_t *op, const op_config_t *cfg) {
   const int st = check_config(*cfg, op->r, op->L, op->di);
   if (st != OP_OK) return st;
   op->cfg = *cfg;
-  op->tile_h = effective_tile_h(op->cfg, op->w, op->h, op->r, op->L, op->di);
+  op->tile_h = effective_tile_h(
+      op->cfg, op->w, std::max(1u, opk::output_window(op->w, op->h, op->r, op->flags).rows()),
+      op->r, op->L, op->di);
   op->map_valid = false;
   return OP_OK;
 }
@@ -498,13 +503,16 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   d.variant = static_cast<uint32_t>(g.variant);
   d.kcols = static_cast<uint32_t>(g.kcols);
   d.xshift = g.xshift;
+  const opk::Window win = opk::output_window(op->w, op->h, op->r, op->flags);
+  opk::set_window(d, win);
+  if (win.rows() == 0u) return OP_OK;  // literal mode: no pixel is r from every edge
   const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, g.boxw);
   const size_t smem = smem_of(g, c, op->r, op->L);
   const int pack_grid = static_cast<int>(std::min<uint32_t>(op->h, 8u * op->di.sms));
   cudaError_t e = opk::launch_pack_single(d, pack_grid, s);
   if (e != cudaSuccess) return OP_E_CUDA;
   if (op->prof_ev && cudaEventRecord(op->prof_ev, s) != cudaSuccess) return OP_E_CUDA;
-  const dim3 grid(d.tiles_x, (op->h + d.tile_h - 1) / d.tile_h);
+  const dim3 grid(d.tiles_x, (win.rows() + d.tile_h - 1) / d.tile_h);
   e = opk::launch_tile(g.nt, g.kcols, g.variant, d, op->map, rc, grid, smem, op->d_err,
                        kWaitTimeoutNs, s);
   return e == cudaSuccess ? OP_OK : OP_E_CUDA;
@@ -770,7 +778,8 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
       if (it != g_tune.end()) th = it->second.tile_h;
     }
     if (th == 0) th = std::max<uint32_t>(64u, 16u * static_cast<uint32_t>(im.radius));
-    th = std::min(th, im.height);
+    const uint32_t rows = opk::output_window(im.width, im.height, im.radius, im.flags).rows();
+    th = std::max(1u, std::min(th, rows));
     tile_h[i] = th;
     geo[i] = opk::image_geometry(nt, kc, im.radius, im.levels, im.width);
     // per step a tile slides one window column (4r + 2 bin updates) and
@@ -816,12 +825,14 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     d.variant = static_cast<uint32_t>(g.variant);
     d.kcols = static_cast<uint32_t>(g.kcols);
     d.xshift = g.xshift;
+    const opk::Window win = opk::output_window(d.w, d.h, d.r, d.mode);
+    opk::set_window(d, win);
     const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc.ch);
     if (st != OP_OK) return st;
     hd[k] = d;
     htp[k] = static_cast<uint32_t>(tiles);
     hrp[k] = static_cast<uint32_t>(rows);
-    tiles += static_cast<uint64_t>(d.tiles_x) * ((d.h + d.tile_h - 1) / d.tile_h);
+    tiles += static_cast<uint64_t>(d.tiles_x) * ((win.rows() + d.tile_h - 1) / d.tile_h);
     rows += d.h;
     poff = align_up(poff + static_cast<size_t>(d.ppitch) * d.h * 4u, kAlign);
   }

@@ -61,13 +61,23 @@ struct __align__(16) ImgDesc {
   const CUtensorMap *tmap;  // device copy of the packed image's tensor map (batch path)
   uint32_t w, h, stride, bpp;
   int32_t r;
-  uint32_t L, mode, ppitch;  // mode: 0 = paper level, 1 = divide by 3 first
+  uint32_t L, mode, ppitch;  // mode bit 0: divide by 3 first; bit 1: literal
   uint32_t tile_h, tiles_x, boxw, variant;
   uint32_t ostride;  // output row pitch in bytes
   uint32_t kcols;    // 1: one column per thread (word format 0); 2 or 4: difference
-                     // histograms over kcols columns per thread (word format 1)
+                     // histograms over kcols columns per thread (word formats 1, 2)
   int32_t xshift;    // x of the first tile (0, or -3..0 so that x0 - r is 4-aligned)
+  // output window: columns [ox0, ox1), rows [oy0, oy1) (the whole image, or
+  // in literal mode the pixels at least r from every edge); tiles cover the
+  // rows from oy0
+  int32_t ox0, ox1, oy0, oy1;
 };
+
+constexpr uint32_t kModeIntDiv3 = 1u;
+// Literal mode: the section-4 listing as printed -- white (level L) is
+// counted outside the levels the argmax reads, nothing is written when no
+// level below L occurs, and only the colour bytes are written.
+constexpr uint32_t kModeLiteral = 2u;
 
 // The difference-histogram path needs r <= 15 (64-bit bins) and L <= 32
 // (5-bit level field next to the valid bit).
@@ -289,15 +299,19 @@ __device__ __forceinline__ void cnt_addsub(uint32_t addr_a, uint32_t da, uint32_
 
 // ------------------------------------------------------------ pack prepass
 
-// Section 4's intensity level of one pixel, clamped to L-1.
+// Section 4's intensity level of one pixel, clamped to L-1 (literal mode:
+// not clamped, so pure white gives L).
 __device__ __forceinline__ uint32_t level_of(uint32_t R, uint32_t G, uint32_t B, uint32_t L,
                                              uint32_t mode) {
   const uint32_t s = R + G + B;
-  const uint32_t l = mode ? ((s / 3u) * L) / 255u : (s * L) / 765u;
+  const uint32_t l = (mode & kModeIntDiv3) ? ((s / 3u) * L) / 255u : (s * L) / 765u;
+  if (mode & kModeLiteral) return l;
   return l < L ? l : L - 1u;
 }
 
-// Word format 0: level << 24 | R << 16 | G << 8 | B.
+// Word format 0: level << 24 | R << 16 | G << 8 | B.  In literal mode a
+// white pixel carries level L, the histogram's scratch level, which the
+// argmax never reads.
 __device__ __forceinline__ uint32_t pack_word(uint32_t R, uint32_t G, uint32_t B, uint32_t L,
                                               uint32_t mode) {
   return (level_of(R, G, B, L, mode) << 24) | (R << 16) | (G << 8) | B;
@@ -310,15 +324,18 @@ __device__ __forceinline__ uint32_t pack_word(uint32_t R, uint32_t G, uint32_t B
 //   10..17 R, 20..27 B, 28..31 G & 15.
 __device__ __forceinline__ uint32_t pack_word_delta(uint32_t R, uint32_t G, uint32_t B,
                                                     uint32_t L, uint32_t mode) {
-  return 1u | (level_of(R, G, B, L, mode) << 1) | ((G >> 4) << 6) | (R << 10) | (B << 20) |
-         ((G & 0xFu) << 28);
+  const uint32_t l = level_of(R, G, B, L, mode);
+  if (l >= L) return 0u;  // literal mode: level L is never read, so it adds nothing
+  return 1u | (l << 1) | ((G >> 4) << 6) | (R << 10) | (B << 20) | ((G & 0xFu) << 28);
 }
 
 // Word format 2 (L <= 32, 16 <= r <= 44): R @0..7 | level @8..12 |
 // B @13..20 | G @21..28 | valid @29 (see DeltaOpsB).
 __device__ __forceinline__ uint32_t pack_word_delta_b(uint32_t R, uint32_t G, uint32_t B,
                                                       uint32_t L, uint32_t mode) {
-  return R | (level_of(R, G, B, L, mode) << 8) | (B << 13) | (G << 21) | (1u << 29);
+  const uint32_t l = level_of(R, G, B, L, mode);
+  if (l >= L) return 0u;  // literal mode: level L adds nothing
+  return R | (l << 8) | (B << 13) | (G << 21) | (1u << 29);
 }
 
 // Packs row y of image d with threads tid, tid+nthr, ...  Rows whose pixels
@@ -779,7 +796,7 @@ __device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc,
 __device__ __forceinline__ void store_pixel(const ImgDesc &d, int x, int y, uint32_t R,
                                             uint32_t G, uint32_t B, uint32_t alpha) {
   uint8_t *o = d.out + static_cast<size_t>(y) * d.ostride + static_cast<size_t>(x) * d.bpp;
-  if (d.bpp == 4) {
+  if (d.bpp == 4 && !(d.mode & kModeLiteral)) {
     const uint32_t v = R | (G << 8) | (B << 16) | (alpha << 24);
     if ((reinterpret_cast<uintptr_t>(o) & 3u) == 0) {
       *reinterpret_cast<uint32_t *>(o) = v;
@@ -936,7 +953,8 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
         const int l = e - 2 * r - 1;  // leaving row
         const bool do_add = e >= 0 && e < H;
         const bool do_rm = l >= 0 && l >= E0 && l < H;
-        const bool out_now = s >= 2 * r && active;  // output row e - r is complete
+        // output row e - r is complete and column xa is in the output window
+        const bool out_now = s >= 2 * r && xa >= d.ox0 && xa < d.ox1;
         const uint32_t *pe = rowe + jl;
         const uint32_t *pl = rowl + jl;
         // the alpha byte is fetched before the updates so its latency is hidden
@@ -966,12 +984,15 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
               m = lv;
             }
           }
-          uint32_t lo, hi, cnt, R, G, B;
-          h.bin(m, lo, hi);
-          unpack_bin<VAR>(lo, hi, VAR == kVarB ? best : 0u, cnt, R, G, B);
-          const uint32_t mul = VAR == kVarA ? rcp_of(cnt) : 0u;
-          store_pixel(d, xa, e - r, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
-                      div_mean<VAR>(B, cnt, mul), alpha);
+          // best == 0: no level below L in the window (literal mode only)
+          if (best != 0u) {
+            uint32_t lo, hi, cnt, R, G, B;
+            h.bin(m, lo, hi);
+            unpack_bin<VAR>(lo, hi, VAR == kVarB ? best : 0u, cnt, R, G, B);
+            const uint32_t mul = VAR == kVarA ? rcp_of(cnt) : 0u;
+            store_pixel(d, xa, e - r, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
+                        div_mean<VAR>(B, cnt, mul), alpha);
+          }
         }
       });
 }
@@ -1171,7 +1192,6 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
   constexpr int NH = NB + K - 1;
   const int t = threadIdx.x;
   const int r = d.r;
-  const int W = static_cast<int>(d.w);
   const uint32_t L = d.L;
   const int xa = x0 + K * t;
   const int xs = x0 - r;  // a multiple of 4 by the choice of d.xshift
@@ -1210,7 +1230,7 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           const int x = xa + i;
-          alpha[i] = (out_now && d.bpp == 4 && x >= 0 && x < W) ? load_alpha(d, x, y) : 0u;
+          alpha[i] = (out_now && d.bpp == 4 && x >= d.ox0 && x < d.ox1) ? load_alpha(d, x, y) : 0u;
         }
         if (SPLIT) {
           if (rm)
@@ -1247,9 +1267,10 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           const int x = xa + i;
-          if (x < 0 || x >= W) continue;
+          if (x < d.ox0 || x >= d.ox1) continue;
           const uint32_t m = 31u - (best[i] & 31u);
           const uint32_t cnt = best[i] >> CSH;
+          if (cnt == 0u) continue;  // no level below L (literal mode only)
           uint64_t v = 0;
 #pragma unroll
           for (int j = 0; j < NB + i; ++j) {

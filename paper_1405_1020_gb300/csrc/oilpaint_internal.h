@@ -106,6 +106,31 @@ inline size_t tile_smem_bytes(size_t hist, const RingCfg &rc) {
          hist;
 }
 
+// Output window of an image: the whole image, or with the literal-mode bit
+// (2) the pixels at least r from every edge -- empty when w <= 2r or h <= 2r.
+struct Window {
+  int32_t x0, x1, y0, y1;
+  uint32_t rows() const { return y1 > y0 ? static_cast<uint32_t>(y1 - y0) : 0u; }
+};
+
+inline Window output_window(uint32_t w, uint32_t h, int r, uint32_t flags) {
+  Window o{0, static_cast<int32_t>(w), 0, static_cast<int32_t>(h)};
+  if (flags & kModeLiteral) {
+    if (static_cast<int64_t>(w) > 2ll * r && static_cast<int64_t>(h) > 2ll * r)
+      o = Window{r, static_cast<int32_t>(w) - r, r, static_cast<int32_t>(h) - r};
+    else
+      o = Window{0, 0, 0, 0};
+  }
+  return o;
+}
+
+inline void set_window(ImgDesc &d, const Window &o) {
+  d.ox0 = o.x0;
+  d.ox1 = o.x1;
+  d.oy0 = o.y0;
+  d.oy1 = o.y1;
+}
+
 // Launchers; each returns cudaSuccess or the launch error.
 cudaError_t launch_pack_single(const ImgDesc &d, int grid, cudaStream_t s);
 // nt threads per CTA (32, 64, 96, 128); kcols 1 (one column per thread,

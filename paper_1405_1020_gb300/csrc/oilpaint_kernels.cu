@@ -58,8 +58,8 @@ __global__ void __launch_bounds__(NT, 1)
   init_cta(sm, rc);
   uint32_t ctr = 0;
   const int x0 = static_cast<int>(blockIdx.x) * NT;
-  const int y0 = static_cast<int>(blockIdx.y * d.tile_h);
-  const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
+  const int y0 = d.oy0 + static_cast<int>(blockIdx.y * d.tile_h);
+  const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
   run_tile<NT, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(NT, 1)
   init_cta(sm, rc);
   uint32_t ctr = 0;
   const int x0 = d.xshift + static_cast<int>(blockIdx.x) * NT * K;
-  const int y0 = static_cast<int>(blockIdx.y * d.tile_h);
-  const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
+  const int y0 = d.oy0 + static_cast<int>(blockIdx.y * d.tile_h);
+  const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
   run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
@@ -113,8 +113,8 @@ __global__ void __launch_bounds__(NT, 1)
     const ImgDesc d = descs[img];
     const int tw = NT * static_cast<int>(d.kcols);
     const int x0 = d.xshift + static_cast<int>(local % d.tiles_x) * tw;
-    const int y0 = static_cast<int>((local / d.tiles_x) * d.tile_h);
-    const int y1 = min(y0 + static_cast<int>(d.tile_h), static_cast<int>(d.h));
+    const int y0 = d.oy0 + static_cast<int>((local / d.tiles_x) * d.tile_h);
+    const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
     bool ok;
     if (K > 1 && d.kcols == static_cast<uint32_t>(K)) {
       constexpr int KD = K > 1 ? K : 2;

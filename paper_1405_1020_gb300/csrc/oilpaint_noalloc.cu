@@ -105,7 +105,8 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (!d_in || !d_out || width < 1 || height < 1 || width > OP_MAX_DIM || height > OP_MAX_DIM ||
       (bpp != 3 && bpp != 4) || static_cast<uint64_t>(stride) < static_cast<uint64_t>(width) * bpp ||
       radius < 0 || radius > OP_MAX_RADIUS || levels < 1 || levels > OP_MAX_LEVELS ||
-      (flags != OP_LEVEL_PAPER && flags != OP_LEVEL_INTDIV3))
+      (flags & ~(OP_LEVEL_INTDIV3 | OP_LITERAL)) ||
+      ((flags & OP_LITERAL) && levels > OP_LITERAL_MAX_LEVELS))
     return OP_E_INVALID;
   const size_t bytes = static_cast<size_t>(height) * stride;
   const uintptr_t a = reinterpret_cast<uintptr_t>(d_in), b = reinterpret_cast<uintptr_t>(d_out);
@@ -149,11 +150,14 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   d.mode = flags;
   d.ppitch = ppitch;
   d.tiles_x = g.tiles_x;
+  const opk::Window win = opk::output_window(width, height, radius, flags);
+  opk::set_window(d, win);
+  if (win.rows() == 0u) return OP_OK;  // literal mode: no pixel is r from every edge
   if (cfg.tile_h) {
-    d.tile_h = std::min(cfg.tile_h, height);
+    d.tile_h = std::min(cfg.tile_h, win.rows());
   } else {
     const int occ = std::max(1, opk::tile_occupancy(g.nt, false, g.kcols, g.variant, smem));
-    d.tile_h = pick_tile_h(height, d.tiles_x, radius, static_cast<uint64_t>(occ) * sms);
+    d.tile_h = pick_tile_h(win.rows(), d.tiles_x, radius, static_cast<uint64_t>(occ) * sms);
   }
   d.boxw = boxw;
   d.variant = static_cast<uint32_t>(g.variant);
@@ -176,7 +180,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (cudaMemsetAsync(sc.err, 0, sizeof(uint32_t), s) != cudaSuccess) return OP_E_CUDA;
   const int pack_grid = static_cast<int>(std::min<uint32_t>(height, 8u * static_cast<uint32_t>(sms)));
   if (opk::launch_pack_single(d, pack_grid, s) != cudaSuccess) return OP_E_CUDA;
-  const dim3 grid(d.tiles_x, (height + d.tile_h - 1) / d.tile_h);
+  const dim3 grid(d.tiles_x, (win.rows() + d.tile_h - 1) / d.tile_h);
   if (opk::launch_tile(g.nt, g.kcols, g.variant, d, map, rc, grid, smem, sc.err, kWaitTimeoutNs,
                        s) != cudaSuccess)
     return OP_E_CUDA;
