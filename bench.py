@@ -289,8 +289,12 @@ def run_ours(args):
         if tr.get("workload") == WORKLOAD and tr.get("kernel_source_hash") == _kernel_hash():
             traffic = tr.get("bytes_per_launch")
     launch = op.config()
-    kernel = ("tile_delta_kernel" if launch["cols_per_thread"] > 1 and LEVELS <= 32
-              else "tile_plain_kernel")
+    if launch.get("path", 0) == 1:
+        kernel = "tile_cols_kernel"
+    elif launch["cols_per_thread"] > 1 and LEVELS <= 32:
+        kernel = "tile_delta_kernel"
+    else:
+        kernel = "tile_plain_kernel"
     roofline = {"bound": "alu", "achieved": round(ach_tops, 3), "peak": round(peak_tops, 3),
                 "unit": "Tops/s", "frac": round(ach_tops / peak_tops, 4), "traffic": traffic,
                 "kernel": kernel, "kernel_ms": round(f_ms, 4),

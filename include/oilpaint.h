@@ -94,9 +94,17 @@ typedef struct op_s op_t;
  *                   need levels <= 32, else the configuration is refused
  *                   (OP_E_UNSUPPORTED) by op_set_config; a batch runs its
  *                   other images on the one-column path.
+ *   path            0: histograms kept per thread (the fields above);
+ *                   1: column histograms with the levels across a warp's
+ *                   lanes (NEXT-1 of the design notes' scope table: work per
+ *                   pixel independent of r): a CTA keeps one histogram per
+ *                   image column of its tile and halo, each warp sweeps
+ *                   32 * cols_per_thread output columns of every row
+ *                   (cols_per_thread 1 or 2), tile_w / cols_per_thread =
+ *                   32, 64 or 128 threads; needs levels <= 32.
  * The halo copy of a tile is at most 256 columns wide: tile_w + 2r + up to
- * 3 columns for one column per thread, K * (threads - 1 + ceil((2r+K-1)/K)
- * + 1) rounded up to 4 for K columns per thread.
+ * 3 columns for one column per thread and for path 1, K * (threads - 1 +
+ * ceil((2r+K-1)/K) + 1) rounded up to 4 for K columns per thread.
  */
 typedef struct {
   uint32_t tile_w;
@@ -104,6 +112,7 @@ typedef struct {
   uint32_t chunk_rows;
   uint32_t prefetch;
   uint32_t cols_per_thread;
+  uint32_t path;
 } op_config_t;
 
 /*

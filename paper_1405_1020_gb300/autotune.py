@@ -34,7 +34,12 @@ def candidates(radius: int, levels: int, tile_hs=(0,)) -> list[dict]:
     for nt, cpt, ch, pf, th in itertools.product((32, 64, 96, 128), (1, 2, 4), (2, 4, 8, 16), (1, 2),
                                                   tile_hs):
         out.append({"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
-                    "cols_per_thread": cpt})
+                    "cols_per_thread": cpt, "path": 0})
+    if levels <= 32:  # column histograms, levels across lanes
+        for nt, cpt, ch, pf, th in itertools.product((32, 64, 128), (1, 2), (1, 2, 4), (1, 2),
+                                                      tile_hs):
+            out.append({"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
+                        "cols_per_thread": cpt, "path": 1})
     return out
 
 

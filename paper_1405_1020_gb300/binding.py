@@ -58,15 +58,15 @@ class OilPaintError(RuntimeError):
 class op_config_t(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_uint32), ("tile_h", ctypes.c_uint32),
                 ("chunk_rows", ctypes.c_uint32), ("prefetch", ctypes.c_uint32),
-                ("cols_per_thread", ctypes.c_uint32)]
+                ("cols_per_thread", ctypes.c_uint32), ("path", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
     @classmethod
     def make(cls, tile_w: int, tile_h: int = 0, chunk_rows: int = 8, prefetch: int = 2,
-             cols_per_thread: int = 1):
-        return cls(tile_w, tile_h, chunk_rows, prefetch, cols_per_thread)
+             cols_per_thread: int = 1, path: int = 0):
+        return cls(tile_w, tile_h, chunk_rows, prefetch, cols_per_thread, path)
 
 
 class op_image_t(ctypes.Structure):

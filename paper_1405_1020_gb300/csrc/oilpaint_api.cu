@@ -104,6 +104,7 @@ uint32_t threads_of(const op_config_t &c) {
 
 // Range checks that need no device.
 bool config_in_range(const op_config_t &c) {
+  if (c.path > 1u) return false;
   if (c.cols_per_thread != 0 && c.cols_per_thread != 1 && c.cols_per_thread != 2 &&
       c.cols_per_thread != 4)
     return false;
@@ -111,17 +112,19 @@ bool config_in_range(const op_config_t &c) {
   if (c.tile_w % cpt) return false;
   const uint32_t nt = c.tile_w / cpt;
   if (nt != 32 && nt != 64 && nt != 96 && nt != 128) return false;
+  if (c.path == 1u && (cpt == 4u || nt == 96u)) return false;  // 1, 2 or 4 warps x 32 or 64
   if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4) return false;
   return c.tile_h <= OP_MAX_DIM;
 }
 
 opk::Geometry geometry_of(const op_config_t &c, int r, uint32_t L, uint32_t w) {
-  return opk::image_geometry(threads_of(c), cols_per_thread(c), r, L, w);
+  return opk::image_geometry(static_cast<int>(c.path), threads_of(c), cols_per_thread(c), r, L,
+                             w);
 }
 
 size_t smem_of(const opk::Geometry &g, const op_config_t &c, int r, uint32_t L) {
   const RingCfg rc = opk::make_ring(r, c.chunk_rows, c.prefetch, g.boxw);
-  return opk::tile_smem_bytes(opk::hist_bytes(g.nt, g.kcols, L, g.variant), rc);
+  return opk::tile_smem_bytes(opk::geometry_hist_bytes(g, r, L), rc);
 }
 
 size_t smem_for(const op_config_t &c, int r, uint32_t L) {
@@ -162,7 +165,9 @@ size_t batch_smem(const op_config_t &c, const BatchNeeds &n) {
 int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
   if (!config_in_range(c)) return OP_E_INVALID;
   const opk::Geometry g = geometry_of(c, r, L, 1u);
-  if (g.kcols != cols_per_thread(c)) return OP_E_UNSUPPORTED;  // no difference path here
+  // the path and columns asked for must apply (K columns and the column
+  // histograms need L <= 32)
+  if (g.path != static_cast<int>(c.path) || g.kcols != cols_per_thread(c)) return OP_E_UNSUPPORTED;
   if (g.boxw > 256u) return OP_E_UNSUPPORTED;
   if (smem_of(g, c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
   return OP_OK;
@@ -221,8 +226,7 @@ uint32_t effective_tile_h(const op_config_t &c, uint32_t w, uint32_t h, int r, u
                           const DevInfo &di) {
   if (c.tile_h) return std::min(c.tile_h, h);
   const opk::Geometry g = geometry_of(c, r, L, w);
-  const int occ = std::max(1, opk::tile_occupancy(g.nt, false, g.kcols, g.variant,
-                                                  smem_of(g, c, r, L)));
+  const int occ = std::max(1, opk::geometry_occupancy(g, smem_of(g, c, r, L)));
   return auto_tile_h(h, g.tiles_x, r, static_cast<uint64_t>(occ) * di.sms);
 }
 
@@ -503,6 +507,8 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   d.variant = static_cast<uint32_t>(g.variant);
   d.kcols = static_cast<uint32_t>(g.kcols);
   d.xshift = g.xshift;
+  d.fmt = g.fmt;
+  d.path = static_cast<uint32_t>(g.path);
   const opk::Window win = opk::output_window(op->w, op->h, op->r, op->flags);
   opk::set_window(d, win);
   if (win.rows() == 0u) return OP_OK;  // literal mode: no pixel is r from every edge
@@ -655,6 +661,10 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
     g_last_error = OP_E_INVALID;
     return nullptr;
   }
+  if (c.path != 0u) {  // the persistent kernel keeps histograms per thread
+    g_last_error = OP_E_UNSUPPORTED;
+    return nullptr;
+  }
   const BatchNeeds needs = batch_needs(c, max_radius, max_levels);
   if (needs.boxw > 256u || batch_smem(c, needs) > di.smem_optin - 1024u) {
     g_last_error = OP_E_UNSUPPORTED;
@@ -781,7 +791,7 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     const uint32_t rows = opk::output_window(im.width, im.height, im.radius, im.flags).rows();
     th = std::max(1u, std::min(th, rows));
     tile_h[i] = th;
-    geo[i] = opk::image_geometry(nt, kc, im.radius, im.levels, im.width);
+    geo[i] = opk::image_geometry(0, nt, kc, im.radius, im.levels, im.width);
     // per step a tile slides one window column (4r + 2 bin updates) and
     // K - 1 difference columns (4 each); per output row it scans K argmaxes
     const double r = im.radius, k = geo[i].kcols;
@@ -825,6 +835,8 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     d.variant = static_cast<uint32_t>(g.variant);
     d.kcols = static_cast<uint32_t>(g.kcols);
     d.xshift = g.xshift;
+    d.fmt = g.fmt;
+    d.path = 0u;
     const opk::Window win = opk::output_window(d.w, d.h, d.r, d.mode);
     opk::set_window(d, win);
     const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc.ch);

@@ -67,6 +67,9 @@ struct __align__(16) ImgDesc {
   uint32_t kcols;    // 1: one column per thread (word format 0); 2 or 4: difference
                      // histograms over kcols columns per thread (word formats 1, 2)
   int32_t xshift;    // x of the first tile (0, or -3..0 so that x0 - r is 4-aligned)
+  uint32_t fmt;      // packed word format: 0 one column per thread, 1 (r <= 15) and 2
+                     // (r > 15) difference and column histograms
+  uint32_t path;     // 0: histograms per thread; 1: column histograms, levels across lanes
   // output window: columns [ox0, ox1), rows [oy0, oy1) (the whole image, or
   // in literal mode the pixels at least r from every edge); tiles cover the
   // rows from oy0
@@ -347,7 +350,7 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
   const uint8_t *src = d.in + static_cast<size_t>(y) * d.stride;
   uint32_t *dst = d.packed + static_cast<size_t>(y) * d.ppitch;
   const uint32_t L = d.L, mode = d.mode, w = d.w;
-  const uint32_t fmt = d.kcols > 1 ? (d.variant == kVarA ? 1u : 2u) : 0u;
+  const uint32_t fmt = d.fmt;
   auto word = [&](uint32_t R, uint32_t G, uint32_t B) {
     return fmt == 1u   ? pack_word_delta(R, G, B, L, mode)
            : fmt == 2u ? pack_word_delta_b(R, G, B, L, mode)
@@ -671,8 +674,9 @@ struct DeltaOpsB {
   uint32_t scratch;  // the thread's scratch sums bin
   uint32_t cd;       // count address = (sums address >> 1) + cd
 
+  // level field (bits 8..12) times NT * 8 bytes
   __device__ __forceinline__ uint32_t saddr(uint32_t base, uint32_t w) const {
-    return base + (w & 0x1F00u) * (NT / 32u);
+    return base + (((w & 0x1F00u) * NT) >> 5);
   }
   __device__ __forceinline__ uint32_t caddr(uint32_t s) const { return (s >> 1) + cd; }
 
@@ -1294,6 +1298,180 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
             store_pixel(d, x, y, R / cnt, G / cnt, B / cnt, alpha[i]);
           }
         }
+      });
+}
+
+// Shared-memory atomic adds (the start-window histograms of the column path).
+__device__ __forceinline__ void red_add64(uint32_t addr, uint32_t lo, uint32_t hi) {
+  asm volatile(
+      "{\n\t.reg .u64 v;\n\t"
+      "mov.b64 v, {%1, %2};\n\t"
+      "red.shared.add.u64 [%0], v;\n\t}" ::"r"(addr),
+      "r"(lo), "r"(hi)
+      : "memory");
+}
+
+__device__ __forceinline__ void red_add32(uint32_t addr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Shared-memory layout of the column path after the ring (all sizes in
+// bytes, Lp = L | 1 levels per histogram so that a column's histogram is an
+// odd number of 8-byte bins long and 32 lanes updating 32 neighbouring
+// columns spread over the banks):
+//   colhist  [ncols][Lp] 8-byte bins  (ncols = T + 2r image columns)
+//   winners  [NW][32]    8-byte bins  (each warp's last 32 winning bins)
+//   scratch  [NT]        8-byte bins  (same-level folds)
+// and for variant B the column histograms' counts (4 bytes, same layout at
+// half the stride).
+__host__ __device__ constexpr uint32_t cols_levels(uint32_t L) { return L | 1u; }
+__host__ __device__ constexpr uint32_t cols_sums_bytes(uint32_t ncols, uint32_t nw, uint32_t nt,
+                                                       uint32_t L) {
+  return (ncols * cols_levels(L) + nw * 32u + nt) * 8u;
+}
+
+// Column histograms with the levels across a warp's lanes (r <= 44, L <= 32;
+// VAR A bins and word format 1 for r <= 15, VAR B and format 2 above).  A CTA
+// of NW warps owns the tile [x0, x0 + T) x [y0, y1), T = NW * 32 * TWK, and
+// keeps one histogram per image column x0 - r .. x0 + T + r - 1 over the
+// window's 2r + 1 rows.  Per row step:
+//   A. all threads slide the column histograms down one row (+ the entering
+//      pixel, - the leaving one: 2 bin updates per column);
+//   B. warp w sums the 2r + 1 column histograms of its first window, then
+//      sweeps its 32 * TWK output columns of the row: lane l holds level l of
+//      the current window in registers; an output is one max-reduction over
+//      the lanes of (count, 31 - l) keys (the lowest level wins ties), after
+//      which the winning lane stores its bin in slot k of 32, and moving one
+//      column right adds the entering column's histogram and subtracts the
+//      leaving one (one 64-bit add and subtract per lane).  After 32 outputs
+//      lane k reads slot k and all lanes compute their means and store
+//      together.
+// The sweep's work per output pixel does not depend on r.  Pixels outside the image
+// are TMA zero fill, whose delta is zero.
+template <int NW, int TWK, int VAR>
+__device__ bool run_tile_cols(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
+                              const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
+                              uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
+                              bool tmap_global = false) {
+  constexpr int NT = 32 * NW;
+  constexpr int TW = 32 * TWK;  // output columns per warp
+  constexpr int T = NW * TW;
+  constexpr uint32_t FULL = 0xFFFFFFFFu;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int r = d.r;
+  const uint32_t L = d.L;
+  const uint32_t Lp = cols_levels(L);
+  const uint32_t S = Lp * 8u;  // bytes between two columns' histograms
+  const int ncols = T + 2 * r;
+  const int xs = x0 - r;  // a multiple of 4 by the choice of d.xshift
+  const int E0 = y0 - r;
+  const int nsteps = (y1 - y0) + 2 * r;
+  const uint32_t colb = sm.sums;
+  const uint32_t winb = colb + static_cast<uint32_t>(ncols) * S;  // 32 winner slots per warp
+  const uint32_t scrb = winb + NW * 32u * 8u;
+  const uint32_t sums_end = scrb + NT * 8u;
+  // VAR B counts: the same layout at half the stride
+  const uint32_t cbase = (sums_end + 127u) & ~127u;
+  const uint32_t cd = cbase - (colb >> 1);
+  const uint8_t *gbase = sm.ring_ptr - sm.ring;  // generic address of shared address 0
+  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<1>, DeltaOpsB<1>>::type;
+  Ops ops;
+  ops.scratch = scrb + static_cast<uint32_t>(t) * 8u;
+  if constexpr (VAR == kVarB) ops.cd = cd;
+  // zero the column histograms (all Lp levels)
+  {
+    const uint32_t words = static_cast<uint32_t>(ncols) * Lp * 2u;
+    for (uint32_t i = t; i < words; i += NT) sts_zero32(colb + i * 4u);
+    if (VAR == kVarB)
+      for (uint32_t i = t; i < words / 2u; i += NT) sts_zero32(cbase + i * 4u);
+  }
+  const bool lv_ok = static_cast<uint32_t>(lane) < L;
+  const uint32_t tag = 31u - static_cast<uint32_t>(lane);
+  const uint32_t mywin = winb + static_cast<uint32_t>(warp) * 32u * 8u;
+
+  return ring_pass(
+      d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
+      y1, [&](int s, const uint32_t *rowe, const uint32_t *rowl) {
+        const bool rm = s >= 2 * r + 1;  // the leaving row was added by this tile
+        // A. column histograms, then this warp's start window
+        for (int j = t; j < ncols; j += NT) {
+          const uint32_t base = colb + static_cast<uint32_t>(j) * S;
+          if (rm)
+            ops.addsub(base, rowe[j], rowl[j]);
+          else
+            ops.add(base, rowe[j]);
+        }
+        __syncthreads();
+        if (s >= 2 * r) {
+          // B. sweep this warp's outputs of row y
+          const int y = E0 + s - r;
+          const int xw = x0 + warp * TW;
+          const uint8_t *cp = gbase + colb + static_cast<uint32_t>(lane) * 8u;
+          const uint8_t *cc = gbase + (colb >> 1) + cd + static_cast<uint32_t>(lane) * 4u;
+          // the window of column xw: the sum of its 2r + 1 column histograms
+          uint64_t acc = 0;
+          uint32_t cnt = 0;
+          if (lv_ok) {
+            for (int j = warp * TW; j <= warp * TW + 2 * r; ++j) {
+              acc += *reinterpret_cast<const uint64_t *>(cp + static_cast<uint32_t>(j) * S);
+              if (VAR == kVarB)
+                cnt += *reinterpret_cast<const uint32_t *>(cc + static_cast<uint32_t>(j) * (S / 2u));
+            }
+          }
+          // the winning lane leaves its bin for output k in slot k
+          uint64_t *wslot = reinterpret_cast<uint64_t *>(const_cast<uint8_t *>(gbase + mywin));
+          uint32_t Wk = 0;
+#pragma unroll
+          for (int bt = 0; bt < TWK; ++bt) {
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+              const uint32_t lo = static_cast<uint32_t>(acc);
+              const uint32_t hi = static_cast<uint32_t>(acc >> 32);
+              uint32_t key = 0u;
+              if (lv_ok) key = (VAR == kVarA ? (lo << 22) : (cnt << 5)) | tag;
+              const uint32_t kmax = __reduce_max_sync(FULL, key);
+              const int m = static_cast<int>(31u - (kmax & 31u));
+              if (lane == m) wslot[k] = acc;
+              if (lane == k) Wk = kmax;
+              // move one column right: + column x + r + 1, - column x - r
+              const int kk = bt * 32 + k;
+              if (kk + 1 < TW && lv_ok) {
+                const uint32_t jin = static_cast<uint32_t>(warp * TW + kk + 2 * r + 1);
+                const uint32_t jout = static_cast<uint32_t>(warp * TW + kk);
+                acc += *reinterpret_cast<const uint64_t *>(cp + jin * S);
+                acc -= *reinterpret_cast<const uint64_t *>(cp + jout * S);
+                if (VAR == kVarB) {
+                  cnt += *reinterpret_cast<const uint32_t *>(cc + jin * (S / 2u));
+                  cnt -= *reinterpret_cast<const uint32_t *>(cc + jout * (S / 2u));
+                }
+              }
+            }
+            // lane k of this batch owns output xw + 32 bt + k
+            __syncwarp();
+            const uint64_t wv = wslot[lane];
+            __syncwarp();  // slots are rewritten by the next batch
+            const uint32_t Wlo = static_cast<uint32_t>(wv), Whi = static_cast<uint32_t>(wv >> 32);
+            const int x = xw + bt * 32 + lane;
+            const uint32_t c = VAR == kVarA ? (Wk >> 22) : (Wk >> 5);  // the winner's count
+            if (x >= d.ox0 && x < d.ox1 && c != 0u) {
+              const uint32_t alpha = d.bpp == 4 ? load_alpha(d, x, y) : 0u;
+              if (VAR == kVarA) {
+                const uint32_t R = (Wlo >> 10) & 0x3FFFFu;
+                const uint32_t G = (Wlo >> 28) | ((Whi & 0x3FFFu) << 4);
+                const uint32_t B = Whi >> 14;
+                const uint32_t mul = rcp_of(c);
+                store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul),
+                            __umulhi(B << 1, mul), alpha);
+              } else {
+                const uint32_t R = Wlo & 0x1FFFFFu;
+                const uint32_t G = (Wlo >> 21) | ((Whi & 0x3FFu) << 11);
+                const uint32_t B = (Whi >> 10) & 0x1FFFFFu;
+                store_pixel(d, x, y, R / c, G / c, B / c, alpha);
+              }
+            }
+          }
+        }
+        __syncthreads();  // the next step's A rewrites what B read
       });
 }
 

@@ -55,10 +55,13 @@ inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
   return (w + 3u) & ~3u;
 }
 
-// Launch geometry of one image: threads per CTA, columns per thread (2 or 4
-// only where the difference-histogram path applies), tile width, the x of
-// the first tile, tiles per row and the halo box width.
+// Launch geometry of one image: path (0 histograms per thread, 1 column
+// histograms), threads per CTA, columns per thread (path 0: 2 or 4 only where
+// the difference-histogram path applies; path 1: outputs per warp / 32), tile
+// width, the x of the first tile, tiles per row, the halo box width, the
+// histogram variant and the packed word format.
 struct Geometry {
+  int path;
   uint32_t nt;
   int kcols;
   uint32_t tile_w;
@@ -66,25 +69,45 @@ struct Geometry {
   uint32_t tiles_x;
   uint32_t boxw;
   int variant;
+  uint32_t fmt;
 };
 
-inline Geometry image_geometry(uint32_t nt, int kcols_wanted, int r, uint32_t L, uint32_t w) {
+inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, uint32_t L,
+                               uint32_t w) {
   Geometry g;
   g.nt = nt;
-  g.kcols = (kcols_wanted > 1 && delta_eligible(r, L)) ? kcols_wanted : 1;
-  g.tile_w = nt * static_cast<uint32_t>(g.kcols);
   g.variant = variant_for_radius(r);
-  if (g.kcols > 1) {
-    // first tile at x0 = xshift with x0 - r a multiple of 4
+  g.path = (path == 1 && delta_eligible(r, L)) ? 1 : 0;
+  if (g.path == 1) {
+    g.kcols = kcols_wanted == 2 ? 2 : 1;
+    g.tile_w = nt * static_cast<uint32_t>(g.kcols);
     g.xshift = (r & 3) ? (r & 3) - 4 : 0;
-    g.boxw = delta_box_width(nt, g.kcols, r);
+    g.boxw = (g.tile_w + 2u * static_cast<uint32_t>(r) + 3u) & ~3u;
   } else {
-    g.xshift = 0;
-    g.boxw = box_width(nt, r);
+    g.kcols = (kcols_wanted > 1 && delta_eligible(r, L)) ? kcols_wanted : 1;
+    g.tile_w = nt * static_cast<uint32_t>(g.kcols);
+    if (g.kcols > 1) {
+      // first tile at x0 = xshift with x0 - r a multiple of 4
+      g.xshift = (r & 3) ? (r & 3) - 4 : 0;
+      g.boxw = delta_box_width(nt, g.kcols, r);
+    } else {
+      g.xshift = 0;
+      g.boxw = box_width(nt, r);
+    }
   }
+  g.fmt = (g.path == 1 || g.kcols > 1) ? (g.variant == kVarA ? 1u : 2u) : 0u;
   g.tiles_x = static_cast<uint32_t>((static_cast<int64_t>(w) - g.xshift + g.tile_w - 1) /
                                     g.tile_w);
   return g;
+}
+
+// Shared bytes of the column path's histograms (column sums, start windows,
+// scratch; variant B adds the counts after a 128-byte boundary).
+inline size_t cols_hist_bytes(const Geometry &g, int r, uint32_t L) {
+  const uint32_t ncols = g.tile_w + 2u * static_cast<uint32_t>(r);
+  const size_t sums = cols_sums_bytes(ncols, g.nt / 32u, g.nt, L);
+  if (g.variant == kVarA) return sums;
+  return ((sums + 127u) & ~static_cast<size_t>(127u)) + sums / 2u;
 }
 
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
@@ -92,6 +115,7 @@ inline Geometry image_geometry(uint32_t nt, int kcols_wanted, int r, uint32_t L,
 // more where the window histogram is split, of L levels per thread plus one
 // scratch bin, bins of 8 bytes (variant A) or 8 + 4 bytes (variant B)).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
+  // (column path: cols_hist_bytes)
   if (kcols > 1) {
     const size_t nh = static_cast<size_t>(kcols) + (split_for(kcols, variant) ? 1u : 0u);
     return (nh * L + 1u) * nt * (variant == kVarA ? 8u : 12u);
@@ -134,7 +158,9 @@ inline void set_window(ImgDesc &d, const Window &o) {
 // Launchers; each returns cudaSuccess or the launch error.
 cudaError_t launch_pack_single(const ImgDesc &d, int grid, cudaStream_t s);
 // nt threads per CTA (32, 64, 96, 128); kcols 1 (one column per thread,
-// histogram variant `variant`) or 2 / 4 (difference histograms)
+// histogram variant `variant`) or 2 / 4 (difference histograms); with
+// d.path == 1 the column-histogram kernel with nt / 32 warps sweeping
+// 32 * kcols outputs each
 cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
                         const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
                         uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
@@ -153,5 +179,16 @@ cudaError_t set_tile_smem_limit(size_t bytes);
 // Resident CTAs per SM of the plain (kcols 1: variant), difference-histogram
 // (kcols 2, 4) or persistent kernel.
 int tile_occupancy(uint32_t nt, bool persistent, int kcols, int variant, size_t smem);
+// ... of the column-histogram kernel: nt = 32 * warps, twk = outputs per warp / 32.
+int tile_occupancy_cols(uint32_t nt, int twk, int variant, size_t smem);
+
+// Histogram bytes and resident CTAs of an image's single-image kernel.
+inline size_t geometry_hist_bytes(const Geometry &g, int r, uint32_t L) {
+  return g.path == 1 ? cols_hist_bytes(g, r, L) : hist_bytes(g.nt, g.kcols, L, g.variant);
+}
+inline int geometry_occupancy(const Geometry &g, size_t smem) {
+  return g.path == 1 ? tile_occupancy_cols(g.nt, g.kcols, g.variant, smem)
+                     : tile_occupancy(g.nt, false, g.kcols, g.variant, smem);
+}
 
 }  // namespace opk

@@ -77,6 +77,20 @@ __global__ void __launch_bounds__(NT, 1)
   run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
+template <int NW, int TWK, int VAR>
+__global__ void __launch_bounds__(32 * NW, 1)
+    tile_cols_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d, const RingCfg rc,
+                     uint32_t *err, uint64_t timeout_ns) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const SmemMap sm = carve_smem(smem, rc, 0u);
+  init_cta(sm, rc);
+  uint32_t ctr = 0;
+  const int x0 = d.xshift + static_cast<int>(blockIdx.x) * (32 * NW * TWK);
+  const int y0 = d.oy0 + static_cast<int>(blockIdx.y * d.tile_h);
+  const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
+  run_tile_cols<NW, TWK, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+}
+
 // K = 1: every image on the one-column path; K = 2 or 4: images with
 // d.kcols == K on the difference-histogram path, the others on the
 // one-column path.  Shared memory is sized by the host for the largest.
@@ -188,9 +202,37 @@ static void delta_n(int k, const ImgDesc &d, const CUtensorMap &map, const RingC
   }
 }
 
+template <int NW>
+static void cols_n(int twk, int variant, const ImgDesc &d, const CUtensorMap &map,
+                   const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns,
+                   cudaStream_t s) {
+  const bool a = variant == kVarA;
+  if (twk == 2) {
+    if (a)
+      tile_cols_kernel<NW, 2, kVarA><<<grid, 32 * NW, smem, s>>>(map, d, rc, err, timeout_ns);
+    else
+      tile_cols_kernel<NW, 2, kVarB><<<grid, 32 * NW, smem, s>>>(map, d, rc, err, timeout_ns);
+  } else {
+    if (a)
+      tile_cols_kernel<NW, 1, kVarA><<<grid, 32 * NW, smem, s>>>(map, d, rc, err, timeout_ns);
+    else
+      tile_cols_kernel<NW, 1, kVarB><<<grid, 32 * NW, smem, s>>>(map, d, rc, err, timeout_ns);
+  }
+}
+
 cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
                         const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
                         uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  if (d.path == 1u) {
+    if (kcols != 1 && kcols != 2) return cudaErrorInvalidValue;
+    switch (nt) {
+      case 32: cols_n<1>(kcols, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+      case 64: cols_n<2>(kcols, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+      case 128: cols_n<4>(kcols, variant, d, map, rc, grid, smem, err, timeout_ns, s); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
   switch (nt) {
     case 32:
@@ -277,9 +319,22 @@ static cudaError_t set_limit_n(int b) {
   return cudaFuncSetAttribute(persistent_kernel<NT, 4>, a, b);
 }
 
+template <int NW>
+static cudaError_t set_limit_cols(int b) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(tile_cols_kernel<NW, 1, kVarA>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_cols_kernel<NW, 1, kVarB>, a, b)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(tile_cols_kernel<NW, 2, kVarA>, a, b)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tile_cols_kernel<NW, 2, kVarB>, a, b);
+}
+
 cudaError_t set_tile_smem_limit(size_t bytes) {
   const int b = static_cast<int>(bytes);
   cudaError_t e;
+  if ((e = set_limit_cols<1>(b)) != cudaSuccess) return e;
+  if ((e = set_limit_cols<2>(b)) != cudaSuccess) return e;
+  if ((e = set_limit_cols<4>(b)) != cudaSuccess) return e;
   if ((e = set_limit_n<32>(b)) != cudaSuccess) return e;
   if ((e = set_limit_n<64>(b)) != cudaSuccess) return e;
   if ((e = set_limit_n<96>(b)) != cudaSuccess) return e;
@@ -307,6 +362,25 @@ static int occupancy_n(bool persistent, int kcols, int variant, size_t smem) {
                             : occ_of(tile_delta_kernel<NT, 2, kVarB>, NT, smem);
   return variant == kVarA ? occ_of(tile_plain_kernel<NT, kVarA>, NT, smem)
                           : occ_of(tile_plain_kernel<NT, kVarB>, NT, smem);
+}
+
+template <int NW>
+static int occupancy_cols(int twk, int variant, size_t smem) {
+  const bool a = variant == kVarA;
+  if (twk == 2)
+    return a ? occ_of(tile_cols_kernel<NW, 2, kVarA>, 32 * NW, smem)
+             : occ_of(tile_cols_kernel<NW, 2, kVarB>, 32 * NW, smem);
+  return a ? occ_of(tile_cols_kernel<NW, 1, kVarA>, 32 * NW, smem)
+           : occ_of(tile_cols_kernel<NW, 1, kVarB>, 32 * NW, smem);
+}
+
+int tile_occupancy_cols(uint32_t nt, int twk, int variant, size_t smem) {
+  switch (nt) {
+    case 32: return occupancy_cols<1>(twk, variant, smem);
+    case 64: return occupancy_cols<2>(twk, variant, smem);
+    case 128: return occupancy_cols<4>(twk, variant, smem);
+    default: return 0;
+  }
 }
 
 int tile_occupancy(uint32_t nt, bool persistent, int kcols, int variant, size_t smem) {

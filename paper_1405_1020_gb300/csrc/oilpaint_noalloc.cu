@@ -129,11 +129,12 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   const int cpt = (cfg.cols_per_thread == 2 || cfg.cols_per_thread == 4)
                       ? static_cast<int>(cfg.cols_per_thread)
                       : 1;
-  const opk::Geometry g = opk::image_geometry(cfg.tile_w / static_cast<uint32_t>(cpt), cpt,
+  const opk::Geometry g = opk::image_geometry(static_cast<int>(cfg.path),
+                                              cfg.tile_w / static_cast<uint32_t>(cpt), cpt,
                                               radius, levels, width);
   const uint32_t boxw = g.boxw;
   const opk::RingCfg rc = opk::make_ring(radius, cfg.chunk_rows, cfg.prefetch, boxw);
-  const size_t smem = opk::tile_smem_bytes(opk::hist_bytes(g.nt, g.kcols, levels, g.variant), rc);
+  const size_t smem = opk::tile_smem_bytes(opk::geometry_hist_bytes(g, radius, levels), rc);
 
   opk::ImgDesc d{};
   d.in = d_in;
@@ -156,13 +157,15 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (cfg.tile_h) {
     d.tile_h = std::min(cfg.tile_h, win.rows());
   } else {
-    const int occ = std::max(1, opk::tile_occupancy(g.nt, false, g.kcols, g.variant, smem));
+    const int occ = std::max(1, opk::geometry_occupancy(g, smem));
     d.tile_h = pick_tile_h(win.rows(), d.tiles_x, radius, static_cast<uint64_t>(occ) * sms);
   }
   d.boxw = boxw;
   d.variant = static_cast<uint32_t>(g.variant);
   d.kcols = static_cast<uint32_t>(g.kcols);
   d.xshift = g.xshift;
+  d.fmt = g.fmt;
+  d.path = static_cast<uint32_t>(g.path);
 
   auto fn = encode_fn();
   if (!fn) return OP_E_CUDA;

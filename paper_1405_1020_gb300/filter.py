@@ -63,7 +63,8 @@ def _config(cfg) -> B.op_config_t:
         return cfg
     d = dict(cfg)
     return B.op_config_t.make(d.get("tile_w", 128), d.get("tile_h", 0), d.get("chunk_rows", 8),
-                              d.get("prefetch", 2), d.get("cols_per_thread", 1))
+                              d.get("prefetch", 2), d.get("cols_per_thread", 1),
+                              d.get("path", 0))
 
 
 class OilPaint:

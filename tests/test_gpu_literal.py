@@ -45,11 +45,11 @@ def check(img, r, L, bpp=3, pad=0, mode=0, config=None):
 
 @pytest.mark.parametrize("r,L", [(0, 20), (1, 1), (2, 20), (5, 7), (15, 20), (15, 32), (16, 20),
                                  (20, 32), (9, 64), (15, 254), (44, 20), (3, 2)])
-@pytest.mark.parametrize("cpt", [1, 2, 4])
-def test_literal_matches_oracle(r, L, cpt):
+@pytest.mark.parametrize("cpt,path", [(1, 0), (2, 0), (4, 0), (1, 1), (2, 1)])
+def test_literal_matches_oracle(r, L, cpt, path):
     img = whitened(120, 211, seed=r * 31 + L)
     for bpp, pad, nt in ((3, 1, 32), (4, 8, 64)):
-        cfg = {"tile_w": nt * cpt, "cols_per_thread": cpt, "chunk_rows": 4}
+        cfg = {"tile_w": nt * cpt, "cols_per_thread": cpt, "chunk_rows": 4, "path": path}
         try:
             check(img, r, L, bpp, pad, 0, cfg)
         except B.OilPaintError as e:

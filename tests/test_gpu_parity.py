@@ -194,6 +194,41 @@ def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
         assert boxw > 256 or smem > 226 * 1024, (cfg, r, L, smem)
 
 
+def _column_path_cases(n=48, seed=13):
+    """The column-histogram path (path 1, L <= 32): 1, 2 or 4 warps sweeping
+    32 or 64 columns each, both bin variants (r <= 15 and above), every
+    r mod 4, widths around the tile width."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n):
+        w = int(rng.choice([1, 2, 5, 31, 33, 63, 64, 65, 127, 128, 129, 200, 257, 400]))
+        h = int(rng.choice([1, 2, 3, 9, 17, 64, 150]))
+        r = int(rng.integers(0, 16)) if k < 32 else int(rng.integers(16, 45))
+        L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32]))
+        bpp = int(rng.choice([3, 4]))
+        pad = int(rng.choice([0, 1, 4, 13]))
+        mode = int(rng.integers(0, 2))
+        twk = int(rng.choice([1, 2]))
+        nt = int(rng.choice([32, 64, 128]))
+        cfg = {"tile_w": nt * twk, "tile_h": int(rng.choice([0, 1, 3, 16, 64])),
+               "chunk_rows": int(rng.choice([1, 2, 3, 8])), "prefetch": int(rng.integers(1, 3)),
+               "cols_per_thread": twk, "path": 1}
+        cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
+    return cases
+
+
+@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _column_path_cases())
+def test_fuzz_column_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
+    img = synth.camera_like(h, w, seed=1300 + k, npoly=12, rad_range=(1, 60)) if k % 2 else \
+        synth.uniform_rgb(h, w, seed=1300 + k)
+    try:
+        check_case(img, r, L, bpp, pad, mode, cfg)
+    except B.OilPaintError as e:
+        # refused only when the halo box is wider than 256 columns
+        assert e.status == B.OP_E_UNSUPPORTED, e
+        assert cfg["tile_w"] + 2 * r + 3 > 256, (cfg, r)
+
+
 # ---- edge cases --------------------------------------------------------------
 
 @pytest.mark.parametrize("w,h,r,L", [
