@@ -31,7 +31,7 @@ def candidates(radius: int, levels: int, tile_hs=(0,)) -> list[dict]:
     prefetch depth x tile height; configurations the library refuses (halo
     wider than 256 columns, shared memory) are skipped when timed."""
     out = []
-    for nt, cpt, ch, pf, th in itertools.product((32, 64, 96, 128), (1, 2, 4), (2, 4, 8, 16), (1, 2),
+    for nt, cpt, ch, pf, th in itertools.product((32, 64, 96, 128), (1, 2, 4), (1, 2, 4, 8, 16), (1, 2),
                                                   tile_hs):
         out.append({"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
                     "cols_per_thread": cpt, "path": 0})

@@ -113,7 +113,7 @@ def run(steps: int = 10, warmup: int = 3, n: int = 64, config=None) -> dict:
         "plain_mpix_s": round(total_px / ms_plain / 1e3, 1),
         "batched_mpix_s": round(total_px / ms_graph / 1e3, 1),
         "speedup_vs_plain": round(ms_plain / ms_graph, 3),
-        "launches_plain": 2 * n, "launches_batched": 2,
+        "launches_plain": 2 * n, "launches_batched": 4 if max_r > 15 else 2,
         "identical_outputs": identical, "config": cfg,
     }
 

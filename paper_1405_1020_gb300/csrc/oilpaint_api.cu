@@ -14,6 +14,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "oilpaint.h"
 #include "oilpaint_internal.h"
 
@@ -87,6 +89,14 @@ int device_info(int dev, DevInfo *out) {
   *out = di;
   return OP_OK;
 }
+
+// NVTX range over one host call (a no-op unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ------------------------------------------------------------ configs
 
@@ -473,6 +483,7 @@ static int ensure_workspace(op_t *op) {
 }
 
 int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
+  NvtxRange nvtx("op_run");
   if (!op || !d_in || !d_out) return OP_E_INVALID;
   const size_t bytes = static_cast<size_t>(op->h) * op->stride;
   if (ranges_overlap(d_in, d_out, bytes)) return OP_E_INVALID;
@@ -525,6 +536,7 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
 }
 
 int op_run_host_async(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *stream) {
+  NvtxRange nvtx("op_run_host_async");
   if (!op || !h_in || !h_out) return OP_E_INVALID;
   const size_t bytes = static_cast<size_t>(op->h) * op->stride;
   if (ranges_overlap(h_in, h_out, bytes)) return OP_E_INVALID;
@@ -610,11 +622,22 @@ struct op_batch_s {
   int device;
   DevInfo di;
   op_config_t cfg;
-  RingCfg rc;
-  size_t smem;
-  int grid_persist, grid_pack;
+  // Images of radius <= 15 (8-byte bins) and above (12-byte bins) run as two
+  // groups, each one persistent launch with its own shared-memory size, grid,
+  // ticket queue and tables, so the small-radius group is not held to the
+  // occupancy of the large one.  The second group is launched on a side
+  // stream forked from the caller's, so it fills the first group's tail.
+  int groups;  // 1 when max_r <= 15, else 2
+  RingCfg rc[2];
+  size_t smem[2];
+  int grid_persist[2];
+  int grid_pack;
+  uint32_t gn[2] = {0, 0};
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   // workspace layout
-  size_t off_ctrl, off_hdr, off_descs, off_maps, off_tile_prefix, off_row_prefix, off_packed, total;
+  size_t off_ctrl, off_hdr, off_descs[2], off_maps, off_tile_prefix[2], off_row_prefix[2],
+      off_packed, total;
   size_t stage_bytes;  // hdr .. row_prefix, copied in one transfer
   uint8_t *ws = nullptr;
   bool ws_owned = false;
@@ -651,9 +674,30 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
   if (cfg) {
     c = *cfg;
   } else {
-    st = pick_config(max_radius, max_levels, di, &c);
-    if (st != OP_OK) {
-      g_last_error = st;
+    // Batch default: the first of a preference list whose every group fits.
+    // A mixed batch shares one shape across all its radii and level counts,
+    // so the single-image tuning table (one image of the largest radius and
+    // level count) is not what it needs: on GB300 the 64-image mixed batch
+    // ran fastest with 64 threads x 2 columns (a smaller histogram per CTA
+    // than 4 columns) and 2-row halo chunks.
+    static const uint32_t prefs[][2] = {{64, 2}, {32, 2}, {32, 4}, {64, 1}, {32, 1}};
+    bool found = false;
+    for (const auto &p : prefs) {
+      c = op_config_t{p[0] * p[1], 0, 2, 1, p[1], 0};
+      bool fits = true;
+      for (int g = 0; g < (max_radius > opk::kMaxRadiusA ? 2 : 1) && fits; ++g) {
+        const BatchNeeds nd = batch_needs(
+            c, g ? max_radius : std::min(max_radius, static_cast<int32_t>(opk::kMaxRadiusA)),
+            max_levels);
+        fits = nd.boxw <= 256u && batch_smem(c, nd) <= di.smem_optin - 1024u;
+      }
+      if (fits) {
+        found = true;
+        break;
+      }
+    }
+    if (!found) {
+      g_last_error = OP_E_UNSUPPORTED;
       return nullptr;
     }
   }
@@ -665,10 +709,16 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
     g_last_error = OP_E_UNSUPPORTED;
     return nullptr;
   }
-  const BatchNeeds needs = batch_needs(c, max_radius, max_levels);
-  if (needs.boxw > 256u || batch_smem(c, needs) > di.smem_optin - 1024u) {
-    g_last_error = OP_E_UNSUPPORTED;
-    return nullptr;
+  const int groups = max_radius > opk::kMaxRadiusA ? 2 : 1;
+  const int group_r[2] = {std::min(max_radius, static_cast<int32_t>(opk::kMaxRadiusA)),
+                          max_radius};
+  BatchNeeds needs[2];
+  for (int g = 0; g < groups; ++g) {
+    needs[g] = batch_needs(c, group_r[g], max_levels);
+    if (needs[g].boxw > 256u || batch_smem(c, needs[g]) > di.smem_optin - 1024u) {
+      g_last_error = OP_E_UNSUPPORTED;
+      return nullptr;
+    }
   }
   op_batch_t *b = new (std::nothrow) op_batch_t();
   if (!b) {
@@ -682,38 +732,49 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
   b->device = dev;
   b->di = di;
   b->cfg = c;
-  b->rc = opk::make_ring(max_radius, c.chunk_rows, c.prefetch, needs.boxw);
-  b->smem = batch_smem(c, needs);
-  const int occ = opk::tile_occupancy(threads_of(c), true, cols_per_thread(c), -1, b->smem);
-  if (occ < 1) {
-    delete b;
-    g_last_error = OP_E_UNSUPPORTED;
-    return nullptr;
+  b->groups = groups;
+  for (int g = 0; g < groups; ++g) {
+    b->rc[g] = opk::make_ring(group_r[g], c.chunk_rows, c.prefetch, needs[g].boxw);
+    b->smem[g] = batch_smem(c, needs[g]);
+    const int occ = opk::tile_occupancy(threads_of(c), true, cols_per_thread(c), -1, b->smem[g]);
+    if (occ < 1) {
+      delete b;
+      g_last_error = OP_E_UNSUPPORTED;
+      return nullptr;
+    }
+    b->grid_persist[g] = occ * di.sms;
   }
-  b->grid_persist = occ * di.sms;
   b->grid_pack = 8 * di.sms;
   size_t o = 0;
-  b->off_ctrl = o;  // queue counter, error word, timeout diagnostic record (words 8..23)
+  b->off_ctrl = o;  // queue counters (words 0, 2), error word (1), timeout record (8..23)
   o = align_up(o + 24 * sizeof(uint32_t), kAlign);
-  b->off_hdr = o;
-  o = align_up(o + sizeof(uint32_t), kAlign);
-  b->off_descs = o;
-  o = align_up(o + static_cast<size_t>(max_images) * sizeof(ImgDesc), kAlign);
+  b->off_hdr = o;  // image count of each group
+  o = align_up(o + 2 * sizeof(uint32_t), kAlign);
+  for (int g = 0; g < 2; ++g) {
+    b->off_descs[g] = o;
+    o = align_up(o + static_cast<size_t>(max_images) * sizeof(ImgDesc), kAlign);
+  }
   b->off_maps = o;
   o = align_up(o + static_cast<size_t>(max_images) * sizeof(CUtensorMap), kAlign);
-  b->off_tile_prefix = o;
-  o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
-  b->off_row_prefix = o;
-  o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
+  for (int g = 0; g < 2; ++g) {
+    b->off_tile_prefix[g] = o;
+    o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
+  }
+  for (int g = 0; g < 2; ++g) {
+    b->off_row_prefix[g] = o;
+    o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
+  }
   b->off_packed = o;
   b->stage_bytes = o - b->off_hdr;
   o = align_up(o + static_cast<size_t>(max_pixels) * 4u + static_cast<size_t>(max_images) * kAlign,
                kAlign);
   b->total = o;
   if (cudaMallocHost(&b->h_stage, b->stage_bytes) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->stage_done, cudaEventDisableTiming) != cudaSuccess) {
-    cudaFreeHost(b->h_stage);
-    delete b;
+      cudaEventCreateWithFlags(&b->stage_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
+    op_batch_destroy(b);
     g_last_error = OP_E_NOMEM;
     return nullptr;
   }
@@ -747,6 +808,7 @@ int op_batch_set_workspace(op_batch_t *b, void *d_ws, size_t bytes) {
 }
 
 int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stream) {
+  NvtxRange nvtx("op_batch_set");
   if (!b || (n && !images) || n > b->max_images) return OP_E_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!b->ws) {
@@ -800,19 +862,31 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     order[i] = i;
   }
   if (padded > b->max_pixels) return OP_E_INVALID;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](uint32_t a, uint32_t c) { return tile_cost[a] > tile_cost[c]; });
+  // group of each image (radius above 15 -> group 1), then most expensive
+  // tiles first within a group
+  auto group_of = [&](uint32_t i) {
+    return b->groups == 2 && images[i].radius > opk::kMaxRadiusA ? 1 : 0;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
+    const int ga = group_of(a), gc = group_of(c);
+    return ga != gc ? ga < gc : tile_cost[a] > tile_cost[c];
+  });
   // the previous op_batch_set's copy must have left the pinned staging buffer
   if (cudaEventSynchronize(b->stage_done) != cudaSuccess) return OP_E_CUDA;
+  auto host = [&](size_t off) { return b->h_stage + (off - b->off_hdr); };
   uint32_t *hn = reinterpret_cast<uint32_t *>(b->h_stage);
-  ImgDesc *hd = reinterpret_cast<ImgDesc *>(b->h_stage + (b->off_descs - b->off_hdr));
-  CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(b->h_stage + (b->off_maps - b->off_hdr));
-  uint32_t *htp = reinterpret_cast<uint32_t *>(b->h_stage + (b->off_tile_prefix - b->off_hdr));
-  uint32_t *hrp = reinterpret_cast<uint32_t *>(b->h_stage + (b->off_row_prefix - b->off_hdr));
+  CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(host(b->off_maps));
   const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(b->ws + b->off_maps);
   size_t poff = b->off_packed;
-  uint64_t tiles = 0, rows = 0;
+  uint32_t gcount[2] = {0, 0};
+  uint64_t gtiles[2] = {0, 0}, grows[2] = {0, 0};
   for (uint32_t k = 0; k < n; ++k) {
+    const int grp = group_of(order[k]);
+    const uint32_t q = gcount[grp]++;  // index within its group
+    ImgDesc *hd = reinterpret_cast<ImgDesc *>(host(b->off_descs[grp]));
+    uint32_t *htp = reinterpret_cast<uint32_t *>(host(b->off_tile_prefix[grp]));
+    uint32_t *hrp = reinterpret_cast<uint32_t *>(host(b->off_row_prefix[grp]));
+    uint64_t &tiles = gtiles[grp], &rows = grows[grp];
     const op_image_t &im = images[order[k]];
     ImgDesc d{};
     d.in = im.in;
@@ -839,19 +913,26 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     d.path = 0u;
     const opk::Window win = opk::output_window(d.w, d.h, d.r, d.mode);
     opk::set_window(d, win);
-    const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc.ch);
+    const int st =
+        encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc[0].ch);
     if (st != OP_OK) return st;
-    hd[k] = d;
-    htp[k] = static_cast<uint32_t>(tiles);
-    hrp[k] = static_cast<uint32_t>(rows);
+    hd[q] = d;
+    htp[q] = static_cast<uint32_t>(tiles);
+    hrp[q] = static_cast<uint32_t>(rows);
     tiles += static_cast<uint64_t>(d.tiles_x) * ((win.rows() + d.tile_h - 1) / d.tile_h);
     rows += d.h;
     poff = align_up(poff + static_cast<size_t>(d.ppitch) * d.h * 4u, kAlign);
   }
-  if (tiles >= 0xFFFFFFFFull || poff > b->total) return OP_E_INVALID;
-  htp[n] = static_cast<uint32_t>(tiles);
-  hrp[n] = static_cast<uint32_t>(rows);
-  *hn = n;
+  if (poff > b->total) return OP_E_INVALID;
+  for (int g = 0; g < 2; ++g) {
+    if (gtiles[g] >= 0xFFFFFFFFull || grows[g] >= 0xFFFFFFFFull) return OP_E_INVALID;
+    reinterpret_cast<uint32_t *>(host(b->off_tile_prefix[g]))[gcount[g]] =
+        static_cast<uint32_t>(gtiles[g]);
+    reinterpret_cast<uint32_t *>(host(b->off_row_prefix[g]))[gcount[g]] =
+        static_cast<uint32_t>(grows[g]);
+    hn[g] = gcount[g];
+    b->gn[g] = gcount[g];
+  }
   if (!b->ctrl_clean) {
     if (cudaMemsetAsync(b->ws + b->off_ctrl, 0, 24 * sizeof(uint32_t), s) != cudaSuccess)
       return OP_E_CUDA;
@@ -866,22 +947,41 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
 }
 
 int op_batch_run(op_batch_t *b, void *stream) {
+  NvtxRange nvtx("op_batch_run");
   if (!b || !b->ws) return OP_E_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t *ctrl = reinterpret_cast<uint32_t *>(b->ws + b->off_ctrl);
-  const uint32_t *d_n = reinterpret_cast<const uint32_t *>(b->ws + b->off_hdr);
-  const ImgDesc *descs = reinterpret_cast<const ImgDesc *>(b->ws + b->off_descs);
-  const uint32_t *tp = reinterpret_cast<const uint32_t *>(b->ws + b->off_tile_prefix);
-  const uint32_t *rp = reinterpret_cast<const uint32_t *>(b->ws + b->off_row_prefix);
-  // Fixed grids; the image count and the tables are read from device memory,
-  // so the launches do not depend on the current batch and a captured graph
-  // stays valid across op_batch_set calls.
-  cudaError_t e = opk::launch_pack_batch(descs, rp, d_n, ctrl, b->grid_pack, s);
-  if (e != cudaSuccess) return OP_E_CUDA;
-  e = opk::launch_persistent(threads_of(b->cfg), cols_per_thread(b->cfg), descs, tp, d_n, ctrl,
-                             b->rc, b->max_L,
-                             b->grid_persist, b->smem, ctrl + 1, kWaitTimeoutNs, s);
-  return e == cudaSuccess ? OP_OK : OP_E_CUDA;
+  const uint32_t *hdr = reinterpret_cast<const uint32_t *>(b->ws + b->off_hdr);
+  auto descs = [&](int g) { return reinterpret_cast<const ImgDesc *>(b->ws + b->off_descs[g]); };
+  auto tp = [&](int g) { return reinterpret_cast<const uint32_t *>(b->ws + b->off_tile_prefix[g]); };
+  auto rp = [&](int g) { return reinterpret_cast<const uint32_t *>(b->ws + b->off_row_prefix[g]); };
+  uint32_t *queue[2] = {ctrl + 0, ctrl + 2};
+  // Fixed grids; the image counts and the tables are read from device
+  // memory, so the launches do not depend on the current batch and a
+  // captured graph stays valid across op_batch_set calls.
+  for (int g = 0; g < b->groups; ++g)
+    if (opk::launch_pack_batch(descs(g), rp(g), hdr + g, queue[g], b->grid_pack, s) !=
+        cudaSuccess)
+      return OP_E_CUDA;
+  const uint32_t nt = threads_of(b->cfg);
+  const int k = cols_per_thread(b->cfg);
+  if (b->groups == 2) {
+    // the large-radius group first, on the side stream
+    if (cudaEventRecord(b->fork, s) != cudaSuccess ||
+        cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
+      return OP_E_CUDA;
+    if (opk::launch_persistent(nt, k, descs(1), tp(1), hdr + 1, queue[1], b->rc[1], b->max_L,
+                               b->grid_persist[1], b->smem[1], ctrl + 1, kWaitTimeoutNs,
+                               b->side) != cudaSuccess)
+      return OP_E_CUDA;
+    if (cudaEventRecord(b->join, b->side) != cudaSuccess) return OP_E_CUDA;
+  }
+  if (opk::launch_persistent(nt, k, descs(0), tp(0), hdr, queue[0], b->rc[0], b->max_L,
+                             b->grid_persist[0], b->smem[0], ctrl + 1, kWaitTimeoutNs,
+                             s) != cudaSuccess)
+    return OP_E_CUDA;
+  if (b->groups == 2 && cudaStreamWaitEvent(s, b->join, 0) != cudaSuccess) return OP_E_CUDA;
+  return OP_OK;
 }
 
 int op_batch_capture(op_batch_t *b, void *stream) {
@@ -912,6 +1012,7 @@ int op_batch_capture(op_batch_t *b, void *stream) {
 }
 
 int op_batch_launch_graph(op_batch_t *b, void *stream) {
+  NvtxRange nvtx("op_batch_launch_graph");
   if (!b || !b->exec) return OP_E_INVALID;
   return cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? OP_OK
                                                                                       : OP_E_CUDA;
@@ -935,6 +1036,12 @@ int op_batch_destroy(op_batch_t *b) {
   if (!b) return OP_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->side) {
+    cudaStreamSynchronize(b->side);
+    cudaStreamDestroy(b->side);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
   if (b->stage_done) cudaEventDestroy(b->stage_done);
   if (b->ws_owned) cudaFree(b->ws);
   cudaFreeHost(b->h_stage);

@@ -202,3 +202,24 @@ def test_batch_rejects_invalid_sets():
     b.run()
     assert b.sync_status() == B.OP_OK
     b.close()
+
+
+@pytest.mark.parametrize("radii", [(16, 20, 44), (0, 2, 15)], ids=["large-only", "small-only"])
+def test_batch_with_one_radius_group_empty(radii):
+    """A batch created for radii up to 44 runs r <= 15 and r > 15 as two
+    groups; either group may be empty in a given set."""
+    images = make_images(9, seed=11 + radii[0], max_r=44, levels=(16, 20, 32))
+    rng = np.random.default_rng(radii[1])
+    for im in images:
+        im["r"] = int(rng.choice(radii))
+    descs = to_device(images)
+    pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
+    b = Batch(16, pix + 64, 44, 32,
+              config={"tile_w": 64, "chunk_rows": 2, "prefetch": 1, "cols_per_thread": 2})
+    stream = torch.cuda.Stream()
+    b.set(descs, stream)
+    b.capture(stream)
+    b.launch_graph(stream)
+    assert b.sync_status(stream) == B.OP_OK
+    check_all(images, f"radii {radii}")
+    b.close()
