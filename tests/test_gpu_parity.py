@@ -242,6 +242,23 @@ def test_edge_shapes(w, h, r, L):
     check_case(img, r, L, bpp=4, pad=0)
 
 
+@pytest.mark.parametrize("w,h", [(65535, 3), (3, 65535)])
+@pytest.mark.parametrize("r,L,cfg", [
+    (44, 20, None),
+    (15, 20, {"tile_w": 128, "cols_per_thread": 4, "chunk_rows": 2}),
+    (20, 32, {"tile_w": 128, "cols_per_thread": 2, "chunk_rows": 4, "tile_h": 1}),
+    (7, 64, {"tile_w": 64, "cols_per_thread": 1, "chunk_rows": 8}),
+])
+def test_maximum_dimensions(w, h, r, L, cfg):
+    """Width or height at OP_MAX_DIM: the longest tile rows and columns, the
+    most tiles per row (512 of 128 columns), and with one-row tiles the
+    largest grid height the launch allows (65535)."""
+    rng = np.random.default_rng(w + r)
+    img = rng.integers(0, 256, (h, w, 3)).astype(np.uint8)
+    img[rng.random((h, w)) < 0.3] = (40, 200, 90)  # runs of one level
+    check_case(img, r, L, bpp=3, pad=5, config=cfg)
+
+
 def test_constant_white_and_black():
     for colour in (255, 0):
         img = np.full((70, 90, 3), colour, np.uint8)
