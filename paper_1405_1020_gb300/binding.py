@@ -20,6 +20,7 @@ OP_E_CUDA = -2
 OP_E_NOMEM = -3
 OP_E_TIMEOUT = -4
 OP_E_UNSUPPORTED = -5
+OP_E_BOUNDS = -6  # the bounds-checking build found and skipped an out-of-range access
 
 OP_LEVEL_PAPER = 0
 OP_LEVEL_INTDIV3 = 1
@@ -31,7 +32,10 @@ OP_MAX_LEVELS = 256
 OP_MAX_DIM = 65535
 OP_NOALLOC_MAX_WORDS = 4 * 1024 * 1024
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboilpaint.so")
+_PKG = os.path.dirname(os.path.abspath(__file__))
+# OPK_LIBRARY=checked loads the bounds-checking build (liboilpaint_checked.so)
+LIB_PATH = os.path.join(_PKG, "liboilpaint_checked.so" if os.environ.get("OPK_LIBRARY") == "checked"
+                        else "liboilpaint.so")
 
 # every symbol include/oilpaint.h declares
 EXPORTS = (

@@ -31,21 +31,30 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liboilpaint.so")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+CHECKED_LIB = os.path.join(PKG, "liboilpaint_checked.so")
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     deps += [os.path.join(INCLUDE, "oilpaint.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link the library if missing or older than its sources."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile and link the library if missing or older than its sources.
+    checked=True builds the bounds-checking variant liboilpaint_checked.so
+    (OPK_CHECKED: every shared-memory, pixel and TMA access is range-checked,
+    violations are reported as OP_E_BOUNDS instead of faulting)."""
+    lib = CHECKED_LIB if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DOPK_CHECKED=1",)
     nvcc = _nvcc()
-    bdir = os.path.join(PKG, "_build")
+    bdir = os.path.join(PKG, "_build_checked" if checked else "_build")
     os.makedirs(bdir, exist_ok=True)
     procs = []
     objs = []
@@ -67,12 +76,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -352,6 +352,7 @@ const char *op_status_string(int status) {
     case OP_E_NOMEM: return "out of memory";
     case OP_E_TIMEOUT: return "device wait timed out";
     case OP_E_UNSUPPORTED: return "unsupported configuration";
+    case OP_E_BOUNDS: return "bounds check failed (checked build)";
     default: return "unknown status";
   }
 }
@@ -591,7 +592,9 @@ int op_sync_status(op_t *op, void *stream) {
     if (cudaMemset(op->d_err, 0, sizeof(err)) != cudaSuccess) return OP_E_CUDA;
     return OP_E_TIMEOUT;
   }
-  return OP_OK;
+  uint32_t bits = 0;
+  if (opk::take_check_error(&bits) != cudaSuccess) return OP_E_CUDA;
+  return bits ? OP_E_BOUNDS : OP_OK;
 }
 
 int op_destroy(op_t *op) {
@@ -1029,7 +1032,9 @@ int op_batch_sync_status(op_batch_t *b, void *stream) {
     if (cudaMemset(d_err, 0, sizeof(err)) != cudaSuccess) return OP_E_CUDA;
     return OP_E_TIMEOUT;
   }
-  return OP_OK;
+  uint32_t bits = 0;
+  if (opk::take_check_error(&bits) != cudaSuccess) return OP_E_CUDA;
+  return bits ? OP_E_BOUNDS : OP_OK;
 }
 
 int op_batch_destroy(op_batch_t *b) {

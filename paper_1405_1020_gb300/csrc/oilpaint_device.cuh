@@ -105,6 +105,37 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Checked builds (-DOPK_CHECKED=1, the library's bounds-checking variant;
+// no GPU sanitizer is used).  Every shared-memory access through the helpers
+// below is checked against the running kernel's dynamic shared memory and its
+// alignment, every global pixel access against the image, and every TMA
+// copy's x coordinate against the 16-byte rule.  A violation sets a bit in
+// g_check_error (read and cleared by the host after each run) and the access
+// is skipped instead of faulting.
+#ifndef OPK_CHECKED
+#define OPK_CHECKED 0
+#endif
+
+#if OPK_CHECKED
+static __device__ uint32_t g_check_error;
+extern __shared__ uint8_t opk_dyn_smem[];
+
+__device__ __forceinline__ void check_fail(uint32_t bit) { atomicOr(&g_check_error, bit); }
+
+__device__ __forceinline__ bool smem_ok(uint32_t addr, uint32_t bytes) {
+  uint32_t dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const uint32_t lo = smem_addr(opk_dyn_smem);
+  const uint32_t align = bytes < 8u ? bytes : 8u;
+  const bool ok = addr >= lo && addr + bytes <= lo + dyn && (addr & (align - 1u)) == 0u;
+  if (!ok) check_fail(1u);
+  return ok;
+}
+#define OPK_SMEM_OK(a, n) smem_ok((a), (n))
+#else
+#define OPK_SMEM_OK(a, n) true
+#endif
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -174,20 +205,27 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 }
 
 __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  if (!OPK_SMEM_OK(addr, 4u)) return 0u;
   uint32_t v;
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
 }
 
 __device__ __forceinline__ void lds_v2(uint32_t addr, uint32_t &lo, uint32_t &hi) {
+  if (!OPK_SMEM_OK(addr, 8u)) {
+    lo = hi = 0u;
+    return;
+  }
   asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(addr));
 }
 
 __device__ __forceinline__ void sts_zero64(uint32_t addr) {
+  if (!OPK_SMEM_OK(addr, 8u)) return;
   asm volatile("st.shared.v2.u32 [%0], {%1, %1};" ::"r"(addr), "r"(0u));
 }
 
 __device__ __forceinline__ void sts_zero32(uint32_t addr) {
+  if (!OPK_SMEM_OK(addr, 4u)) return;
   asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(0u));
 }
 
@@ -195,6 +233,7 @@ __device__ __forceinline__ void sts_zero32(uint32_t addr) {
 // volatile asm, so they keep their program order among themselves; the ring
 // reads are ordinary loads and may be scheduled around them.
 __device__ __forceinline__ void bin_add64(uint32_t addr, uint32_t dlo, uint32_t dhi) {
+  if (!OPK_SMEM_OK(addr, 8u)) return;
   asm volatile(
       "{\n\t.reg .u32 a, b;\n\t"
       "ld.shared.v2.u32 {a, b}, [%0];\n\t"
@@ -205,6 +244,7 @@ __device__ __forceinline__ void bin_add64(uint32_t addr, uint32_t dlo, uint32_t 
 }
 
 __device__ __forceinline__ void bin_sub64(uint32_t addr, uint32_t dlo, uint32_t dhi) {
+  if (!OPK_SMEM_OK(addr, 8u)) return;
   asm volatile(
       "{\n\t.reg .u32 a, b;\n\t"
       "ld.shared.v2.u32 {a, b}, [%0];\n\t"
@@ -215,6 +255,7 @@ __device__ __forceinline__ void bin_sub64(uint32_t addr, uint32_t dlo, uint32_t 
 }
 
 __device__ __forceinline__ void cnt_add(uint32_t addr, uint32_t d) {
+  if (!OPK_SMEM_OK(addr, 4u)) return;
   asm volatile(
       "{\n\t.reg .u32 a;\n\t"
       "ld.shared.u32 a, [%0];\n\t"
@@ -228,6 +269,7 @@ __device__ __forceinline__ void cnt_add(uint32_t addr, uint32_t d) {
 // so the two updates share one shared-memory latency.  addr_a != addr_b.
 __device__ __forceinline__ void bin_addsub64(uint32_t addr_a, uint32_t alo, uint32_t ahi,
                                              uint32_t addr_b, uint32_t blo, uint32_t bhi) {
+  if (!OPK_SMEM_OK(addr_a, 8u) || !OPK_SMEM_OK(addr_b, 8u)) return;
   asm volatile(
       "{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
@@ -244,6 +286,7 @@ __device__ __forceinline__ void bin_addsub64(uint32_t addr_a, uint32_t alo, uint
 // Two 64-bit additions issued together (addr_a != addr_b).
 __device__ __forceinline__ void bin_add64x2(uint32_t addr_a, uint32_t alo, uint32_t ahi,
                                             uint32_t addr_b, uint32_t blo, uint32_t bhi) {
+  if (!OPK_SMEM_OK(addr_a, 8u) || !OPK_SMEM_OK(addr_b, 8u)) return;
   asm volatile(
       "{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
@@ -264,6 +307,8 @@ __device__ __forceinline__ void bin_addsub64x2(uint32_t A, uint32_t alo, uint32_
                                                uint32_t blo, uint32_t bhi, uint32_t C,
                                                uint32_t clo, uint32_t chi, uint32_t D,
                                                uint32_t dlo, uint32_t dhi) {
+  if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u))
+    return;
   asm volatile(
       "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
@@ -289,6 +334,7 @@ __device__ __forceinline__ void bin_addsub64x2(uint32_t A, uint32_t alo, uint32_
 // The same for two 32-bit counts: +da at addr_a, -db at addr_b.
 __device__ __forceinline__ void cnt_addsub(uint32_t addr_a, uint32_t da, uint32_t addr_b,
                                            uint32_t db) {
+  if (!OPK_SMEM_OK(addr_a, 4u) || !OPK_SMEM_OK(addr_b, 4u)) return;
   asm volatile(
       "{\n\t.reg .u32 a, b;\n\t"
       "ld.shared.u32 a, [%0];\n\t"
@@ -604,6 +650,9 @@ struct DeltaOpsA {
 __device__ __forceinline__ void binb_addsub(uint32_t As, uint32_t Ac, uint32_t alo, uint32_t ahi,
                                             uint32_t ac, uint32_t Bs, uint32_t Bc, uint32_t blo,
                                             uint32_t bhi, uint32_t bc) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
+      !OPK_SMEM_OK(Bc, 4u))
+    return;
   asm volatile(
       "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
@@ -627,6 +676,9 @@ __device__ __forceinline__ void binb_addsub(uint32_t As, uint32_t Ac, uint32_t a
 __device__ __forceinline__ void binb_add_x2(uint32_t As, uint32_t Ac, uint32_t alo, uint32_t ahi,
                                             uint32_t ac, uint32_t Bs, uint32_t Bc, uint32_t blo,
                                             uint32_t bhi, uint32_t bc) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
+      !OPK_SMEM_OK(Bc, 4u))
+    return;
   asm volatile(
       "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
@@ -648,6 +700,7 @@ __device__ __forceinline__ void binb_add_x2(uint32_t As, uint32_t Ac, uint32_t a
 
 __device__ __forceinline__ void binb_add(uint32_t As, uint32_t Ac, uint32_t lo, uint32_t hi,
                                          uint32_t c) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u)) return;
   asm volatile(
       "{\n\t.reg .u32 a0, a1, a2;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
@@ -799,6 +852,12 @@ __device__ __forceinline__ SmemMap carve_smem(uint8_t *smem, const RingCfg &rc,
 // Writes the output pixel (x, y): R, G, B and, with 4 bytes per pixel, alpha.
 __device__ __forceinline__ void store_pixel(const ImgDesc &d, int x, int y, uint32_t R,
                                             uint32_t G, uint32_t B, uint32_t alpha) {
+#if OPK_CHECKED
+  if (x < 0 || y < 0 || x >= static_cast<int>(d.w) || y >= static_cast<int>(d.h)) {
+    check_fail(2u);
+    return;
+  }
+#endif
   uint8_t *o = d.out + static_cast<size_t>(y) * d.ostride + static_cast<size_t>(x) * d.bpp;
   if (d.bpp == 4 && !(d.mode & kModeLiteral)) {
     const uint32_t v = R | (G << 8) | (B << 16) | (alpha << 24);
@@ -818,6 +877,12 @@ __device__ __forceinline__ void store_pixel(const ImgDesc &d, int x, int y, uint
 }
 
 __device__ __forceinline__ uint32_t load_alpha(const ImgDesc &d, int x, int y) {
+#if OPK_CHECKED
+  if (x < 0 || y < 0 || x >= static_cast<int>(d.w) || y >= static_cast<int>(d.h)) {
+    check_fail(2u);
+    return 0u;
+  }
+#endif
   return __ldg(d.in + static_cast<size_t>(y) * d.stride + static_cast<size_t>(x) * 4u + 3u);
 }
 
@@ -853,6 +918,13 @@ __device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *t
     const uint32_t slot = g % rc.nslot;
     const uint32_t bar = sm.bars + slot * 8u;
     const uint32_t dst = sm.ring + slot * rc.slot_bytes;
+#if OPK_CHECKED
+    // x a multiple of 4 words (16 bytes); both halves inside the ring slot
+    if ((xs & 3) != 0 || box_bytes > rc.half_bytes || !OPK_SMEM_OK(dst, rc.slot_bytes)) {
+      check_fail(4u);
+      return;  // nothing armed: the wait for this chunk runs out and reports a timeout
+    }
+#endif
     mbar_arrive_expect_tx(bar, 2u * box_bytes);
     tma_load_2d(dst, tmap, xs, E0 + k * ch, bar);
     tma_load_2d(dst + rc.half_bytes, tmap, xs, E0 + k * ch - 2 * r - 1, bar);
@@ -1303,6 +1375,7 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
 
 // Shared-memory atomic adds (the start-window histograms of the column path).
 __device__ __forceinline__ void red_add64(uint32_t addr, uint32_t lo, uint32_t hi) {
+  if (!OPK_SMEM_OK(addr, 8u)) return;
   asm volatile(
       "{\n\t.reg .u64 v;\n\t"
       "mov.b64 v, {%1, %2};\n\t"
@@ -1312,6 +1385,7 @@ __device__ __forceinline__ void red_add64(uint32_t addr, uint32_t lo, uint32_t h
 }
 
 __device__ __forceinline__ void red_add32(uint32_t addr, uint32_t v) {
+  if (!OPK_SMEM_OK(addr, 4u)) return;
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 

@@ -172,6 +172,9 @@ cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
 cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStream_t s);
+// Checked builds: the bounds-check violation bits since the last call
+// (1 shared memory, 2 image pixels, 4 TMA copy), cleared; 0 otherwise.
+cudaError_t take_check_error(uint32_t *bits);
 
 // Raise the dynamic shared-memory limit of every filter kernel instance to
 // `bytes`; returns the error of the first failing call.

@@ -299,6 +299,22 @@ cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
   return cudaGetLastError();
 }
 
+cudaError_t take_check_error(uint32_t *bits) {
+#if OPK_CHECKED
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_check_error, sizeof(v));
+  if (e == cudaSuccess && v) {
+    const uint32_t z = 0;
+    e = cudaMemcpyToSymbol(g_check_error, &z, sizeof(z));
+  }
+  *bits = v;
+  return e;
+#else
+  *bits = 0;
+  return cudaSuccess;
+#endif
+}
+
 cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStream_t s) {
   selftest_wait_kernel<<<1, 32, 0, s>>>(d_err, timeout_ns);
   return cudaGetLastError();

@@ -191,5 +191,8 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (cudaMemcpyAsync(&err, sc.err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return OP_E_CUDA;
-  return err ? OP_E_TIMEOUT : OP_OK;
+  if (err) return OP_E_TIMEOUT;
+  uint32_t bits = 0;
+  if (opk::take_check_error(&bits) != cudaSuccess) return OP_E_CUDA;
+  return bits ? OP_E_BOUNDS : OP_OK;
 }

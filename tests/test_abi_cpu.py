@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings(lib):
     for st, word in ((0, "ok"), (-1, "invalid"), (-2, "CUDA"), (-3, "memory"), (-4, "timed out"),
-                     (-5, "unsupported")):
+                     (-5, "unsupported"), (-6, "bounds")):
         assert word in B.op_status_string(st)
 
 
