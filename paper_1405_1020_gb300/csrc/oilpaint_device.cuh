@@ -1227,16 +1227,17 @@ __device__ __forceinline__ void delta_step_split(const Ops &ops, const uint32_t 
   }
 }
 
-// Whether the K-column path splits the window histogram by column parity:
-// with four columns per thread the histograms already limit a CTA to few
-// resident warps, and the extra independent update chain pays for the
-// extra histogram; with two columns the extra histogram costs more
-// occupancy than the chain gains.
-// Variant B bins (12 bytes) never split.
-constexpr bool kSplit2 = false;
-constexpr bool kSplit4 = true;
-__host__ __device__ constexpr bool split_for(int k, int var) {
-  return var == kVarA && (k == 4 ? kSplit4 : kSplit2);
+// Into how many histograms the K-column path splits the window histogram
+// (by column parity): with four columns per thread a second, independent
+// update chain pays for the extra histogram; with two columns the extra
+// histogram costs more occupancy than the chain gains, and a four-way split
+// of the four-column window histogram measured slower still (two more
+// histograms per thread, one resident CTA fewer per SM).  Variant B bins
+// (12 bytes) never split.
+constexpr int kSplit2 = 1;
+constexpr int kSplit4 = 2;
+__host__ __device__ constexpr int hsplit(int k, int var) {
+  return var == kVarA ? (k == 4 ? kSplit4 : kSplit2) : 1;
 }
 
 // K output columns per thread through difference histograms (r <= 44,
@@ -1245,7 +1246,7 @@ __host__ __device__ constexpr bool split_for(int k, int var) {
 // is a multiple of 4 (tiles start at d.xshift), so every thread's window
 // starts on a 16-byte boundary of the ring.  It keeps
 //   H    the histogram of the window of column xa (2r+1 columns; split into
-//        two histograms over its even and odd columns where split_for says),
+//        hsplit(K, VAR) histograms by column index where that is above 1),
 //   D_i  (i = 1..K-1) the histogram of column xa+i+r minus that of column
 //        xa+i-1-r, so that the window histogram of column xa+i is
 //        H + D_1 + ... + D_i.
@@ -1263,8 +1264,8 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
                                uint32_t &chunk_ctr, uint32_t *err, uint64_t timeout_ns,
                                uint32_t *diag = nullptr, bool tmap_global = false) {
   static_assert(K == 2 || K == 4, "two or four columns per thread");
-  constexpr bool SPLIT = split_for(K, VAR);
-  constexpr int NB = SPLIT ? 2 : 1;  // histograms making up H
+  constexpr int NB = hsplit(K, VAR);  // histograms making up H
+  static_assert(NB == 1 || NB == 2, "split of H");
   constexpr int NH = NB + K - 1;
   const int t = threadIdx.x;
   const int r = d.r;
@@ -1308,7 +1309,7 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
           const int x = xa + i;
           alpha[i] = (out_now && d.bpp == 4 && x >= d.ox0 && x < d.ox1) ? load_alpha(d, x, y) : 0u;
         }
-        if (SPLIT) {
+        if constexpr (NB == 2) {
           if (rm)
             delta_step_split<K, true>(ops, pe, pl, r, h0, hstride);
           else
@@ -1332,7 +1333,8 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
         for (uint32_t lv = 0; lv < L; ++lv) {
           const uint32_t tag = 31u - lv;
           uint32_t acc = count_word(0, lv);
-          if (SPLIT) acc += count_word(1, lv);
+#pragma unroll
+          for (int b = 1; b < NB; ++b) acc += count_word(b, lv);
           best[0] = max(best[0], (acc << CSH) | tag);
 #pragma unroll
           for (int i = 1; i < K; ++i) {

@@ -117,7 +117,7 @@ inline size_t cols_hist_bytes(const Geometry &g, int r, uint32_t L) {
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
   // (column path: cols_hist_bytes)
   if (kcols > 1) {
-    const size_t nh = static_cast<size_t>(kcols) + (split_for(kcols, variant) ? 1u : 0u);
+    const size_t nh = static_cast<size_t>(kcols) + static_cast<size_t>(hsplit(kcols, variant)) - 1u;
     return (nh * L + 1u) * nt * (variant == kVarA ? 8u : 12u);
   }
   return static_cast<size_t>(L + 1u) * nt * bin_bytes(variant);
