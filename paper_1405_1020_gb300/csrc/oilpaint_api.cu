@@ -852,24 +852,49 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
       auto it = g_tune.find({im.radius, im.levels});
       if (it != g_tune.end()) th = it->second.tile_h;
     }
-    if (th == 0) th = std::max<uint32_t>(64u, 16u * static_cast<uint32_t>(im.radius));
-    const uint32_t rows = opk::output_window(im.width, im.height, im.radius, im.flags).rows();
-    th = std::max(1u, std::min(th, rows));
-    tile_h[i] = th;
+    tile_h[i] = th;  // 0: chosen below from the image's share of the GPU
     geo[i] = opk::image_geometry(0, nt, kc, im.radius, im.levels, im.width);
-    // per step a tile slides one window column (4r + 2 bin updates) and
-    // K - 1 difference columns (4 each); per output row it scans K argmaxes
-    const double r = im.radius, k = geo[i].kcols;
-    tile_cost[i] = (th + 2.0 * r) * (4.0 * r + 2.0 + 4.0 * (k - 1.0)) +
-                   th * k * (im.levels + 10.0);
     order[i] = i;
   }
   if (padded > b->max_pixels) return OP_E_INVALID;
-  // group of each image (radius above 15 -> group 1), then most expensive
-  // tiles first within a group
+  // group of each image (radius above 15 -> group 1)
   auto group_of = [&](uint32_t i) {
     return b->groups == 2 && images[i].radius > opk::kMaxRadiusA ? 1 : 0;
   };
+  // Tile heights: an image gets its pixel share of its group's resident
+  // CTAs (two waves' worth when the group holds several images, so that the
+  // ticket queue can balance them; one for a lone image) and the waves model
+  // of the single-image path picks its tile height for that many slots.  A
+  // lone small request thus spreads over the GPU in short tiles (latency),
+  // a large mixed batch keeps tall tiles (less refill per output row).
+  {
+    double gpix[2] = {0.0, 0.0};
+    uint32_t gnum[2] = {0, 0};
+    for (uint32_t i = 0; i < n; ++i) {
+      gpix[group_of(i)] += static_cast<double>(images[i].width) * images[i].height;
+      ++gnum[group_of(i)];
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+      const op_image_t &im = images[i];
+      const uint32_t rows = opk::output_window(im.width, im.height, im.radius, im.flags).rows();
+      uint32_t th = tile_h[i];
+      if (th == 0) {
+        const int g = group_of(i);
+        const double share = static_cast<double>(im.width) * im.height / gpix[g] *
+                             b->grid_persist[g] * (gnum[g] > 1 ? 2.0 : 1.0);
+        th = auto_tile_h(std::max(1u, rows), geo[i].tiles_x, im.radius,
+                         std::max<uint64_t>(1u, static_cast<uint64_t>(share)));
+      }
+      th = std::max(1u, std::min(th, rows));
+      tile_h[i] = th;
+      // per step a tile slides one window column (4r + 2 bin updates) and
+      // K - 1 difference columns (4 each); per output row it scans K argmaxes
+      const double r = im.radius, k = geo[i].kcols;
+      tile_cost[i] = (th + 2.0 * r) * (4.0 * r + 2.0 + 4.0 * (k - 1.0)) +
+                     th * k * (im.levels + 10.0);
+    }
+  }
+  // most expensive tiles first within a group
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
     const int ga = group_of(a), gc = group_of(c);
     return ga != gc ? ga < gc : tile_cost[a] > tile_cost[c];
