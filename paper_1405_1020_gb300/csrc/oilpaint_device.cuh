@@ -300,27 +300,55 @@ __device__ __forceinline__ void bin_add64x2(uint32_t addr_a, uint32_t alo, uint3
       "r"(alo), "r"(ahi), "r"(addr_b), "r"(blo), "r"(bhi));
 }
 
-// Two bin_addsub64 issued together: +a at A, -b at B, +c at C, -d at D, all
-// four loads before any add.  A, B, C, D are distinct, except that B and D
-// may both be the scratch bin, whose contents are never read.
-__device__ __forceinline__ void bin_addsub64x2(uint32_t A, uint32_t alo, uint32_t ahi, uint32_t B,
-                                               uint32_t blo, uint32_t bhi, uint32_t C,
-                                               uint32_t clo, uint32_t chi, uint32_t D,
-                                               uint32_t dlo, uint32_t dhi) {
+// +(alo, ahi) at A and -(blo, bhi) at B as one two-deep update that is
+// right whether or not A == B: both loads are issued first, and when the
+// two bins coincide the subtraction is applied to the sum, which the second
+// store (to the same bin) leaves in place.
+__device__ __forceinline__ void bin_addsub64_chain(uint32_t A, uint32_t alo, uint32_t ahi,
+                                                   uint32_t B, uint32_t blo, uint32_t bhi) {
+  if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u)) return;
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t.reg .pred p;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
+      "add.cc.u32 a0, a0, %1;\n\t"
+      "addc.u32 a1, a1, %2;\n\t"
+      "setp.eq.u32 p, %0, %3;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "sub.cc.u32 b0, b0, %4;\n\t"
+      "subc.u32 b1, b1, %5;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(A),
+      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi));
+}
+
+// Two such updates issued together (A, B in one histogram; C, D in
+// another): four loads first.
+__device__ __forceinline__ void bin_addsub64x2_chain(uint32_t A, uint32_t alo, uint32_t ahi,
+                                                     uint32_t B, uint32_t blo, uint32_t bhi,
+                                                     uint32_t C, uint32_t clo, uint32_t chi,
+                                                     uint32_t D, uint32_t dlo, uint32_t dhi) {
   if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u))
     return;
   asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t"
+      "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t.reg .pred p, q;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
       "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
       "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"
       "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"
       "add.cc.u32 a0, a0, %1;\n\t"
       "addc.u32 a1, a1, %2;\n\t"
-      "sub.cc.u32 b0, b0, %4;\n\t"
-      "subc.u32 b1, b1, %5;\n\t"
       "add.cc.u32 c0, c0, %7;\n\t"
       "addc.u32 c1, c1, %8;\n\t"
+      "setp.eq.u32 p, %0, %3;\n\t"
+      "setp.eq.u32 q, %6, %9;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "selp.b32 d0, c0, d0, q;\n\t"
+      "selp.b32 d1, c1, d1, q;\n\t"
+      "sub.cc.u32 b0, b0, %4;\n\t"
+      "subc.u32 b1, b1, %5;\n\t"
       "sub.cc.u32 d0, d0, %10;\n\t"
       "subc.u32 d1, d1, %11;\n\t"
       "st.shared.v2.u32 [%0], {a0, a1};\n\t"
@@ -587,8 +615,6 @@ __device__ __forceinline__ void neg64(uint32_t &lo, uint32_t &hi) {
 // level-0 bin.
 template <int NT>
 struct DeltaOpsA {
-  uint32_t scratch;  // the thread's scratch bin
-
   __device__ __forceinline__ void add(uint32_t base, uint32_t w) const {
     uint32_t lo, hi;
     dh_delta(w, lo, hi);
@@ -599,38 +625,25 @@ struct DeltaOpsA {
     dh_delta(w, lo, hi);
     bin_sub64(dh_addr<NT>(base, w), lo, hi);
   }
-  // +win -wout: the bin of win gets (alo, ahi) added and bin ab gets (blo,
-  // bhi) subtracted; when both words have the same level the two fold into
-  // one delta and ab becomes the scratch bin.
-  __device__ __forceinline__ void pair(uint32_t base, uint32_t win, uint32_t wout, uint32_t &aa,
-                                       uint32_t &alo, uint32_t &ahi, uint32_t &ab, uint32_t &blo,
-                                       uint32_t &bhi) const {
+  // +win -wout in one histogram as one two-deep update (the bins of the two
+  // words may coincide).
+  __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
+    uint32_t alo, ahi, blo, bhi;
     dh_delta(win, alo, ahi);
     dh_delta(wout, blo, bhi);
-    aa = dh_addr<NT>(base, win);
-    ab = dh_addr<NT>(base, wout);
-    if (aa == ab) {
-      const uint64_t net =
-          (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
-      alo = static_cast<uint32_t>(net);
-      ahi = static_cast<uint32_t>(net >> 32);
-      ab = scratch;
-    }
-  }
-  // +win -wout in one histogram as one two-deep update.
-  __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
-    uint32_t aa, alo, ahi, ab, blo, bhi;
-    pair(base, win, wout, aa, alo, ahi, ab, blo, bhi);
-    bin_addsub64(aa, alo, ahi, ab, blo, bhi);
+    bin_addsub64_chain(dh_addr<NT>(base, win), alo, ahi, dh_addr<NT>(base, wout), blo, bhi);
   }
   // +win_p -wout_p in histogram p and +win_q -wout_q in histogram q != p as
   // one four-deep update.
   __device__ __forceinline__ void addsub_x2(uint32_t p, uint32_t win_p, uint32_t wout_p,
                                             uint32_t q, uint32_t win_q, uint32_t wout_q) const {
-    uint32_t A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi;
-    pair(p, win_p, wout_p, A, alo, ahi, B, blo, bhi);
-    pair(q, win_q, wout_q, C, clo, chi, D, dlo, dhi);
-    bin_addsub64x2(A, alo, ahi, B, blo, bhi, C, clo, chi, D, dlo, dhi);
+    uint32_t alo, ahi, blo, bhi, clo, chi, dlo, dhi;
+    dh_delta(win_p, alo, ahi);
+    dh_delta(wout_p, blo, bhi);
+    dh_delta(win_q, clo, chi);
+    dh_delta(wout_q, dlo, dhi);
+    bin_addsub64x2_chain(dh_addr<NT>(p, win_p), alo, ahi, dh_addr<NT>(p, wout_p), blo, bhi,
+                         dh_addr<NT>(q, win_q), clo, chi, dh_addr<NT>(q, wout_q), dlo, dhi);
   }
   // (+/-)wp at histogram p and (+/-)wq at histogram q != p.
   template <bool NEG_P, bool NEG_Q>
@@ -644,17 +657,17 @@ struct DeltaOpsA {
   }
 };
 
-// Variant B: +(lo, hi) at sums address s and +c at count address sc, and
-// -(lo, hi) / -c at a second bin, all loads first (distinct bins except
-// that the second may be the scratch bin).
-__device__ __forceinline__ void binb_addsub(uint32_t As, uint32_t Ac, uint32_t alo, uint32_t ahi,
-                                            uint32_t ac, uint32_t Bs, uint32_t Bc, uint32_t blo,
-                                            uint32_t bhi, uint32_t bc) {
+// binb_addsub for bins that may coincide (As == Bs implies Ac == Bc): the
+// subtraction is applied to the sum when they do, as bin_addsub64_chain.
+__device__ __forceinline__ void binb_addsub_chain(uint32_t As, uint32_t Ac, uint32_t alo,
+                                                  uint32_t ahi, uint32_t ac, uint32_t Bs,
+                                                  uint32_t Bc, uint32_t blo, uint32_t bhi,
+                                                  uint32_t bc) {
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
       !OPK_SMEM_OK(Bc, 4u))
     return;
   asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
+      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t.reg .pred p;\n\t"
       "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
       "ld.shared.u32 a2, [%1];\n\t"
       "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
@@ -662,6 +675,10 @@ __device__ __forceinline__ void binb_addsub(uint32_t As, uint32_t Ac, uint32_t a
       "add.cc.u32 a0, a0, %2;\n\t"
       "addc.u32 a1, a1, %3;\n\t"
       "add.u32 a2, a2, %4;\n\t"
+      "setp.eq.u32 p, %0, %5;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "selp.b32 b2, a2, b2, p;\n\t"
       "sub.cc.u32 b0, b0, %7;\n\t"
       "subc.u32 b1, b1, %8;\n\t"
       "sub.u32 b2, b2, %9;\n\t"
@@ -724,8 +741,7 @@ __device__ __forceinline__ void dhb_delta(uint32_t w, uint32_t &lo, uint32_t &hi
 
 template <int NT>
 struct DeltaOpsB {
-  uint32_t scratch;  // the thread's scratch sums bin
-  uint32_t cd;       // count address = (sums address >> 1) + cd
+  uint32_t cd;  // count address = (sums address >> 1) + cd
 
   // level field (bits 8..12) times NT * 8 bytes
   __device__ __forceinline__ uint32_t saddr(uint32_t base, uint32_t w) const {
@@ -746,26 +762,12 @@ struct DeltaOpsB {
     const uint32_t s = saddr(base, w);
     binb_add(s, caddr(s), lo, hi, 0u - c);
   }
-  __device__ __forceinline__ void pair(uint32_t base, uint32_t win, uint32_t wout, uint32_t &as,
-                                       uint32_t &alo, uint32_t &ahi, uint32_t &ac, uint32_t &bs,
-                                       uint32_t &blo, uint32_t &bhi, uint32_t &bc) const {
+  __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
+    uint32_t alo, ahi, ac, blo, bhi, bc;
     dhb_delta(win, alo, ahi, ac);
     dhb_delta(wout, blo, bhi, bc);
-    as = saddr(base, win);
-    bs = saddr(base, wout);
-    if (as == bs) {
-      const uint64_t net =
-          (static_cast<uint64_t>(ahi) << 32 | alo) - (static_cast<uint64_t>(bhi) << 32 | blo);
-      alo = static_cast<uint32_t>(net);
-      ahi = static_cast<uint32_t>(net >> 32);
-      ac -= bc;
-      bs = scratch;
-    }
-  }
-  __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
-    uint32_t as, alo, ahi, ac, bs, blo, bhi, bc;
-    pair(base, win, wout, as, alo, ahi, ac, bs, blo, bhi, bc);
-    binb_addsub(as, caddr(as), alo, ahi, ac, bs, caddr(bs), blo, bhi, bc);
+    const uint32_t as = saddr(base, win), bs = saddr(base, wout);
+    binb_addsub_chain(as, caddr(as), alo, ahi, ac, bs, caddr(bs), blo, bhi, bc);
   }
   // Two histograms: issued as two two-deep updates (a four-deep one would
   // need 20 operands and more registers than it saves latency here).
@@ -1251,9 +1253,8 @@ __host__ __device__ constexpr int hsplit(int k, int var) {
 //        xa+i-1-r, so that the window histogram of column xa+i is
 //        H + D_1 + ... + D_i.
 // A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  Histograms are
-// L levels of NT bins (level-major, thread-minor), followed by one scratch
-// bin per thread; VAR B keeps its counts in a second array of the same
-// shape.  The argmax runs over running sums of counts (VAR A: the
+// L levels of NT bins (level-major, thread-minor); VAR B keeps its counts in
+// a second array of the same shape.  The argmax runs over running sums of counts (VAR A: the
 // histograms' low words, whose bottom 10 bits are the counts) with keys
 // (count, 31 - level), so the lowest level wins ties under max.  Pixels
 // outside the image are TMA zero fill whose delta is zero, so no thread
@@ -1278,13 +1279,11 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
   const uint32_t lstride = NT * 8u;      // between levels of one histogram
   const uint32_t hstride = L * lstride;  // between histograms
   const uint32_t h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
-  const uint32_t scratch = h0 + NH * hstride;
   // VAR B counts: same shape at half the stride, after the sums
-  const uint32_t cbase = sm.sums + (NH * L + 1u) * lstride;
+  const uint32_t cbase = sm.sums + NH * L * lstride;
   const uint32_t cd = cbase - (sm.sums >> 1);
   using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<NT>, DeltaOpsB<NT>>::type;
   Ops ops;
-  ops.scratch = scratch;
   if constexpr (VAR == kVarB) ops.cd = cd;
   auto hist = [&](int i) { return h0 + static_cast<uint32_t>(i) * hstride; };
   auto cnt_of = [&](uint32_t s) { return (s >> 1) + cd; };
@@ -1342,6 +1341,11 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
             best[i] = max(best[i], (acc << CSH) | tag);
           }
         }
+        // the reciprocals are fetched first, so that their latency overlaps
+        // the loads of the winning bins
+        uint32_t mulv[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) mulv[i] = VAR == kVarA ? rcp_of(best[i] >> CSH) : 0u;
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           const int x = xa + i;
@@ -1362,7 +1366,7 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
             const uint32_t R = (lo >> 10) & 0x3FFFFu;
             const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
             const uint32_t B = hi >> 14;
-            const uint32_t mul = rcp_of(cnt);
+            const uint32_t mul = mulv[i];
             store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul),
                         __umulhi(B << 1, mul), alpha[i]);
           } else {
@@ -1397,13 +1401,11 @@ __device__ __forceinline__ void red_add32(uint32_t addr, uint32_t v) {
 // columns spread over the banks):
 //   colhist  [ncols][Lp] 8-byte bins  (ncols = T + 2r image columns)
 //   winners  [NW][32]    8-byte bins  (each warp's last 32 winning bins)
-//   scratch  [NT]        8-byte bins  (same-level folds)
 // and for variant B the column histograms' counts (4 bytes, same layout at
 // half the stride).
 __host__ __device__ constexpr uint32_t cols_levels(uint32_t L) { return L | 1u; }
-__host__ __device__ constexpr uint32_t cols_sums_bytes(uint32_t ncols, uint32_t nw, uint32_t nt,
-                                                       uint32_t L) {
-  return (ncols * cols_levels(L) + nw * 32u + nt) * 8u;
+__host__ __device__ constexpr uint32_t cols_sums_bytes(uint32_t ncols, uint32_t nw, uint32_t L) {
+  return (ncols * cols_levels(L) + nw * 32u) * 8u;
 }
 
 // Column histograms with the levels across a warp's lanes (r <= 44, L <= 32;
@@ -1444,15 +1446,13 @@ __device__ bool run_tile_cols(const ImgDesc &d, const CUtensorMap *tmap, int x0,
   const int nsteps = (y1 - y0) + 2 * r;
   const uint32_t colb = sm.sums;
   const uint32_t winb = colb + static_cast<uint32_t>(ncols) * S;  // 32 winner slots per warp
-  const uint32_t scrb = winb + NW * 32u * 8u;
-  const uint32_t sums_end = scrb + NT * 8u;
+  const uint32_t sums_end = winb + NW * 32u * 8u;
   // VAR B counts: the same layout at half the stride
   const uint32_t cbase = (sums_end + 127u) & ~127u;
   const uint32_t cd = cbase - (colb >> 1);
   const uint8_t *gbase = sm.ring_ptr - sm.ring;  // generic address of shared address 0
   using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<1>, DeltaOpsB<1>>::type;
   Ops ops;
-  ops.scratch = scrb + static_cast<uint32_t>(t) * 8u;
   if constexpr (VAR == kVarB) ops.cd = cd;
   // zero the column histograms (all Lp levels)
   {

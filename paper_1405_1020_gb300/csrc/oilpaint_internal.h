@@ -101,24 +101,24 @@ inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, u
   return g;
 }
 
-// Shared bytes of the column path's histograms (column sums, start windows,
-// scratch; variant B adds the counts after a 128-byte boundary).
+// Shared bytes of the column path's histograms (column sums, winner slots;
+// variant B adds the counts after a 128-byte boundary).
 inline size_t cols_hist_bytes(const Geometry &g, int r, uint32_t L) {
   const uint32_t ncols = g.tile_w + 2u * static_cast<uint32_t>(r);
-  const size_t sums = cols_sums_bytes(ncols, g.nt / 32u, g.nt, L);
+  const size_t sums = cols_sums_bytes(ncols, g.nt / 32u, L);
   if (g.variant == kVarA) return sums;
   return ((sums + 127u) & ~static_cast<size_t>(127u)) + sums / 2u;
 }
 
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
 // per thread, bins of the variant's size; 2 or 4: kcols histograms, one
-// more where the window histogram is split, of L levels per thread plus one
-// scratch bin, bins of 8 bytes (variant A) or 8 + 4 bytes (variant B)).
+// more where the window histogram is split, of L levels per thread, bins of
+// 8 bytes (variant A) or 8 + 4 bytes (variant B)).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
   // (column path: cols_hist_bytes)
   if (kcols > 1) {
     const size_t nh = static_cast<size_t>(kcols) + static_cast<size_t>(hsplit(kcols, variant)) - 1u;
-    return (nh * L + 1u) * nt * (variant == kVarA ? 8u : 12u);
+    return nh * L * nt * (variant == kVarA ? 8u : 12u);
   }
   return static_cast<size_t>(L + 1u) * nt * bin_bytes(variant);
 }
