@@ -323,6 +323,63 @@ __device__ __forceinline__ void bin_addsub64_chain(uint32_t A, uint32_t alo, uin
       "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi));
 }
 
+// +(alo, ahi) at A, then +(blo, bhi) at B, where A and B may coincide (the
+// second addition applies to the first's sum): both loads first.
+__device__ __forceinline__ void bin_add64x2_chain(uint32_t A, uint32_t alo, uint32_t ahi,
+                                                  uint32_t B, uint32_t blo, uint32_t bhi) {
+  if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u)) return;
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t.reg .pred p;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
+      "add.cc.u32 a0, a0, %1;\n\t"
+      "addc.u32 a1, a1, %2;\n\t"
+      "setp.eq.u32 p, %0, %3;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "add.cc.u32 b0, b0, %4;\n\t"
+      "addc.u32 b1, b1, %5;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(A),
+      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi));
+}
+
+// Two such chained pairs issued together (A, B in one histogram; C, D in
+// another): four loads first.
+__device__ __forceinline__ void bin_add64x4_chain(uint32_t A, uint32_t alo, uint32_t ahi,
+                                                  uint32_t B, uint32_t blo, uint32_t bhi,
+                                                  uint32_t C, uint32_t clo, uint32_t chi,
+                                                  uint32_t D, uint32_t dlo, uint32_t dhi) {
+  if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u))
+    return;
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t.reg .pred p, q;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
+      "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"
+      "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"
+      "add.cc.u32 a0, a0, %1;\n\t"
+      "addc.u32 a1, a1, %2;\n\t"
+      "add.cc.u32 c0, c0, %7;\n\t"
+      "addc.u32 c1, c1, %8;\n\t"
+      "setp.eq.u32 p, %0, %3;\n\t"
+      "setp.eq.u32 q, %6, %9;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "selp.b32 d0, c0, d0, q;\n\t"
+      "selp.b32 d1, c1, d1, q;\n\t"
+      "add.cc.u32 b0, b0, %4;\n\t"
+      "addc.u32 b1, b1, %5;\n\t"
+      "add.cc.u32 d0, d0, %10;\n\t"
+      "addc.u32 d1, d1, %11;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.v2.u32 [%3], {b0, b1};\n\t"
+      "st.shared.v2.u32 [%6], {c0, c1};\n\t"
+      "st.shared.v2.u32 [%9], {d0, d1};\n\t}" ::"r"(A),
+      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi), "r"(D),
+      "r"(dlo), "r"(dhi));
+}
+
 // Two such updates issued together (A, B in one histogram; C, D in
 // another): four loads first.
 __device__ __forceinline__ void bin_addsub64x2_chain(uint32_t A, uint32_t alo, uint32_t ahi,
@@ -625,6 +682,24 @@ struct DeltaOpsA {
     dh_delta(w, lo, hi);
     bin_sub64(dh_addr<NT>(base, w), lo, hi);
   }
+  // +w0 +w1 in one histogram as one two-deep update (their bins may coincide).
+  __device__ __forceinline__ void add2(uint32_t base, uint32_t w0, uint32_t w1) const {
+    uint32_t alo, ahi, blo, bhi;
+    dh_delta(w0, alo, ahi);
+    dh_delta(w1, blo, bhi);
+    bin_add64x2_chain(dh_addr<NT>(base, w0), alo, ahi, dh_addr<NT>(base, w1), blo, bhi);
+  }
+  // +w0 +w1 in histogram p and +w2 +w3 in histogram q != p, four deep.
+  __device__ __forceinline__ void add2x2(uint32_t p, uint32_t w0, uint32_t w1, uint32_t q,
+                                         uint32_t w2, uint32_t w3) const {
+    uint32_t alo, ahi, blo, bhi, clo, chi, dlo, dhi;
+    dh_delta(w0, alo, ahi);
+    dh_delta(w1, blo, bhi);
+    dh_delta(w2, clo, chi);
+    dh_delta(w3, dlo, dhi);
+    bin_add64x4_chain(dh_addr<NT>(p, w0), alo, ahi, dh_addr<NT>(p, w1), blo, bhi,
+                      dh_addr<NT>(q, w2), clo, chi, dh_addr<NT>(q, w3), dlo, dhi);
+  }
   // +win -wout in one histogram as one two-deep update (the bins of the two
   // words may coincide).
   __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
@@ -761,6 +836,15 @@ struct DeltaOpsB {
     neg64(lo, hi);
     const uint32_t s = saddr(base, w);
     binb_add(s, caddr(s), lo, hi, 0u - c);
+  }
+  __device__ __forceinline__ void add2(uint32_t base, uint32_t w0, uint32_t w1) const {
+    add(base, w0);
+    add(base, w1);
+  }
+  __device__ __forceinline__ void add2x2(uint32_t p, uint32_t w0, uint32_t w1, uint32_t q,
+                                         uint32_t w2, uint32_t w3) const {
+    add2(p, w0, w1);
+    add2(q, w2, w3);
   }
   __device__ __forceinline__ void addsub(uint32_t base, uint32_t win, uint32_t wout) const {
     uint32_t alo, ahi, ac, blo, bhi, bc;
@@ -1132,9 +1216,14 @@ __device__ __forceinline__ void delta_step(const Ops &ops, const uint32_t *pe, c
 #pragma unroll 2
   for (; (g + 1) * K - 1 <= 2 * r; ++g) {
     a = load(pe + g * K);
-    if (RM) b = load(pl + g * K);
+    if (RM) {
+      b = load(pl + g * K);
 #pragma unroll
-    for (int q = 0; q < K; ++q) upd(h0, VecOf<K>::at(a, q), VecOf<K>::at(b, q));
+      for (int q = 0; q < K; ++q) upd(h0, VecOf<K>::at(a, q), VecOf<K>::at(b, q));
+    } else {
+#pragma unroll
+      for (int q = 0; q < K; q += 2) ops.add2(h0, VecOf<K>::at(a, q), VecOf<K>::at(a, q + 1));
+    }
   }
   for (; g < ngroups; ++g) {
     a = load(pe + g * K);
@@ -1189,8 +1278,14 @@ __device__ __forceinline__ void delta_step_split(const Ops &ops, const uint32_t 
     const V a = load(pe + g * K);
     V b = V{};
     if (RM) b = load(pl + g * K);
+    if (!RM && K == 4) {
+      // the fill only adds: H_even's two words chain, as do H_odd's
+      ops.add2x2(hev, at(a, 0), at(a, 2), hod, at(a, 1), at(a, 3));
+    } else {
 #pragma unroll
-    for (int q = 0; q < K; q += 2) both(hev, at(a, q), at(b, q), hod, at(a, q + 1), at(b, q + 1));
+      for (int q = 0; q < K; q += 2)
+        both(hev, at(a, q), at(b, q), hod, at(a, q + 1), at(b, q + 1));
+    }
   }
   // the c = 2r + 1 - nfull*K remaining window words (c odd, 1 <= c < K);
   // the last is even and goes to H_even together with D_1's leaving word 0
