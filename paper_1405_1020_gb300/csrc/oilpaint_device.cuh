@@ -494,9 +494,19 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
     const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
     uint4 *d16 = reinterpret_cast<uint4 *>(dst);
     const uint32_t nq = w >> 2;
-    for (uint32_t q = tid; q < nq; q += nthr) {
-      const uint4 p = __ldg(s16 + q);
-      d16[q] = make_uint4(rgba(p.x), rgba(p.y), rgba(p.z), rgba(p.w));
+    // four 16-byte loads in flight per thread before any conversion
+    for (uint32_t q0 = tid; q0 < nq; q0 += 4u * nthr) {
+      uint4 p[4];
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        const uint32_t q = q0 + k * nthr;
+        if (q < nq) p[k] = __ldg(s16 + q);
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < 4u; ++k) {
+        const uint32_t q = q0 + k * nthr;
+        if (q < nq) d16[q] = make_uint4(rgba(p[k].x), rgba(p[k].y), rgba(p[k].z), rgba(p[k].w));
+      }
     }
     x0 = nq << 2;
   } else if (d.bpp == 3 && (a & 3u) == 0) {
