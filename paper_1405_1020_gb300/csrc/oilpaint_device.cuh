@@ -264,25 +264,6 @@ __device__ __forceinline__ void cnt_add(uint32_t addr, uint32_t d) {
       "r"(d));
 }
 
-// Two independent 64-bit read-modify-writes issued together: +(alo,ahi) at
-// addr_a and -(blo,bhi) at addr_b.  Both loads are issued before either add,
-// so the two updates share one shared-memory latency.  addr_a != addr_b.
-__device__ __forceinline__ void bin_addsub64(uint32_t addr_a, uint32_t alo, uint32_t ahi,
-                                             uint32_t addr_b, uint32_t blo, uint32_t bhi) {
-  if (!OPK_SMEM_OK(addr_a, 8u) || !OPK_SMEM_OK(addr_b, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
-      "add.cc.u32 a0, a0, %1;\n\t"
-      "addc.u32 a1, a1, %2;\n\t"
-      "sub.cc.u32 b0, b0, %4;\n\t"
-      "subc.u32 b1, b1, %5;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(addr_a),
-      "r"(alo), "r"(ahi), "r"(addr_b), "r"(blo), "r"(bhi));
-}
-
 // Two 64-bit additions issued together (addr_a != addr_b).
 __device__ __forceinline__ void bin_add64x2(uint32_t addr_a, uint32_t alo, uint32_t ahi,
                                             uint32_t addr_b, uint32_t blo, uint32_t bhi) {
@@ -416,19 +397,38 @@ __device__ __forceinline__ void bin_addsub64x2_chain(uint32_t A, uint32_t alo, u
       "r"(dlo), "r"(dhi));
 }
 
-// The same for two 32-bit counts: +da at addr_a, -db at addr_b.
-__device__ __forceinline__ void cnt_addsub(uint32_t addr_a, uint32_t da, uint32_t addr_b,
-                                           uint32_t db) {
-  if (!OPK_SMEM_OK(addr_a, 4u) || !OPK_SMEM_OK(addr_b, 4u)) return;
+// Variant B bins (64-bit sums at As / Bs, 32-bit counts at Ac / Bc): +(alo,
+// ahi, ac) at A and -(blo, bhi, bc) at B, all loads first; As == Bs implies
+// Ac == Bc, and then the subtraction applies to the sum (as
+// bin_addsub64_chain).
+__device__ __forceinline__ void binb_addsub_chain(uint32_t As, uint32_t Ac, uint32_t alo,
+                                                  uint32_t ahi, uint32_t ac, uint32_t Bs,
+                                                  uint32_t Bc, uint32_t blo, uint32_t bhi,
+                                                  uint32_t bc) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
+      !OPK_SMEM_OK(Bc, 4u))
+    return;
   asm volatile(
-      "{\n\t.reg .u32 a, b;\n\t"
-      "ld.shared.u32 a, [%0];\n\t"
-      "ld.shared.u32 b, [%2];\n\t"
-      "add.u32 a, a, %1;\n\t"
-      "sub.u32 b, b, %3;\n\t"
-      "st.shared.u32 [%0], a;\n\t"
-      "st.shared.u32 [%2], b;\n\t}" ::"r"(addr_a),
-      "r"(da), "r"(addr_b), "r"(db));
+      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t.reg .pred p;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u32 a2, [%1];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
+      "ld.shared.u32 b2, [%6];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "setp.eq.u32 p, %0, %5;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "selp.b32 b2, a2, b2, p;\n\t"
+      "sub.cc.u32 b0, b0, %7;\n\t"
+      "subc.u32 b1, b1, %8;\n\t"
+      "sub.u32 b2, b2, %9;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u32 [%1], a2;\n\t"
+      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
+      "st.shared.u32 [%6], b2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
 }
 
 // ------------------------------------------------------------ pack prepass
@@ -553,15 +553,14 @@ __device__ __forceinline__ void delta_b(uint32_t w, uint32_t &lo, uint32_t &hi) 
 // One histogram owned by one thread (one output column per thread, word
 // format 0): level l of thread t lives at sums + l * NT * 8 (+ cnts + l * NT
 // * 4 for variant B), so the 32 lanes of a warp always touch 32 consecutive
-// bins whatever their levels.  Level L is a scratch bin that absorbs the
-// no-op half of a paired update.
+// bins whatever their levels.  Level L exists but the argmax never reads it
+// (literal mode's white pixels land there).
 template <int NT, int VAR>
 struct Hist {
   static constexpr uint32_t kStride64 = NT * 8u;
   static constexpr uint32_t kStride32 = NT * 4u;
   uint32_t sums;     // smem address of level 0's 64-bit bin
   uint32_t cnts;     // smem address of level 0's count (variant B)
-  uint32_t scratch;  // level L (the scratch bin), as a level index
 
   __device__ __forceinline__ void clear(uint32_t L) const {
     for (uint32_t l = 0; l < L; ++l) {
@@ -589,26 +588,18 @@ struct Hist {
     bin_sub64(sums + lvl * kStride64, lo, hi);
     if (VAR == kVarB) cnt_add(cnts + lvl * kStride32, 0xFFFFFFFFu);
   }
-  // Adds pixel win and removes pixel wout as one two-deep update.  When both
-  // fall in the same level the net delta goes to that bin and the removal is
-  // redirected to the scratch bin, so the two addresses always differ.
+  // Adds pixel win and removes pixel wout as one two-deep update; when both
+  // fall in the same level the removal applies to the sum (chained).
   __device__ __forceinline__ void addsub(uint32_t win, uint32_t wout) const {
-    const uint32_t la = win >> 24;
-    uint32_t lb = wout >> 24;
+    const uint32_t la = win >> 24, lb = wout >> 24;
     uint32_t alo, ahi, blo, bhi;
     delta(win, alo, ahi);
     delta(wout, blo, bhi);
-    uint32_t ca = 1u;
-    if (la == lb) {
-      const uint64_t net = (static_cast<uint64_t>(ahi) << 32 | alo) -
-                           (static_cast<uint64_t>(bhi) << 32 | blo);
-      alo = static_cast<uint32_t>(net);
-      ahi = static_cast<uint32_t>(net >> 32);
-      ca = 0u;
-      lb = scratch;
-    }
-    bin_addsub64(sums + la * kStride64, alo, ahi, sums + lb * kStride64, blo, bhi);
-    if (VAR == kVarB) cnt_addsub(cnts + la * kStride32, ca, cnts + lb * kStride32, 1u);
+    if (VAR == kVarA)
+      bin_addsub64_chain(sums + la * kStride64, alo, ahi, sums + lb * kStride64, blo, bhi);
+    else
+      binb_addsub_chain(sums + la * kStride64, cnts + la * kStride32, alo, ahi, 1u,
+                        sums + lb * kStride64, cnts + lb * kStride32, blo, bhi, 1u);
   }
   // Count of level l, for variant A kept in place in bits 22..31 of the high
   // word (comparing these words compares counts).
@@ -741,38 +732,6 @@ struct DeltaOpsA {
     bin_add64x2(dh_addr<NT>(p, wp), plo, phi, dh_addr<NT>(q, wq), qlo, qhi);
   }
 };
-
-// binb_addsub for bins that may coincide (As == Bs implies Ac == Bc): the
-// subtraction is applied to the sum when they do, as bin_addsub64_chain.
-__device__ __forceinline__ void binb_addsub_chain(uint32_t As, uint32_t Ac, uint32_t alo,
-                                                  uint32_t ahi, uint32_t ac, uint32_t Bs,
-                                                  uint32_t Bc, uint32_t blo, uint32_t bhi,
-                                                  uint32_t bc) {
-  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
-      !OPK_SMEM_OK(Bc, 4u))
-    return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t.reg .pred p;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u32 a2, [%1];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
-      "ld.shared.u32 b2, [%6];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "setp.eq.u32 p, %0, %5;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "selp.b32 b2, a2, b2, p;\n\t"
-      "sub.cc.u32 b0, b0, %7;\n\t"
-      "subc.u32 b1, b1, %8;\n\t"
-      "sub.u32 b2, b2, %9;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u32 [%1], a2;\n\t"
-      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
-      "st.shared.u32 [%6], b2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
-}
 
 // Two additions at two distinct bins (signs folded into the deltas).
 __device__ __forceinline__ void binb_add_x2(uint32_t As, uint32_t Ac, uint32_t alo, uint32_t ahi,
@@ -1115,7 +1074,6 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
   Hist<NT, VAR> h;
   h.sums = sm.sums + static_cast<uint32_t>(t) * 8u;
   h.cnts = sm.cnts + static_cast<uint32_t>(t) * 4u;
-  h.scratch = L;
   h.clear(L);
 
   return ring_pass(
