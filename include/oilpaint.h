@@ -157,6 +157,12 @@ int op_default_config(int32_t radius, uint32_t levels, op_config_t *cfg);
  * (read by later op_create / op_batch_set calls).  Not persisted. */
 int op_tune_table_set(int32_t radius, uint32_t levels, const op_config_t *cfg);
 
+/* Record a tuned configuration for a batch group whose largest radius and
+ * level count are (max_radius, max_levels) (see op_batch_create); read by
+ * later op_batch_create calls with cfg NULL, before the single-image table.
+ * path must be 0; cfg NULL removes the entry.  Not persisted. */
+int op_batch_tune_table_set(int32_t max_radius, uint32_t max_levels, const op_config_t *cfg);
+
 /* Bytes of device workspace op_run needs: the packed-word image of
  * section 4's per-pixel level and colour (one 32-bit word per pixel, rows
  * padded to 16 bytes). */
@@ -236,21 +242,37 @@ typedef struct op_batch_s op_batch_t;
 /*
  * op_batch_create -- a batch runner for up to `max_images` images holding at
  * most `max_pixels` pixels in total, every radius <= max_radius and level
- * count <= max_levels.  All images of a run share one persistent kernel
- * launch: each CTA takes (image, tile) tickets from a device-side atomic
- * counter until the queue is empty.  cfg: tile_w, chunk_rows, prefetch and
- * cols_per_thread of that launch (NULL = defaults; tile_h is chosen per
- * image); with 2 or 4 columns per thread, images of <= 32 levels take the
- * difference-histogram path and the others one column per thread with
- * tile_w / cols_per_thread threads.  Returns NULL
- * with op_last_error() on failure.
+ * count <= max_levels.  The images of a run are split into up to four
+ * groups -- radius above 15 or not (when max_radius > 15), levels above 20
+ * or not (when max_levels > 20) -- and each group is one persistent kernel
+ * launch whose CTAs take (image, tile) tickets from the group's device-side
+ * atomic counter until its queue is empty; the groups' launches run
+ * concurrently on streams forked from the caller's.  cfg: tile_w,
+ * chunk_rows, prefetch and cols_per_thread of every group's launch (path
+ * must be 0); NULL = per group, the first that fits of the batch tuning
+ * table's entry for the group's largest radius and level count
+ * (op_batch_tune_table_set), the single-image table's entry for them and a
+ * built-in default.  tile_h is chosen per image.  With 2 or 4 columns per thread,
+ * images of <= 32 levels take the difference-histogram path and the others
+ * one column per thread with tile_w / cols_per_thread threads.  Returns NULL
+ * with op_last_error() on failure (OP_E_UNSUPPORTED: cfg does not fit a
+ * group's largest image in one CTA).
  */
 op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t max_radius,
                             uint32_t max_levels, const op_config_t *cfg);
 
-/* Launch configuration of the batch's persistent kernel into *cfg (tile_h
- * is 0: it is chosen per image). */
+/* Launch configuration of the first group's persistent kernel into *cfg
+ * (tile_h is 0: it is chosen per image). */
 int op_batch_get_config(const op_batch_t *b, op_config_t *cfg);
+
+/* Number of image groups of the batch (1, 2 or 4), or OP_E_INVALID. */
+int op_batch_group_count(const op_batch_t *b);
+
+/* Group `group`'s launch configuration and the largest radius and level
+ * count it holds (each output pointer may be NULL); OP_E_INVALID if group
+ * is out of range. */
+int op_batch_get_group(const op_batch_t *b, uint32_t group, op_config_t *cfg,
+                       int32_t *max_radius, uint32_t *max_levels);
 
 /* Device workspace a batch needs: descriptors, tensor maps, tile tables and
  * the packed-word images of max_pixels pixels. */
@@ -269,8 +291,9 @@ int op_batch_set_workspace(op_batch_t *b, void *d_ws, size_t bytes);
  */
 int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stream);
 
-/* Launch the batch's pack kernel and persistent filter kernel on `stream`
- * (2 launches, fixed grids). */
+/* Launch the batch's pack kernel and one persistent filter kernel per group
+ * (1 + groups launches, fixed grids) on `stream` and, forked from it and
+ * joined back into it, the batch's side streams. */
 int op_batch_run(op_batch_t *b, void *stream);
 
 /* Capture op_batch_run's launches into a CUDA graph owned by `b` (replacing

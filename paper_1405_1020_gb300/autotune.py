@@ -109,9 +109,91 @@ def load_table(path: str = TABLE_PATH) -> int:
     return load_tuning(path)
 
 
-def save_table(entries: dict, path: str, device_name: str) -> None:
+def save_table(entries: dict, path: str, device_name: str, batch_entries: dict | None = None
+               ) -> None:
+    table = {"device": device_name, "entries": entries}
+    if batch_entries:
+        table["batch_entries"] = batch_entries
     with open(path, "w") as f:
-        json.dump({"device": device_name, "entries": entries}, f, indent=1, sort_keys=True)
+        json.dump(table, f, indent=1, sort_keys=True)
+
+
+def batch_candidates() -> list[dict]:
+    """Persistent-kernel configurations tried for one batch group: threads
+    per CTA x output columns per thread x halo chunk height (one chunk in
+    flight)."""
+    return [{"tile_w": nt * cpt, "tile_h": 0, "chunk_rows": ch, "prefetch": 1,
+             "cols_per_thread": cpt, "path": 0}
+            for nt, cpt, ch in itertools.product((32, 64, 128), (1, 2, 4), (1, 2, 4))]
+
+
+def tune_batch(images: list[dict], max_radius: int, max_levels: int, reps: int = 7,
+               rounds: int = 1, verbose: bool = False) -> dict:
+    """Tune the configuration of each group of a batch created for
+    (max_radius, max_levels) on `images` (dicts with src, w, h, stride, bpp,
+    r, L; CUDA uint8 sources): coordinate descent over the groups, each
+    candidate timed as the median of `reps` graph replays and required to
+    write the same bytes as the first.  Records the winners in the library's
+    batch table; returns {"max_radius,max_levels": {"config", "ms"}} per group
+    and the batch time under the winners."""
+    from .filter import Batch
+
+    pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
+    stream = torch.cuda.Stream()
+    outs = [torch.empty_like(im["src"]) for im in images]
+    descs = [(im["src"], o, im["w"], im["h"], im["stride"], im["bpp"], im["r"], im["L"])
+             for im, o in zip(images, outs)]
+    torch.cuda.synchronize()
+
+    def time_batch():
+        b = Batch(len(images), pix + 4096, max_radius, max_levels)
+        try:
+            b.set(descs, stream)
+            b.capture(stream)
+            for _ in range(2):
+                b.launch_graph(stream)
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+            for e0, e1 in evs:
+                e0.record(stream)
+                b.launch_graph(stream)
+                e1.record(stream)
+            if b.sync_status(stream) != B.OP_OK:
+                raise B.OilPaintError("device error in the batch")
+            groups = b.groups()
+        finally:
+            b.close()
+        return statistics.median(e0.elapsed_time(e1) for e0, e1 in evs), groups
+
+    base_ms, groups = time_batch()
+    ref = [o.clone() for o in outs]
+    keys = [(g["max_radius"], g["max_levels"]) for g in groups]
+    best = {k: dict(g["config"]) for k, g in zip(keys, groups)}
+    best_ms = base_ms
+    for _ in range(rounds):
+        for k in keys:
+            for cfg in batch_candidates():
+                B.check(B.op_batch_tune_table_set(k[0], k[1], B.op_config_t.make(**cfg)),
+                        "op_batch_tune_table_set")
+                try:
+                    ms, got = time_batch()
+                except B.OilPaintError as e:
+                    if e.status == B.OP_E_UNSUPPORTED:
+                        continue
+                    raise
+                # a candidate that does not fit the group falls back: skip it
+                gcfg = got[keys.index(k)]["config"]
+                if any(gcfg[f] != cfg[f] for f in ("tile_w", "chunk_rows", "cols_per_thread")):
+                    continue
+                if not all(torch.equal(a, c) for a, c in zip(ref, outs)):
+                    raise B.OilPaintError(f"batch config {cfg} for group {k} changed the output")
+                if verbose:
+                    print(f"group {k} {cfg} {ms:.4f} ms")
+                if ms < best_ms:
+                    best_ms, best[k] = ms, dict(cfg)
+            B.check(B.op_batch_tune_table_set(k[0], k[1], B.op_config_t.make(**best[k])),
+                    "op_batch_tune_table_set")
+    return {"groups": {f"{k[0]},{k[1]}": {"config": best[k]} for k in keys},
+            "ms": best_ms, "ms_untuned": base_ms}
 
 
 def tune_pairs(pairs, width: int = 4000, height: int = 3000, bpp: int = 4, reps: int = 5,

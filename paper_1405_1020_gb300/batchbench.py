@@ -101,6 +101,7 @@ def run(steps: int = 10, warmup: int = 3, n: int = 64, config=None) -> dict:
     ms_graph = statistics.median(t_graph)
     ms_eager = statistics.median(t_eager)
     cfg = batch.config()
+    groups = batch.groups()
     for op in ops:
         op.close()
     batch.close()
@@ -113,7 +114,10 @@ def run(steps: int = 10, warmup: int = 3, n: int = 64, config=None) -> dict:
         "plain_mpix_s": round(total_px / ms_plain / 1e3, 1),
         "batched_mpix_s": round(total_px / ms_graph / 1e3, 1),
         "speedup_vs_plain": round(ms_plain / ms_graph, 3),
-        "launches_plain": 2 * n, "launches_batched": 4 if max_r > 15 else 2,
+        "launches_plain": 2 * n, "launches_batched": 1 + len(groups),
         "identical_outputs": identical, "config": cfg,
+        "groups": [{"max_radius": g["max_radius"], "max_levels": g["max_levels"],
+                    **{k: g["config"][k] for k in ("tile_w", "chunk_rows", "cols_per_thread")}}
+                   for g in groups],
     }
 

@@ -40,11 +40,13 @@ LIB_PATH = os.path.join(_PKG, "liboilpaint_checked.so" if os.environ.get("OPK_LI
 # every symbol include/oilpaint.h declares
 EXPORTS = (
     "op_create", "op_create_ex", "op_last_error", "op_status_string", "op_get_config",
-    "op_set_config", "op_default_config", "op_tune_table_set", "op_workspace_size",
+    "op_set_config", "op_default_config", "op_tune_table_set",
+    "op_batch_tune_table_set", "op_workspace_size",
     "op_set_workspace", "op_run", "op_run_host", "op_run_host_async", "op_set_profile_event",
     "op_sync_status",
     "op_destroy",
-    "op_batch_create", "op_batch_get_config", "op_batch_workspace_size",
+    "op_batch_create", "op_batch_get_config", "op_batch_group_count", "op_batch_get_group",
+    "op_batch_workspace_size",
     "op_batch_set_workspace", "op_batch_set",
     "op_batch_run", "op_batch_capture", "op_batch_launch_graph", "op_batch_sync_status",
     "op_batch_destroy", "op_selftest_wait_timeout", "op_run_noalloc",
@@ -104,6 +106,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "op_set_config": (ci, [vp, cfgp]),
         "op_default_config": (ci, [i32, u32, cfgp]),
         "op_tune_table_set": (ci, [i32, u32, cfgp]),
+        "op_batch_tune_table_set": (ci, [i32, u32, cfgp]),
         "op_workspace_size": (sz, [vp]),
         "op_set_workspace": (ci, [vp, vp, sz]),
         "op_run": (ci, [vp, vp, vp, vp]),
@@ -114,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "op_destroy": (ci, [vp]),
         "op_batch_create": (vp, [u32, u64, i32, u32, cfgp]),
         "op_batch_get_config": (ci, [vp, cfgp]),
+        "op_batch_group_count": (ci, [vp]),
+        "op_batch_get_group": (ci, [vp, u32, cfgp, ctypes.POINTER(i32), ctypes.POINTER(u32)]),
         "op_batch_workspace_size": (sz, [vp]),
         "op_batch_set_workspace": (ci, [vp, vp, sz]),
         "op_batch_set": (ci, [vp, ctypes.POINTER(op_image_t), u32, vp]),
@@ -178,6 +183,12 @@ def op_tune_table_set(radius, levels, cfg: op_config_t):
     return load().op_tune_table_set(radius, levels, ctypes.byref(cfg))
 
 
+def op_batch_tune_table_set(max_radius, max_levels, cfg: op_config_t | None):
+    """cfg None removes the entry."""
+    return load().op_batch_tune_table_set(max_radius, max_levels,
+                                          None if cfg is None else ctypes.byref(cfg))
+
+
 def op_workspace_size(op):
     return load().op_workspace_size(op)
 
@@ -217,6 +228,17 @@ def op_batch_create(max_images, max_pixels, max_radius, max_levels, cfg: op_conf
 
 def op_batch_get_config(b, cfg: op_config_t):
     return load().op_batch_get_config(b, ctypes.byref(cfg))
+
+
+def op_batch_group_count(b):
+    return load().op_batch_group_count(b)
+
+
+def op_batch_get_group(b, group: int, cfg: op_config_t, max_radius, max_levels):
+    """max_radius / max_levels: ctypes.c_int32 / c_uint32 (or None)."""
+    return load().op_batch_get_group(b, group, ctypes.byref(cfg),
+                                     None if max_radius is None else ctypes.byref(max_radius),
+                                     None if max_levels is None else ctypes.byref(max_levels))
 
 
 def op_batch_workspace_size(b):

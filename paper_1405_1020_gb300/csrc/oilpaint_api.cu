@@ -102,6 +102,8 @@ struct NvtxRange {
 
 std::mutex g_tune_mu;
 std::map<std::pair<int, uint32_t>, op_config_t> g_tune;
+// batch groups, keyed by the group's largest radius and level count
+std::map<std::pair<int, uint32_t>, op_config_t> g_batch_tune;
 
 // Output columns per thread and threads per CTA of a configuration.
 int cols_per_thread(const op_config_t &c) {
@@ -455,6 +457,19 @@ int op_tune_table_set(int32_t radius, uint32_t levels, const op_config_t *cfg) {
   return OP_OK;
 }
 
+int op_batch_tune_table_set(int32_t max_radius, uint32_t max_levels, const op_config_t *cfg) {
+  if (max_radius < 0 || max_radius > OP_MAX_RADIUS || max_levels < 1 ||
+      max_levels > OP_MAX_LEVELS)
+    return OP_E_INVALID;
+  if (cfg && (!config_in_range(*cfg) || cfg->path != 0u)) return OP_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (cfg)
+    g_batch_tune[{max_radius, max_levels}] = *cfg;
+  else
+    g_batch_tune.erase({max_radius, max_levels});
+  return OP_OK;
+}
+
 size_t op_workspace_size(const op_t *op) {
   if (!op) return 0;
   return static_cast<size_t>(op->ppitch) * op->h * 4u;
@@ -624,23 +639,28 @@ struct op_batch_s {
   uint32_t max_L;
   int device;
   DevInfo di;
-  op_config_t cfg;
-  // Images of radius <= 15 (8-byte bins) and above (12-byte bins) run as two
-  // groups, each one persistent launch with its own shared-memory size, grid,
-  // ticket queue and tables, so the small-radius group is not held to the
-  // occupancy of the large one.  The second group is launched on a side
-  // stream forked from the caller's, so it fills the first group's tail.
-  int groups;  // 1 when max_r <= 15, else 2
-  RingCfg rc[2];
-  size_t smem[2];
-  int grid_persist[2];
-  int grid_pack;
-  uint32_t gn[2] = {0, 0};
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // Images are split by radius (above 15: 12-byte bins) and by level count
+  // (above kBatchLevelSplit: larger histograms) into up to four groups.  Each
+  // group is one persistent launch with its own configuration, shared-memory
+  // size, grid, ticket queue and table segment, so images with small
+  // histograms are not held to the occupancy of the largest ones.  Groups
+  // other than the first run on side streams forked from the caller's, the
+  // costliest first, so the cheaper groups fill the tails of the others.
+  bool split_r = false, split_L = false;
+  int groups = 1;
+  int32_t group_r[opk::kBatchGroups] = {};
+  uint32_t group_L[opk::kBatchGroups] = {};
+  op_config_t gcfg[opk::kBatchGroups] = {};
+  RingCfg rc[opk::kBatchGroups] = {};
+  size_t smem[opk::kBatchGroups] = {};
+  int grid_persist[opk::kBatchGroups] = {};
+  int grid_pack = 0;
+  uint32_t gn[opk::kBatchGroups] = {};
+  cudaStream_t side[opk::kBatchGroups - 1] = {};
+  cudaEvent_t fork = nullptr, join[opk::kBatchGroups - 1] = {};
   // workspace layout
-  size_t off_ctrl, off_hdr, off_descs[2], off_maps, off_tile_prefix[2], off_row_prefix[2],
-      off_packed, total;
+  size_t off_ctrl, off_hdr, off_descs, off_maps, off_tile_prefix, off_row_prefix, off_packed,
+      total;
   size_t stage_bytes;  // hdr .. row_prefix, copied in one transfer
   uint8_t *ws = nullptr;
   bool ws_owned = false;
@@ -650,7 +670,44 @@ struct op_batch_s {
   uint32_t n = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+
+  int group_of(int32_t r, uint32_t L) const {
+    const int rb = split_r && r > opk::kMaxRadiusA ? 1 : 0;
+    const int lb = split_L && L > opk::kBatchLevelSplit ? 1 : 0;
+    return rb * (split_L ? 2 : 1) + lb;
+  }
 };
+
+namespace {
+
+// Control block words: [1] error word, [2 .. 2 + kBatchGroups) the groups'
+// ticket queues, [8 .. 24) the timeout diagnostic record.
+constexpr uint32_t kCtrlWords = 24;
+constexpr uint32_t kCtrlQueue = 2;
+// Header words: image count of each group, index of its first descriptor,
+// index of its first tile-prefix entry, then the batch's image count.
+constexpr uint32_t kHdrCount = 0;
+constexpr uint32_t kHdrDesc = opk::kBatchGroups;
+constexpr uint32_t kHdrPrefix = 2 * opk::kBatchGroups;
+constexpr uint32_t kHdrTotal = 3 * opk::kBatchGroups;
+constexpr uint32_t kHdrWords = kHdrTotal + 1;
+
+// Whether configuration c runs every image of a group bounded by radius r and
+// L levels in one persistent CTA; its shared memory and CTAs per SM if so.
+bool batch_group_fits(const op_config_t &c, int32_t r, uint32_t L, const DevInfo &di,
+                      size_t *smem, int *occ) {
+  if (!config_in_range(c) || c.path != 0u) return false;
+  const BatchNeeds nd = batch_needs(c, r, L);
+  const size_t sm = batch_smem(c, nd);
+  if (nd.boxw > 256u || sm > di.smem_optin - 1024u) return false;
+  const int o = opk::tile_occupancy(threads_of(c), true, cols_per_thread(c), -1, sm);
+  if (o < 1) return false;
+  *smem = sm;
+  *occ = o;
+  return true;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -660,6 +717,14 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
       max_radius > OP_MAX_RADIUS || max_levels < 1 || max_levels > OP_MAX_LEVELS ||
       max_pixels > (1ull << 34)) {
     g_last_error = OP_E_INVALID;
+    return nullptr;
+  }
+  if (cfg && (!config_in_range(*cfg))) {
+    g_last_error = OP_E_INVALID;
+    return nullptr;
+  }
+  if (cfg && cfg->path != 0u) {  // the persistent kernel keeps histograms per thread
+    g_last_error = OP_E_UNSUPPORTED;
     return nullptr;
   }
   int dev = 0;
@@ -673,56 +738,6 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
     g_last_error = st;
     return nullptr;
   }
-  op_config_t c;
-  if (cfg) {
-    c = *cfg;
-  } else {
-    // Batch default: the first of a preference list whose every group fits.
-    // A mixed batch shares one shape across all its radii and level counts,
-    // so the single-image tuning table (one image of the largest radius and
-    // level count) is not what it needs: on GB300 the 64-image mixed batch
-    // ran fastest with 64 threads x 2 columns (a smaller histogram per CTA
-    // than 4 columns) and 2-row halo chunks.
-    static const uint32_t prefs[][2] = {{64, 2}, {32, 2}, {32, 4}, {64, 1}, {32, 1}};
-    bool found = false;
-    for (const auto &p : prefs) {
-      c = op_config_t{p[0] * p[1], 0, 2, 1, p[1], 0};
-      bool fits = true;
-      for (int g = 0; g < (max_radius > opk::kMaxRadiusA ? 2 : 1) && fits; ++g) {
-        const BatchNeeds nd = batch_needs(
-            c, g ? max_radius : std::min(max_radius, static_cast<int32_t>(opk::kMaxRadiusA)),
-            max_levels);
-        fits = nd.boxw <= 256u && batch_smem(c, nd) <= di.smem_optin - 1024u;
-      }
-      if (fits) {
-        found = true;
-        break;
-      }
-    }
-    if (!found) {
-      g_last_error = OP_E_UNSUPPORTED;
-      return nullptr;
-    }
-  }
-  if (!config_in_range(c)) {
-    g_last_error = OP_E_INVALID;
-    return nullptr;
-  }
-  if (c.path != 0u) {  // the persistent kernel keeps histograms per thread
-    g_last_error = OP_E_UNSUPPORTED;
-    return nullptr;
-  }
-  const int groups = max_radius > opk::kMaxRadiusA ? 2 : 1;
-  const int group_r[2] = {std::min(max_radius, static_cast<int32_t>(opk::kMaxRadiusA)),
-                          max_radius};
-  BatchNeeds needs[2];
-  for (int g = 0; g < groups; ++g) {
-    needs[g] = batch_needs(c, group_r[g], max_levels);
-    if (needs[g].boxw > 256u || batch_smem(c, needs[g]) > di.smem_optin - 1024u) {
-      g_last_error = OP_E_UNSUPPORTED;
-      return nullptr;
-    }
-  }
   op_batch_t *b = new (std::nothrow) op_batch_t();
   if (!b) {
     g_last_error = OP_E_NOMEM;
@@ -734,49 +749,86 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
   b->max_L = max_levels;
   b->device = dev;
   b->di = di;
-  b->cfg = c;
-  b->groups = groups;
-  for (int g = 0; g < groups; ++g) {
-    b->rc[g] = opk::make_ring(group_r[g], c.chunk_rows, c.prefetch, needs[g].boxw);
-    b->smem[g] = batch_smem(c, needs[g]);
-    const int occ = opk::tile_occupancy(threads_of(c), true, cols_per_thread(c), -1, b->smem[g]);
-    if (occ < 1) {
+  b->split_r = max_radius > opk::kMaxRadiusA;
+  b->split_L = max_levels > opk::kBatchLevelSplit;
+  b->groups = (b->split_r ? 2 : 1) * (b->split_L ? 2 : 1);
+  for (int rb = 0; rb <= (b->split_r ? 1 : 0); ++rb)
+    for (int lb = 0; lb <= (b->split_L ? 1 : 0); ++lb) {
+      const int g = rb * (b->split_L ? 2 : 1) + lb;
+      b->group_r[g] = rb ? max_radius : std::min(max_radius, int32_t{opk::kMaxRadiusA});
+      b->group_L[g] = lb ? max_levels : std::min(max_levels, opk::kBatchLevelSplit);
+    }
+  for (int g = 0; g < b->groups; ++g) {
+    const int32_t r = b->group_r[g];
+    const uint32_t L = b->group_L[g];
+    size_t sm = 0;
+    int occ = 0;
+    bool found = false;
+    if (cfg) {
+      found = batch_group_fits(*cfg, r, L, di, &sm, &occ);
+      b->gcfg[g] = *cfg;
+    } else {
+      // Default: the first that fits a persistent CTA of the batch tuning
+      // table's entry for the group's bounds, the single-image table's entry
+      // for an image of those bounds, and a preference list (on GB300 the
+      // mixed batches ran fastest with 64 threads x 2 columns and 2-row
+      // halo chunks where neither table has an entry).
+      std::vector<op_config_t> cands;
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_batch_tune.find({r, L});
+        if (it != g_batch_tune.end()) cands.push_back(it->second);
+        it = g_tune.find({r, L});
+        if (it != g_tune.end()) cands.push_back(it->second);
+      }
+      static const uint32_t prefs[][2] = {{64, 2}, {32, 2}, {32, 4}, {64, 1}, {32, 1}};
+      for (const auto &p : prefs) cands.push_back(op_config_t{p[0] * p[1], 0, 2, 1, p[1], 0});
+      for (op_config_t c : cands) {
+        c.tile_h = 0;
+        if (batch_group_fits(c, r, L, di, &sm, &occ)) {
+          b->gcfg[g] = c;
+          found = true;
+          break;
+        }
+      }
+    }
+    if (!found) {
       delete b;
       g_last_error = OP_E_UNSUPPORTED;
       return nullptr;
     }
+    const BatchNeeds nd = batch_needs(b->gcfg[g], r, L);
+    b->rc[g] = opk::make_ring(r, b->gcfg[g].chunk_rows, b->gcfg[g].prefetch, nd.boxw);
+    b->smem[g] = sm;
     b->grid_persist[g] = occ * di.sms;
   }
   b->grid_pack = 8 * di.sms;
   size_t o = 0;
-  b->off_ctrl = o;  // queue counters (words 0, 2), error word (1), timeout record (8..23)
-  o = align_up(o + 24 * sizeof(uint32_t), kAlign);
-  b->off_hdr = o;  // image count of each group
-  o = align_up(o + 2 * sizeof(uint32_t), kAlign);
-  for (int g = 0; g < 2; ++g) {
-    b->off_descs[g] = o;
-    o = align_up(o + static_cast<size_t>(max_images) * sizeof(ImgDesc), kAlign);
-  }
+  b->off_ctrl = o;
+  o = align_up(o + kCtrlWords * sizeof(uint32_t), kAlign);
+  b->off_hdr = o;
+  o = align_up(o + kHdrWords * sizeof(uint32_t), kAlign);
+  b->off_descs = o;  // all images, grouped, in run order
+  o = align_up(o + static_cast<size_t>(max_images) * sizeof(ImgDesc), kAlign);
   b->off_maps = o;
   o = align_up(o + static_cast<size_t>(max_images) * sizeof(CUtensorMap), kAlign);
-  for (int g = 0; g < 2; ++g) {
-    b->off_tile_prefix[g] = o;
-    o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
-  }
-  for (int g = 0; g < 2; ++g) {
-    b->off_row_prefix[g] = o;
-    o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
-  }
+  b->off_tile_prefix = o;  // one segment of n_g + 1 entries per group
+  o = align_up(o + (static_cast<size_t>(max_images) + opk::kBatchGroups) * sizeof(uint32_t),
+               kAlign);
+  b->off_row_prefix = o;  // over all images, for the pack kernel
+  o = align_up(o + (static_cast<size_t>(max_images) + 1) * sizeof(uint32_t), kAlign);
   b->off_packed = o;
   b->stage_bytes = o - b->off_hdr;
   o = align_up(o + static_cast<size_t>(max_pixels) * 4u + static_cast<size_t>(max_images) * kAlign,
                kAlign);
   b->total = o;
-  if (cudaMallocHost(&b->h_stage, b->stage_bytes) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->stage_done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaMallocHost(&b->h_stage, b->stage_bytes) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->stage_done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int g = 1; g < b->groups && ok; ++g)
+    ok = cudaStreamCreateWithFlags(&b->side[g - 1], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[g - 1], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     op_batch_destroy(b);
     g_last_error = OP_E_NOMEM;
     return nullptr;
@@ -789,8 +841,22 @@ size_t op_batch_workspace_size(const op_batch_t *b) { return b ? b->total : 0; }
 
 int op_batch_get_config(const op_batch_t *b, op_config_t *cfg) {
   if (!b || !cfg) return OP_E_INVALID;
-  *cfg = b->cfg;
+  *cfg = b->gcfg[0];
   cfg->tile_h = 0;
+  return OP_OK;
+}
+
+int op_batch_group_count(const op_batch_t *b) { return b ? b->groups : OP_E_INVALID; }
+
+int op_batch_get_group(const op_batch_t *b, uint32_t group, op_config_t *cfg,
+                       int32_t *max_radius, uint32_t *max_levels) {
+  if (!b || group >= static_cast<uint32_t>(b->groups)) return OP_E_INVALID;
+  if (cfg) {
+    *cfg = b->gcfg[group];
+    cfg->tile_h = 0;
+  }
+  if (max_radius) *max_radius = b->group_r[group];
+  if (max_levels) *max_levels = b->group_L[group];
   return OP_OK;
 }
 
@@ -822,10 +888,9 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
     b->ws_owned = true;
     b->ctrl_clean = false;
   }
-  // validate and order the images: most expensive tiles first
-  const uint32_t nt = threads_of(b->cfg);
-  const int kc = cols_per_thread(b->cfg);
+  // validate the images and place each in its group
   std::vector<uint32_t> order(n);
+  std::vector<int> grp(n);
   std::vector<opk::Geometry> geo(n);
   std::vector<double> tile_cost(n);
   std::vector<uint32_t> tile_h(n);
@@ -853,14 +918,13 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
       if (it != g_tune.end()) th = it->second.tile_h;
     }
     tile_h[i] = th;  // 0: chosen below from the image's share of the GPU
-    geo[i] = opk::image_geometry(0, nt, kc, im.radius, im.levels, im.width);
+    grp[i] = b->group_of(im.radius, im.levels);
+    const op_config_t &c = b->gcfg[grp[i]];
+    geo[i] = opk::image_geometry(0, threads_of(c), cols_per_thread(c), im.radius, im.levels,
+                                 im.width);
     order[i] = i;
   }
   if (padded > b->max_pixels) return OP_E_INVALID;
-  // group of each image (radius above 15 -> group 1)
-  auto group_of = [&](uint32_t i) {
-    return b->groups == 2 && images[i].radius > opk::kMaxRadiusA ? 1 : 0;
-  };
   // Tile heights: an image gets its pixel share of its group's resident
   // CTAs (two waves' worth when the group holds several images, so that the
   // ticket queue can balance them; one for a lone image) and the waves model
@@ -868,18 +932,18 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
   // lone small request thus spreads over the GPU in short tiles (latency),
   // a large mixed batch keeps tall tiles (less refill per output row).
   {
-    double gpix[2] = {0.0, 0.0};
-    uint32_t gnum[2] = {0, 0};
+    double gpix[opk::kBatchGroups] = {};
+    uint32_t gnum[opk::kBatchGroups] = {};
     for (uint32_t i = 0; i < n; ++i) {
-      gpix[group_of(i)] += static_cast<double>(images[i].width) * images[i].height;
-      ++gnum[group_of(i)];
+      gpix[grp[i]] += static_cast<double>(images[i].width) * images[i].height;
+      ++gnum[grp[i]];
     }
     for (uint32_t i = 0; i < n; ++i) {
       const op_image_t &im = images[i];
       const uint32_t rows = opk::output_window(im.width, im.height, im.radius, im.flags).rows();
       uint32_t th = tile_h[i];
       if (th == 0) {
-        const int g = group_of(i);
+        const int g = grp[i];
         const double share = static_cast<double>(im.width) * im.height / gpix[g] *
                              b->grid_persist[g] * (gnum[g] > 1 ? 2.0 : 1.0);
         th = auto_tile_h(std::max(1u, rows), geo[i].tiles_x, im.radius,
@@ -894,75 +958,74 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
                      th * k * (im.levels + 10.0);
     }
   }
-  // most expensive tiles first within a group
+  // grouped, most expensive tiles first within a group
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
-    const int ga = group_of(a), gc = group_of(c);
-    return ga != gc ? ga < gc : tile_cost[a] > tile_cost[c];
+    return grp[a] != grp[c] ? grp[a] < grp[c] : tile_cost[a] > tile_cost[c];
   });
   // the previous op_batch_set's copy must have left the pinned staging buffer
   if (cudaEventSynchronize(b->stage_done) != cudaSuccess) return OP_E_CUDA;
   auto host = [&](size_t off) { return b->h_stage + (off - b->off_hdr); };
-  uint32_t *hn = reinterpret_cast<uint32_t *>(b->h_stage);
+  uint32_t *hdr = reinterpret_cast<uint32_t *>(host(b->off_hdr));
+  ImgDesc *hd = reinterpret_cast<ImgDesc *>(host(b->off_descs));
   CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(host(b->off_maps));
+  uint32_t *htp = reinterpret_cast<uint32_t *>(host(b->off_tile_prefix));
+  uint32_t *hrp = reinterpret_cast<uint32_t *>(host(b->off_row_prefix));
   const CUtensorMap *dmaps = reinterpret_cast<const CUtensorMap *>(b->ws + b->off_maps);
   size_t poff = b->off_packed;
-  uint32_t gcount[2] = {0, 0};
-  uint64_t gtiles[2] = {0, 0}, grows[2] = {0, 0};
-  for (uint32_t k = 0; k < n; ++k) {
-    const int grp = group_of(order[k]);
-    const uint32_t q = gcount[grp]++;  // index within its group
-    ImgDesc *hd = reinterpret_cast<ImgDesc *>(host(b->off_descs[grp]));
-    uint32_t *htp = reinterpret_cast<uint32_t *>(host(b->off_tile_prefix[grp]));
-    uint32_t *hrp = reinterpret_cast<uint32_t *>(host(b->off_row_prefix[grp]));
-    uint64_t &tiles = gtiles[grp], &rows = grows[grp];
-    const op_image_t &im = images[order[k]];
-    ImgDesc d{};
-    d.in = im.in;
-    d.out = im.out;
-    d.packed = reinterpret_cast<uint32_t *>(b->ws + poff);
-    d.tmap = dmaps + k;
-    d.w = im.width;
-    d.h = im.height;
-    d.stride = im.stride;
-    d.ostride = im.out_stride ? im.out_stride : im.stride;
-    d.bpp = im.bpp;
-    d.r = im.radius;
-    d.L = im.levels;
-    d.mode = im.flags;
-    d.ppitch = packed_pitch(im.width);
-    d.tile_h = tile_h[order[k]];
-    const opk::Geometry &g = geo[order[k]];
-    d.tiles_x = g.tiles_x;
-    d.boxw = g.boxw;
-    d.variant = static_cast<uint32_t>(g.variant);
-    d.kcols = static_cast<uint32_t>(g.kcols);
-    d.xshift = g.xshift;
-    d.fmt = g.fmt;
-    d.path = 0u;
-    const opk::Window win = opk::output_window(d.w, d.h, d.r, d.mode);
-    opk::set_window(d, win);
-    const int st =
-        encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc[0].ch);
-    if (st != OP_OK) return st;
-    hd[q] = d;
-    htp[q] = static_cast<uint32_t>(tiles);
-    hrp[q] = static_cast<uint32_t>(rows);
-    tiles += static_cast<uint64_t>(d.tiles_x) * ((win.rows() + d.tile_h - 1) / d.tile_h);
-    rows += d.h;
-    poff = align_up(poff + static_cast<size_t>(d.ppitch) * d.h * 4u, kAlign);
+  uint64_t rows = 0;
+  uint32_t k = 0;
+  for (int g = 0; g < opk::kBatchGroups; ++g) {
+    const uint32_t first = k;
+    uint64_t tiles = 0;
+    for (; k < n && grp[order[k]] == g; ++k) {
+      const uint32_t i = order[k];
+      const op_image_t &im = images[i];
+      ImgDesc d{};
+      d.in = im.in;
+      d.out = im.out;
+      d.packed = reinterpret_cast<uint32_t *>(b->ws + poff);
+      d.tmap = dmaps + k;
+      d.w = im.width;
+      d.h = im.height;
+      d.stride = im.stride;
+      d.ostride = im.out_stride ? im.out_stride : im.stride;
+      d.bpp = im.bpp;
+      d.r = im.radius;
+      d.L = im.levels;
+      d.mode = im.flags;
+      d.ppitch = packed_pitch(im.width);
+      d.tile_h = tile_h[i];
+      const opk::Geometry &ge = geo[i];
+      d.tiles_x = ge.tiles_x;
+      d.boxw = ge.boxw;
+      d.variant = static_cast<uint32_t>(ge.variant);
+      d.kcols = static_cast<uint32_t>(ge.kcols);
+      d.xshift = ge.xshift;
+      d.fmt = ge.fmt;
+      d.path = 0u;
+      const opk::Window win = opk::output_window(d.w, d.h, d.r, d.mode);
+      opk::set_window(d, win);
+      const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc[g].ch);
+      if (st != OP_OK) return st;
+      hd[k] = d;
+      htp[k + g] = static_cast<uint32_t>(tiles);
+      hrp[k] = static_cast<uint32_t>(rows);
+      tiles += static_cast<uint64_t>(d.tiles_x) * ((win.rows() + d.tile_h - 1) / d.tile_h);
+      rows += d.h;
+      poff = align_up(poff + static_cast<size_t>(d.ppitch) * d.h * 4u, kAlign);
+    }
+    if (tiles >= 0xFFFFFFFFull) return OP_E_INVALID;
+    htp[k + g] = static_cast<uint32_t>(tiles);  // the segment's end
+    hdr[kHdrCount + g] = k - first;
+    hdr[kHdrDesc + g] = first;
+    hdr[kHdrPrefix + g] = first + g;
+    b->gn[g] = k - first;
   }
-  if (poff > b->total) return OP_E_INVALID;
-  for (int g = 0; g < 2; ++g) {
-    if (gtiles[g] >= 0xFFFFFFFFull || grows[g] >= 0xFFFFFFFFull) return OP_E_INVALID;
-    reinterpret_cast<uint32_t *>(host(b->off_tile_prefix[g]))[gcount[g]] =
-        static_cast<uint32_t>(gtiles[g]);
-    reinterpret_cast<uint32_t *>(host(b->off_row_prefix[g]))[gcount[g]] =
-        static_cast<uint32_t>(grows[g]);
-    hn[g] = gcount[g];
-    b->gn[g] = gcount[g];
-  }
+  if (k != n || poff > b->total || rows >= 0xFFFFFFFFull) return OP_E_INVALID;
+  hrp[n] = static_cast<uint32_t>(rows);
+  hdr[kHdrTotal] = n;
   if (!b->ctrl_clean) {
-    if (cudaMemsetAsync(b->ws + b->off_ctrl, 0, 24 * sizeof(uint32_t), s) != cudaSuccess)
+    if (cudaMemsetAsync(b->ws + b->off_ctrl, 0, kCtrlWords * sizeof(uint32_t), s) != cudaSuccess)
       return OP_E_CUDA;
     b->ctrl_clean = true;
   }
@@ -980,35 +1043,33 @@ int op_batch_run(op_batch_t *b, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   uint32_t *ctrl = reinterpret_cast<uint32_t *>(b->ws + b->off_ctrl);
   const uint32_t *hdr = reinterpret_cast<const uint32_t *>(b->ws + b->off_hdr);
-  auto descs = [&](int g) { return reinterpret_cast<const ImgDesc *>(b->ws + b->off_descs[g]); };
-  auto tp = [&](int g) { return reinterpret_cast<const uint32_t *>(b->ws + b->off_tile_prefix[g]); };
-  auto rp = [&](int g) { return reinterpret_cast<const uint32_t *>(b->ws + b->off_row_prefix[g]); };
-  uint32_t *queue[2] = {ctrl + 0, ctrl + 2};
+  const ImgDesc *descs = reinterpret_cast<const ImgDesc *>(b->ws + b->off_descs);
+  const uint32_t *tp = reinterpret_cast<const uint32_t *>(b->ws + b->off_tile_prefix);
+  const uint32_t *rp = reinterpret_cast<const uint32_t *>(b->ws + b->off_row_prefix);
   // Fixed grids; the image counts and the tables are read from device
   // memory, so the launches do not depend on the current batch and a
   // captured graph stays valid across op_batch_set calls.
-  for (int g = 0; g < b->groups; ++g)
-    if (opk::launch_pack_batch(descs(g), rp(g), hdr + g, queue[g], b->grid_pack, s) !=
-        cudaSuccess)
-      return OP_E_CUDA;
-  const uint32_t nt = threads_of(b->cfg);
-  const int k = cols_per_thread(b->cfg);
-  if (b->groups == 2) {
-    // the large-radius group first, on the side stream
-    if (cudaEventRecord(b->fork, s) != cudaSuccess ||
-        cudaStreamWaitEvent(b->side, b->fork, 0) != cudaSuccess)
-      return OP_E_CUDA;
-    if (opk::launch_persistent(nt, k, descs(1), tp(1), hdr + 1, queue[1], b->rc[1], b->max_L,
-                               b->grid_persist[1], b->smem[1], ctrl + 1, kWaitTimeoutNs,
-                               b->side) != cudaSuccess)
-      return OP_E_CUDA;
-    if (cudaEventRecord(b->join, b->side) != cudaSuccess) return OP_E_CUDA;
-  }
-  if (opk::launch_persistent(nt, k, descs(0), tp(0), hdr, queue[0], b->rc[0], b->max_L,
-                             b->grid_persist[0], b->smem[0], ctrl + 1, kWaitTimeoutNs,
-                             s) != cudaSuccess)
+  if (opk::launch_pack_batch(descs, rp, hdr + kHdrTotal, ctrl + kCtrlQueue, opk::kBatchGroups,
+                             b->grid_pack, s) != cudaSuccess)
     return OP_E_CUDA;
-  if (b->groups == 2 && cudaStreamWaitEvent(s, b->join, 0) != cudaSuccess) return OP_E_CUDA;
+  auto launch = [&](int g, cudaStream_t st) {
+    const op_config_t &c = b->gcfg[g];
+    return opk::launch_persistent(threads_of(c), cols_per_thread(c), descs, tp, hdr + g,
+                                  ctrl + kCtrlQueue + g, b->rc[g], b->group_L[g],
+                                  b->grid_persist[g], b->smem[g], ctrl + 1, kWaitTimeoutNs, st);
+  };
+  if (b->groups > 1 && cudaEventRecord(b->fork, s) != cudaSuccess) return OP_E_CUDA;
+  // the costlier groups (larger radius, then more levels) first, each on its
+  // side stream
+  for (int g = b->groups - 1; g >= 1; --g) {
+    cudaStream_t st = b->side[g - 1];
+    if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess || launch(g, st) != cudaSuccess ||
+        cudaEventRecord(b->join[g - 1], st) != cudaSuccess)
+      return OP_E_CUDA;
+  }
+  if (launch(0, s) != cudaSuccess) return OP_E_CUDA;
+  for (int g = 1; g < b->groups; ++g)
+    if (cudaStreamWaitEvent(s, b->join[g - 1], 0) != cudaSuccess) return OP_E_CUDA;
   return OP_OK;
 }
 
@@ -1066,12 +1127,14 @@ int op_batch_destroy(op_batch_t *b) {
   if (!b) return OP_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->side) {
-    cudaStreamSynchronize(b->side);
-    cudaStreamDestroy(b->side);
+  for (int g = 0; g < opk::kBatchGroups - 1; ++g) {
+    if (b->side[g]) {
+      cudaStreamSynchronize(b->side[g]);
+      cudaStreamDestroy(b->side[g]);
+    }
+    if (b->join[g]) cudaEventDestroy(b->join[g]);
   }
   if (b->fork) cudaEventDestroy(b->fork);
-  if (b->join) cudaEventDestroy(b->join);
   if (b->stage_done) cudaEventDestroy(b->stage_done);
   if (b->ws_owned) cudaFree(b->ws);
   cudaFreeHost(b->h_stage);

@@ -45,6 +45,11 @@ constexpr int kVarA = 0;
 constexpr int kVarB = 1;
 constexpr int kMaxRadiusA = 15;
 constexpr int kMaxRadiusB = 44;
+// A batch splits its images into at most this many groups (radius above
+// kMaxRadiusA or not, levels above kBatchLevelSplit or not), each run by its
+// own persistent launch sized for the group's largest radius and level count.
+constexpr int kBatchGroups = 4;
+constexpr uint32_t kBatchLevelSplit = 20;
 
 // bits of the device error word
 constexpr uint32_t kErrTimeout = 1u;

@@ -164,11 +164,17 @@ cudaError_t launch_pack_single(const ImgDesc &d, int grid, cudaStream_t s);
 cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
                         const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
                         uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
-// d_n: device pointer to the number of images (the batch tables are device-resident).
+// d_n: device pointer to the number of images (the batch tables are
+// device-resident); the launch also zeroes the nqueues ticket counters at
+// d_queues for the filter launches that follow it.
 cudaError_t launch_pack_batch(const ImgDesc *d_descs, const uint32_t *d_row_prefix,
-                              const uint32_t *d_n, uint32_t *d_queue, int grid, cudaStream_t s);
+                              const uint32_t *d_n, uint32_t *d_queues, uint32_t nqueues, int grid,
+                              cudaStream_t s);
+// d_grp: device pointer to one group's image count, with the index of its
+// first descriptor kBatchGroups words and of its first tile-prefix entry
+// 2 kBatchGroups words further on.
 cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
-                              const uint32_t *d_tile_prefix, const uint32_t *d_n,
+                              const uint32_t *d_tile_prefix, const uint32_t *d_grp,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
 cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStream_t s);

@@ -37,8 +37,9 @@ __device__ __forceinline__ uint32_t find_image(const uint32_t *__restrict__ pref
 
 __global__ void __launch_bounds__(256)
     pack_batch_kernel(const ImgDesc *__restrict__ descs, const uint32_t *__restrict__ row_prefix,
-                      const uint32_t *__restrict__ d_n, uint32_t *queue) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *queue = 0u;
+                      const uint32_t *__restrict__ d_n, uint32_t *queues, uint32_t nqueues) {
+  // the filter launches that follow start their ticket queues from zero
+  if (blockIdx.x == 0 && threadIdx.x < nqueues) queues[threadIdx.x] = 0u;
   const uint32_t n = __ldg(d_n);
   if (n == 0) return;
   const uint32_t total = __ldg(row_prefix + n);
@@ -94,17 +95,22 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // K = 1: every image on the one-column path; K = 2 or 4: images with
 // d.kcols == K on the difference-histogram path, the others on the
 // one-column path.  Shared memory is sized by the host for the largest.
+// d_grp points at the group's image count; kBatchGroups and 2 kBatchGroups
+// words further on lie the index of its first descriptor and of its first
+// tile-prefix entry, so one fixed launch serves any batch composition.
 template <int NT, int K>
 __global__ void __launch_bounds__(NT, 1)
     persistent_kernel(const ImgDesc *__restrict__ descs, const uint32_t *__restrict__ tile_prefix,
-                      const uint32_t *__restrict__ d_n, uint32_t *queue, const RingCfg rc,
+                      const uint32_t *__restrict__ d_grp, uint32_t *queue, const RingCfg rc,
                       uint32_t lmax, uint32_t *err, uint64_t timeout_ns) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_job[2];
   const SmemMap sm = carve_smem(smem, rc, (lmax + 1u) * NT);
   init_cta(sm, rc);
-  const uint32_t n = __ldg(d_n);
+  const uint32_t n = __ldg(d_grp);
   if (n == 0) return;
+  descs += __ldg(d_grp + kBatchGroups);
+  tile_prefix += __ldg(d_grp + 2 * kBatchGroups);
   const uint32_t total = __ldg(tile_prefix + n);
   uint32_t ctr = 0;
   // the batch's control block keeps a timeout diagnostic record 8 words
@@ -171,8 +177,10 @@ cudaError_t launch_pack_single(const ImgDesc &d, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_pack_batch(const ImgDesc *d_descs, const uint32_t *d_row_prefix,
-                              const uint32_t *d_n, uint32_t *d_queue, int grid, cudaStream_t s) {
-  pack_batch_kernel<<<grid, 256, 0, s>>>(d_descs, d_row_prefix, d_n, d_queue);
+                              const uint32_t *d_n, uint32_t *d_queues, uint32_t nqueues, int grid,
+                              cudaStream_t s) {
+  if (nqueues > 256u) return cudaErrorInvalidValue;
+  pack_batch_kernel<<<grid, 256, 0, s>>>(d_descs, d_row_prefix, d_n, d_queues, nqueues);
   return cudaGetLastError();
 }
 
@@ -258,40 +266,40 @@ cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
 
 template <int NT>
 static void persistent_n(int k, const ImgDesc *d_descs, const uint32_t *d_tile_prefix,
-                         const uint32_t *d_n, uint32_t *d_queue, const RingCfg &rc,
+                         const uint32_t *d_grp, uint32_t *d_queue, const RingCfg &rc,
                          uint32_t lmax, int grid, size_t smem, uint32_t *err,
                          uint64_t timeout_ns, cudaStream_t s) {
   if (k == 4)
-    persistent_kernel<NT, 4><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
+    persistent_kernel<NT, 4><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_grp, d_queue, rc,
                                                     lmax, err, timeout_ns);
   else if (k == 2)
-    persistent_kernel<NT, 2><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
+    persistent_kernel<NT, 2><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_grp, d_queue, rc,
                                                     lmax, err, timeout_ns);
   else
-    persistent_kernel<NT, 1><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_n, d_queue, rc,
+    persistent_kernel<NT, 1><<<grid, NT, smem, s>>>(d_descs, d_tile_prefix, d_grp, d_queue, rc,
                                                     lmax, err, timeout_ns);
 }
 
 cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
-                              const uint32_t *d_tile_prefix, const uint32_t *d_n,
+                              const uint32_t *d_tile_prefix, const uint32_t *d_grp,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
   if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
   switch (nt) {
     case 32:
-      persistent_n<32>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<32>(kcols, d_descs, d_tile_prefix, d_grp, d_queue, rc, lmax, grid, smem, err,
                        timeout_ns, s);
       break;
     case 64:
-      persistent_n<64>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<64>(kcols, d_descs, d_tile_prefix, d_grp, d_queue, rc, lmax, grid, smem, err,
                        timeout_ns, s);
       break;
     case 96:
-      persistent_n<96>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<96>(kcols, d_descs, d_tile_prefix, d_grp, d_queue, rc, lmax, grid, smem, err,
                        timeout_ns, s);
       break;
     case 128:
-      persistent_n<128>(kcols, d_descs, d_tile_prefix, d_n, d_queue, rc, lmax, grid, smem, err,
+      persistent_n<128>(kcols, d_descs, d_tile_prefix, d_grp, d_queue, rc, lmax, grid, smem, err,
                         timeout_ns, s);
       break;
     default: return cudaErrorInvalidValue;

@@ -6,6 +6,7 @@ is no CPU path: without the built library every call raises OilPaintError.
 """
 from __future__ import annotations
 
+import ctypes
 import json
 import os
 from typing import Iterable, Sequence
@@ -21,8 +22,9 @@ _tuned_loaded = False
 
 def load_tuning(path: str = TUNING_TABLE) -> int:
     """Load the autotuner's saved (radius, levels) -> launch-configuration
-    table into the library (once per process unless `path` is given
-    explicitly); returns the number of entries."""
+    table, and its batch-group table keyed by a group's largest radius and
+    level count, into the library (once per process unless `path` is given
+    explicitly); returns the number of single-image entries."""
     global _tuned_loaded
     if not os.path.exists(path):
         return 0
@@ -32,6 +34,10 @@ def load_tuning(path: str = TUNING_TABLE) -> int:
     for key, ent in entries.items():
         r, L = (int(v) for v in key.split(","))
         B.check(B.op_tune_table_set(r, L, B.op_config_t.make(**ent["config"])), "tune table")
+    for key, ent in table.get("batch_entries", {}).items():
+        r, L = (int(v) for v in key.split(","))
+        B.check(B.op_batch_tune_table_set(r, L, B.op_config_t.make(**ent["config"])),
+                "batch tune table")
     _tuned_loaded = True
     return len(entries)
 
@@ -224,6 +230,16 @@ class Batch:
         c = B.op_config_t()
         B.check(B.op_batch_get_config(self._h, c), "op_batch_get_config")
         return c.as_dict()
+
+    def groups(self) -> list[dict]:
+        """Each image group's largest radius and level count and its launch
+        configuration."""
+        out = []
+        for g in range(B.op_batch_group_count(self._h)):
+            c, r, L = B.op_config_t(), ctypes.c_int32(), ctypes.c_uint32()
+            B.check(B.op_batch_get_group(self._h, g, c, r, L), "op_batch_get_group")
+            out.append({"max_radius": r.value, "max_levels": L.value, "config": c.as_dict()})
+        return out
 
     def diagnostics(self) -> list[int]:
         """The timeout diagnostic record of the batch's control block (16

@@ -82,6 +82,19 @@ def test_tune_table_validation(lib):
     assert B.op_tune_table_set(3, 20, B.op_config_t.make(64, 32, 4, 2)) == B.OP_OK
 
 
+def test_batch_tune_table_validation(lib):
+    set_ = B.op_batch_tune_table_set
+    assert set_(15, 20, B.op_config_t.make(48)) == B.OP_E_INVALID
+    assert set_(-1, 20, B.op_config_t.make(64)) == B.OP_E_INVALID
+    assert set_(45, 20, B.op_config_t.make(64)) == B.OP_E_INVALID
+    assert set_(15, 0, B.op_config_t.make(64)) == B.OP_E_INVALID
+    assert set_(15, 257, B.op_config_t.make(64)) == B.OP_E_INVALID
+    # the persistent kernel keeps one histogram set per thread: no column path
+    assert set_(15, 20, B.op_config_t.make(64, path=1)) == B.OP_E_INVALID
+    assert set_(15, 20, B.op_config_t.make(128, 0, 2, 1, 2)) == B.OP_OK
+    assert set_(15, 20, None) == B.OP_OK  # removes the entry
+
+
 def test_selftest_rejects_bad_timeout(lib):
     assert B.op_selftest_wait_timeout(0, None) == B.OP_E_INVALID
     assert B.op_selftest_wait_timeout(3_000_000_000, None) == B.OP_E_INVALID

@@ -8,7 +8,7 @@ import __graft_entry__
 import oracle
 from paper_1405_1020_gb300 import binding as B
 from paper_1405_1020_gb300 import synth
-from paper_1405_1020_gb300.filter import Batch, OilPaint
+from paper_1405_1020_gb300.filter import TUNING_TABLE, Batch, OilPaint, load_tuning
 from tests.pins import OUT_FILL
 
 pytestmark = pytest.mark.gpu
@@ -223,3 +223,83 @@ def test_batch_with_one_radius_group_empty(radii):
     assert b.sync_status(stream) == B.OP_OK
     check_all(images, f"radii {radii}")
     b.close()
+
+
+def test_four_groups_and_each_group_empty_in_turn():
+    """A batch created for radii up to 20 and 32 levels splits its images by
+    radius (above 15 or not) and level count (above 20 or not) into four
+    groups, each with its own launch configuration; one captured graph
+    serves sets in which any one group is empty."""
+    images = make_images(16, seed=23, max_r=20, levels=(3, 16, 20, 32))
+    for k, im in enumerate(images):  # every group populated
+        im["r"] = (2, 15, 16, 20)[k % 4] if k < 8 else im["r"]
+        im["L"] = (16, 32)[(k // 4) % 2] if k < 8 else im["L"]
+    descs = to_device(images)
+    pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
+    b = Batch(16, pix + 4096, 20, 32)
+    groups = b.groups()
+    assert [(g["max_radius"], g["max_levels"]) for g in groups] == [
+        (15, 20), (15, 32), (20, 20), (20, 32)]
+    assert all(g["config"]["path"] == 0 for g in groups)
+    stream = torch.cuda.Stream()
+    b.set(descs, stream)
+    b.capture(stream)
+    b.launch_graph(stream)
+    assert b.sync_status(stream) == B.OP_OK
+    check_all(images, "four groups")
+
+    def group(im):
+        return 2 * (im["r"] > 15) + (im["L"] > 20)
+
+    for g in range(4):
+        keep = [k for k, im in enumerate(images) if group(im) != g]
+        sub = [images[k] for k in keep]
+        reset(sub)
+        b.set([descs[k] for k in keep], stream)
+        b.launch_graph(stream)
+        assert b.sync_status(stream) == B.OP_OK
+        check_all(sub, f"group {g} empty")
+    b.close()
+
+
+def test_one_config_for_every_group():
+    """A configuration given at creation applies to every group."""
+    cfg = {"tile_w": 128, "chunk_rows": 2, "prefetch": 1, "cols_per_thread": 4}
+    b = Batch(4, 100000, 44, 64, config=cfg)
+    groups = b.groups()
+    assert len(groups) == 4
+    for g in groups:
+        c = g["config"]
+        assert (c["tile_w"], c["chunk_rows"], c["prefetch"], c["cols_per_thread"]) == (128, 2, 1, 4)
+    assert [(g["max_radius"], g["max_levels"]) for g in groups] == [
+        (15, 20), (15, 64), (44, 20), (44, 64)]
+    b.close()
+    b1 = Batch(4, 100000, 15, 20, config=cfg)
+    assert len(b1.groups()) == 1
+    b1.close()
+
+
+def test_batch_tune_table_entry_is_used_where_it_fits():
+    """op_batch_create (cfg NULL) takes a group's configuration from the
+    batch tuning table when the entry fits the group's largest image in one
+    CTA, and falls back to another configuration when it does not."""
+    want = {"tile_w": 64, "chunk_rows": 4, "prefetch": 1, "cols_per_thread": 1}
+    # 4 columns of 128 threads at r = 44: the halo box is wider than 256 columns
+    wide = {"tile_w": 512, "chunk_rows": 2, "prefetch": 1, "cols_per_thread": 4}
+    try:
+        B.check(B.op_batch_tune_table_set(15, 20, B.op_config_t.make(**want)), "set")
+        b = Batch(4, 100000, 20, 20)
+        g = b.groups()
+        assert [(x["max_radius"], x["max_levels"]) for x in g] == [(15, 20), (20, 20)]
+        got = g[0]["config"]
+        assert {k: got[k] for k in want} == want
+        b.close()
+        B.check(B.op_batch_tune_table_set(44, 32, B.op_config_t.make(**wide)), "set")
+        b = Batch(4, 100000, 44, 32)
+        got = b.groups()[3]["config"]
+        assert (got["tile_w"], got["cols_per_thread"]) != (512, 4)
+        b.close()
+    finally:
+        B.op_batch_tune_table_set(15, 20, None)
+        B.op_batch_tune_table_set(44, 32, None)
+        load_tuning(TUNING_TABLE)
