@@ -541,7 +541,7 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   if (win.rows() == 0u) return OP_OK;  // literal mode: no pixel is r from every edge
   const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, g.boxw);
   const size_t smem = smem_of(g, c, op->r, op->L);
-  const int pack_grid = static_cast<int>(std::min<uint32_t>(op->h, 8u * op->di.sms));
+  const int pack_grid = opk::pack_grid_for(op->h, op->di.sms);
   cudaError_t e = opk::launch_pack_single(d, pack_grid, s);
   if (e != cudaSuccess) return OP_E_CUDA;
   if (op->prof_ev && cudaEventRecord(op->prof_ev, s) != cudaSuccess) return OP_E_CUDA;

@@ -110,6 +110,17 @@ inline size_t cols_hist_bytes(const Geometry &g, int r, uint32_t L) {
   return ((sums + 127u) & ~static_cast<size_t>(127u)) + sums / 2u;
 }
 
+// Blocks of the single-image pack launch (256 threads, one image row at a
+// time, rows b, b + grid, ...): as many as 8 per SM can be resident, and the
+// grid is trimmed so that every block packs the same number of rows -- with
+// 8 * sms blocks a 3000-row image left 1216 - 568 blocks idle through the
+// last third of the launch.
+inline int pack_grid_for(uint32_t rows, int sms) {
+  const uint32_t slots = 8u * static_cast<uint32_t>(sms > 0 ? sms : 1);
+  const uint32_t per_block = (rows + slots - 1u) / slots;
+  return static_cast<int>(per_block ? (rows + per_block - 1u) / per_block : 1u);
+}
+
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
 // per thread, bins of the variant's size; 2 or 4: kcols histograms, one
 // more where the window histogram is split, of L levels per thread, bins of

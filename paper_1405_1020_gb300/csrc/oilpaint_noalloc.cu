@@ -181,7 +181,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(sc.err, 0, sizeof(uint32_t), s) != cudaSuccess) return OP_E_CUDA;
-  const int pack_grid = static_cast<int>(std::min<uint32_t>(height, 8u * static_cast<uint32_t>(sms)));
+  const int pack_grid = opk::pack_grid_for(height, sms);
   if (opk::launch_pack_single(d, pack_grid, s) != cudaSuccess) return OP_E_CUDA;
   const dim3 grid(d.tiles_x, (win.rows() + d.tile_h - 1) / d.tile_h);
   if (opk::launch_tile(g.nt, g.kcols, g.variant, d, map, rc, grid, smem, sc.err, kWaitTimeoutNs,

@@ -218,6 +218,7 @@ class OilPaintServer:
         th = threading.Thread(target=client, daemon=True)
         th.start()
         client_done = False
+        pending: list = []  # an arrival taken from the inbox while idle
         in_flight: dict[int, _Round] = {}
         rounds = 0
         round_sizes = []
@@ -225,7 +226,7 @@ class OilPaintServer:
             busy = False
             while True:
                 try:
-                    t = inbox.get_nowait()
+                    t = pending.pop() if pending else inbox.get_nowait()
                 except queue.Empty:
                     break
                 if t is None:
@@ -266,7 +267,14 @@ class OilPaintServer:
                             t.out = None  # output delivered; memory returns to the pool
                     del in_flight[slot]
                     busy = True
-            if not busy:
+            if not busy and not client_done:
+                # idle: block on the inbox (woken at once by an arrival) for at
+                # most idle_sleep_s, then poll the rounds in flight again
+                try:
+                    pending.append(inbox.get(timeout=idle_sleep_s))
+                except queue.Empty:
+                    pass
+            elif not busy:
                 time.sleep(idle_sleep_s)
         t_end = time.perf_counter()
         th.join()
