@@ -1048,7 +1048,9 @@ int op_batch_run(op_batch_t *b, void *stream) {
   const uint32_t *rp = reinterpret_cast<const uint32_t *>(b->ws + b->off_row_prefix);
   // Fixed grids; the image counts and the tables are read from device
   // memory, so the launches do not depend on the current batch and a
-  // captured graph stays valid across op_batch_set calls.
+  // captured graph stays valid across op_batch_set calls.  (Packing each
+  // group on its own stream, overlapping the other groups' filters, measured
+  // no faster on the 64-image batch and less steady.)
   if (opk::launch_pack_batch(descs, rp, hdr + kHdrTotal, ctrl + kCtrlQueue, opk::kBatchGroups,
                              b->grid_pack, s) != cudaSuccess)
     return OP_E_CUDA;
