@@ -519,7 +519,8 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
     // that starts m = a & 3 bytes into a word is read as aligned words and
     // shifted by 8m bits (a fourth word is then needed; it lies in the same
     // aligned word as the group's last byte, so it never leaves the row's
-    // memory page).  Four groups per thread are in flight.
+    // memory page).  (Two or four groups in flight per thread held more
+    // registers than the kernel's occupancy can afford.)
     const uint32_t m = static_cast<uint32_t>(a & 3u);
     const uint32_t *s4 = reinterpret_cast<const uint32_t *>(src - m);
     uint4 *d16 = reinterpret_cast<uint4 *>(dst);
@@ -527,34 +528,20 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
     auto run = [&](auto shifted) {
       constexpr bool SH = decltype(shifted)::value;
       const uint32_t sh = 8u * m;
-      for (uint32_t q0 = tid; q0 < nq; q0 += 4u * nthr) {
-        uint32_t v[4][4];
-#pragma unroll
-        for (uint32_t k = 0; k < 4u; ++k) {
-          const uint32_t q = q0 + k * nthr;
-          if (q < nq) {
-            const uint32_t *g4 = s4 + 3u * q;
-            v[k][0] = __ldg(g4);
-            v[k][1] = __ldg(g4 + 1u);
-            v[k][2] = __ldg(g4 + 2u);
-            v[k][3] = SH ? __ldg(g4 + 3u) : 0u;
-          }
+      for (uint32_t q = tid; q < nq; q += nthr) {
+        const uint32_t *g4 = s4 + 3u * q;
+        const uint32_t w0 = __ldg(g4), w1 = __ldg(g4 + 1u), w2 = __ldg(g4 + 2u);
+        uint32_t p0 = w0, p1 = w1, p2 = w2;
+        if (SH) {
+          const uint32_t w3 = __ldg(g4 + 3u);
+          p0 = __funnelshift_r(w0, w1, sh);
+          p1 = __funnelshift_r(w1, w2, sh);
+          p2 = __funnelshift_r(w2, w3, sh);
         }
-#pragma unroll
-        for (uint32_t k = 0; k < 4u; ++k) {
-          const uint32_t q = q0 + k * nthr;
-          if (q >= nq) break;
-          uint32_t p0 = v[k][0], p1 = v[k][1], p2 = v[k][2];
-          if (SH) {
-            p0 = __funnelshift_r(v[k][0], v[k][1], sh);
-            p1 = __funnelshift_r(v[k][1], v[k][2], sh);
-            p2 = __funnelshift_r(v[k][2], v[k][3], sh);
-          }
-          d16[q] = make_uint4(word(p0 & 0xFFu, (p0 >> 8) & 0xFFu, (p0 >> 16) & 0xFFu),
-                              word(p0 >> 24, p1 & 0xFFu, (p1 >> 8) & 0xFFu),
-                              word((p1 >> 16) & 0xFFu, p1 >> 24, p2 & 0xFFu),
-                              word((p2 >> 8) & 0xFFu, (p2 >> 16) & 0xFFu, p2 >> 24));
-        }
+        d16[q] = make_uint4(word(p0 & 0xFFu, (p0 >> 8) & 0xFFu, (p0 >> 16) & 0xFFu),
+                            word(p0 >> 24, p1 & 0xFFu, (p1 >> 8) & 0xFFu),
+                            word((p1 >> 16) & 0xFFu, p1 >> 24, p2 & 0xFFu),
+                            word((p2 >> 8) & 0xFFu, (p2 >> 16) & 0xFFu, p2 >> 24));
       }
     };
     if (m)
