@@ -60,7 +60,8 @@ def main() -> int:
             assert np.array_equal(dst.cpu().numpy(), want(buf, 233, 150, stride, bpp, r, L, mode)), \
                 (r, L, mode, bpp, cfg)
             n += 1
-    # batch: both radius groups, literal and default images
+    # batch: all four groups (r above 15 or not x L above 20 or not), literal
+    # and default images
     images = []
     for k in range(8):
         w, h = 100 + 37 * k, 60 + 11 * k

@@ -206,8 +206,8 @@ def test_batch_rejects_invalid_sets():
 
 @pytest.mark.parametrize("radii", [(16, 20, 44), (0, 2, 15)], ids=["large-only", "small-only"])
 def test_batch_with_one_radius_group_empty(radii):
-    """A batch created for radii up to 44 runs r <= 15 and r > 15 as two
-    groups; either group may be empty in a given set."""
+    """A batch created for radii up to 44 (and 32 levels) runs r <= 15 and
+    r > 15 in separate groups; either radius side may be empty in a set."""
     images = make_images(9, seed=11 + radii[0], max_r=44, levels=(16, 20, 32))
     rng = np.random.default_rng(radii[1])
     for im in images:
