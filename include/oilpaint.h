@@ -49,7 +49,7 @@ extern "C" {
 #define OP_E_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
 #define OP_E_NOMEM (-3)       /* host or device allocation failed */
 #define OP_E_TIMEOUT (-4)     /* a bounded device-side wait gave up */
-#define OP_E_UNSUPPORTED (-5) /* valid request this build cannot run (e.g. shared memory) */
+#define OP_E_UNSUPPORTED (-5) /* valid request the library cannot run here (e.g. shared memory) */
 #define OP_E_BOUNDS (-6)      /* the bounds-checking build (liboilpaint_checked.so) found
                                  a shared-memory, pixel or TMA access out of range and
                                  skipped it; reported by the sync calls */
