@@ -1419,15 +1419,19 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
 #pragma unroll
         for (int i = 0; i < K; ++i) best[i] = 0u;
         for (uint32_t lv = 0; lv < L; ++lv) {
-          const uint32_t tag = 31u - lv;
           uint32_t acc = count_word(0, lv);
 #pragma unroll
           for (int b = 1; b < NB; ++b) acc += count_word(b, lv);
-          best[0] = max(best[0], (acc << CSH) | tag);
+          // key of window i = (count_i << CSH) | (31 - lv); the key of window
+          // i follows from that of window i-1 by adding D_i's count word
+          // shifted into place (the shift drops VAR A's sums above the count,
+          // and the tag bits below CSH are untouched)
+          uint32_t key = (acc << CSH) | (31u - lv);
+          best[0] = max(best[0], key);
 #pragma unroll
           for (int i = 1; i < K; ++i) {
-            acc += count_word(NB - 1 + i, lv);
-            best[i] = max(best[i], (acc << CSH) | tag);
+            key += count_word(NB - 1 + i, lv) << CSH;
+            best[i] = max(best[i], key);
           }
         }
         // the reciprocals are fetched first, so that their latency overlaps
