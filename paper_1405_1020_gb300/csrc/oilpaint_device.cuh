@@ -682,11 +682,12 @@ __device__ __forceinline__ void dh_delta(uint32_t w, uint32_t &lo, uint32_t &hi)
   hi = (w >> 6) & 0x003FC00Fu;
 }
 
-// Address of w's bin in a histogram whose level 0 is at `base` (levels NT*8
-// bytes apart): the level field sits at bits 1..5, so (w & 0x3E) * NT * 4.
-template <int NT>
+// Address of w's bin in a histogram whose level 0 is at `base` and whose
+// levels are LS bytes apart: the level field sits at bits 1..5, so
+// (w & 0x3E) * LS / 2.
+template <uint32_t LS>
 __device__ __forceinline__ uint32_t dh_addr(uint32_t base, uint32_t w) {
-  return base + (w & 0x3Eu) * (NT * 4u);
+  return base + (w & 0x3Eu) * (LS / 2u);
 }
 
 __device__ __forceinline__ void neg64(uint32_t &lo, uint32_t &hi) {
@@ -696,25 +697,25 @@ __device__ __forceinline__ void neg64(uint32_t &lo, uint32_t &hi) {
 }
 
 // Variant A operations on histograms given by the address of the thread's
-// level-0 bin.
-template <int NT>
+// level-0 bin, levels LS bytes apart.
+template <uint32_t LS>
 struct DeltaOpsA {
   __device__ __forceinline__ void add(uint32_t base, uint32_t w) const {
     uint32_t lo, hi;
     dh_delta(w, lo, hi);
-    bin_add64(dh_addr<NT>(base, w), lo, hi);
+    bin_add64(dh_addr<LS>(base, w), lo, hi);
   }
   __device__ __forceinline__ void sub(uint32_t base, uint32_t w) const {
     uint32_t lo, hi;
     dh_delta(w, lo, hi);
-    bin_sub64(dh_addr<NT>(base, w), lo, hi);
+    bin_sub64(dh_addr<LS>(base, w), lo, hi);
   }
   // +w0 +w1 in one histogram as one two-deep update (their bins may coincide).
   __device__ __forceinline__ void add2(uint32_t base, uint32_t w0, uint32_t w1) const {
     uint32_t alo, ahi, blo, bhi;
     dh_delta(w0, alo, ahi);
     dh_delta(w1, blo, bhi);
-    bin_add64x2_chain(dh_addr<NT>(base, w0), alo, ahi, dh_addr<NT>(base, w1), blo, bhi);
+    bin_add64x2_chain(dh_addr<LS>(base, w0), alo, ahi, dh_addr<LS>(base, w1), blo, bhi);
   }
   // +w0 +w1 in histogram p and +w2 +w3 in histogram q != p, four deep.
   __device__ __forceinline__ void add2x2(uint32_t p, uint32_t w0, uint32_t w1, uint32_t q,
@@ -724,8 +725,8 @@ struct DeltaOpsA {
     dh_delta(w1, blo, bhi);
     dh_delta(w2, clo, chi);
     dh_delta(w3, dlo, dhi);
-    bin_add64x4_chain(dh_addr<NT>(p, w0), alo, ahi, dh_addr<NT>(p, w1), blo, bhi,
-                      dh_addr<NT>(q, w2), clo, chi, dh_addr<NT>(q, w3), dlo, dhi);
+    bin_add64x4_chain(dh_addr<LS>(p, w0), alo, ahi, dh_addr<LS>(p, w1), blo, bhi,
+                      dh_addr<LS>(q, w2), clo, chi, dh_addr<LS>(q, w3), dlo, dhi);
   }
   // +win -wout in one histogram as one two-deep update (the bins of the two
   // words may coincide).
@@ -733,7 +734,7 @@ struct DeltaOpsA {
     uint32_t alo, ahi, blo, bhi;
     dh_delta(win, alo, ahi);
     dh_delta(wout, blo, bhi);
-    bin_addsub64_chain(dh_addr<NT>(base, win), alo, ahi, dh_addr<NT>(base, wout), blo, bhi);
+    bin_addsub64_chain(dh_addr<LS>(base, win), alo, ahi, dh_addr<LS>(base, wout), blo, bhi);
   }
   // +win_p -wout_p in histogram p and +win_q -wout_q in histogram q != p as
   // one four-deep update.
@@ -744,8 +745,8 @@ struct DeltaOpsA {
     dh_delta(wout_p, blo, bhi);
     dh_delta(win_q, clo, chi);
     dh_delta(wout_q, dlo, dhi);
-    bin_addsub64x2_chain(dh_addr<NT>(p, win_p), alo, ahi, dh_addr<NT>(p, wout_p), blo, bhi,
-                         dh_addr<NT>(q, win_q), clo, chi, dh_addr<NT>(q, wout_q), dlo, dhi);
+    bin_addsub64x2_chain(dh_addr<LS>(p, win_p), alo, ahi, dh_addr<LS>(p, wout_p), blo, bhi,
+                         dh_addr<LS>(q, win_q), clo, chi, dh_addr<LS>(q, wout_q), dlo, dhi);
   }
   // (+/-)wp at histogram p and (+/-)wq at histogram q != p.
   template <bool NEG_P, bool NEG_Q>
@@ -755,7 +756,7 @@ struct DeltaOpsA {
     dh_delta(wq, qlo, qhi);
     if (NEG_P) neg64(plo, phi);
     if (NEG_Q) neg64(qlo, qhi);
-    bin_add64x2(dh_addr<NT>(p, wp), plo, phi, dh_addr<NT>(q, wq), qlo, qhi);
+    bin_add64x2(dh_addr<LS>(p, wp), plo, phi, dh_addr<LS>(q, wq), qlo, qhi);
   }
 };
 
@@ -809,13 +810,13 @@ __device__ __forceinline__ void dhb_delta(uint32_t w, uint32_t &lo, uint32_t &hi
   c = w >> 29;
 }
 
-template <int NT>
+template <uint32_t LS>
 struct DeltaOpsB {
   uint32_t cd;  // count address = (sums address >> 1) + cd
 
-  // level field (bits 8..12) times NT * 8 bytes
+  // level field (bits 8..12) times the level stride LS
   __device__ __forceinline__ uint32_t saddr(uint32_t base, uint32_t w) const {
-    return base + (((w & 0x1F00u) * NT) >> 5);
+    return base + (((w & 0x1F00u) * LS) >> 8);
   }
   __device__ __forceinline__ uint32_t caddr(uint32_t s) const { return (s >> 1) + cd; }
 
@@ -1342,7 +1343,8 @@ __host__ __device__ constexpr int hsplit(int k, int var) {
 //        xa+i-1-r, so that the window histogram of column xa+i is
 //        H + D_1 + ... + D_i.
 // A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  Histograms are
-// L levels of NT bins (level-major, thread-minor); VAR B keeps its counts in
+// L levels of NT bins, interleaved level-major (a level's NH rows of NT bins
+// are adjacent, thread-minor); VAR B keeps its counts in
 // a second array of the same shape.  The argmax runs over running sums of counts (VAR A: the
 // histograms' low words, whose bottom 10 bits are the counts) with keys
 // (count, 31 - level), so the lowest level wins ties under max.  Pixels
@@ -1365,13 +1367,17 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
   const int jl = K * t;
   const int E0 = y0 - r;
   const int nsteps = (y1 - y0) + 2 * r;
-  const uint32_t lstride = NT * 8u;      // between levels of one histogram
-  const uint32_t hstride = L * lstride;  // between histograms
+  // Level-major layout: level lv of histogram i, thread t at
+  // sums + lv * NH*NT*8 + i * NT*8 + t * 8, so the NH bins a thread reads for
+  // one level of the argmax lie at fixed offsets from one address.
+  constexpr uint32_t LS = NH * NT * 8u;
+  const uint32_t lstride = LS;       // between levels of one histogram
+  const uint32_t hstride = NT * 8u;  // between histograms
   const uint32_t h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
   // VAR B counts: same shape at half the stride, after the sums
-  const uint32_t cbase = sm.sums + NH * L * lstride;
+  const uint32_t cbase = sm.sums + L * LS;
   const uint32_t cd = cbase - (sm.sums >> 1);
-  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<NT>, DeltaOpsB<NT>>::type;
+  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<LS>, DeltaOpsB<LS>>::type;
   Ops ops;
   if constexpr (VAR == kVarB) ops.cd = cd;
   auto hist = [&](int i) { return h0 + static_cast<uint32_t>(i) * hstride; };
@@ -1544,7 +1550,7 @@ __device__ bool run_tile_cols(const ImgDesc &d, const CUtensorMap *tmap, int x0,
   const uint32_t cbase = (sums_end + 127u) & ~127u;
   const uint32_t cd = cbase - (colb >> 1);
   const uint8_t *gbase = sm.ring_ptr - sm.ring;  // generic address of shared address 0
-  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<1>, DeltaOpsB<1>>::type;
+  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<8u>, DeltaOpsB<8u>>::type;
   Ops ops;
   if constexpr (VAR == kVarB) ops.cd = cd;
   // zero the column histograms (all Lp levels)
