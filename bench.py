@@ -282,12 +282,19 @@ def run_ours(args):
     f_ms = statistics.mean(filt_ms)
     ach_tops = ops_per_pixel(RADIUS, LEVELS) * W * H / (f_ms / 1e3) / 1e12
     traffic = None
+    pipe = None
     tpath = os.path.join(ROOT, "profiles", "filter_traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tr = json.load(f)
         if tr.get("workload") == WORKLOAD and tr.get("kernel_source_hash") == _kernel_hash():
             traffic = tr.get("bytes_per_launch")
+            if tr.get("shared_pipe_pct") is not None:
+                # the pipe that bounds the kernel in the same capture
+                pipe = {"pipe": "shared memory (l1tex)",
+                        "frac": round(tr["shared_pipe_pct"] / 100.0, 4),
+                        "issue_active": round(tr.get("issue_active_pct", 0.0) / 100.0, 4),
+                        "source": "ncu, " + tr.get("summary", "")}
     launch = op.config()
     if launch.get("path", 0) == 1:
         kernel = "tile_cols_kernel"
@@ -300,7 +307,8 @@ def run_ours(args):
                 "kernel": kernel, "kernel_ms": round(f_ms, 4),
                 "pack_ms": round(statistics.mean(pack_ms), 4),
                 "ops_per_pixel": ops_per_pixel(RADIUS, LEVELS),
-                "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz"}
+                "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz",
+                "bounding_pipe": pipe}
 
     # end to end through the host-buffer entry points: every step copies its
     # input from pinned host memory and its result back.  op_run_host_async
