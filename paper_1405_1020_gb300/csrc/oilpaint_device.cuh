@@ -1133,19 +1133,31 @@ __device__ bool run_tile(const ImgDesc &d, const CUtensorMap *tmap, int x0, int 
           for (int j = j0; j < j1; ++j) h.sub(pl[j]);
         }
         if (out_now) {
-          uint32_t m = 0, best = 0;
-          for (uint32_t lv = 0; lv < L; ++lv) {
-            const uint32_t kk = h.count_key(lv);
-            if (kk > best) {
-              best = kk;
-              m = lv;
+          // the first level of the largest count (the strict > scan from
+          // level 0).  VAR A: max over keys (count, 255 - level), the count
+          // in place in bits 22..31 of the high word -- one or and one max
+          // per level; VAR B keeps the scan (its counts would need a shift,
+          // and it measured slower as keys).
+          uint32_t m = 0, bcount = 0;
+          if constexpr (VAR == kVarA) {
+            uint32_t best = 0;
+            for (uint32_t lv = 0; lv < L; ++lv) best = max(best, h.count_key(lv) | (255u - lv));
+            m = 255u - (best & 0xFFu);
+            bcount = best >> 22;
+          } else {
+            for (uint32_t lv = 0; lv < L; ++lv) {
+              const uint32_t kk = h.count_key(lv);
+              if (kk > bcount) {
+                bcount = kk;
+                m = lv;
+              }
             }
           }
-          // best == 0: no level below L in the window (literal mode only)
-          if (best != 0u) {
+          // no level below L in the window (literal mode only)
+          if (bcount != 0u) {
             uint32_t lo, hi, cnt, R, G, B;
             h.bin(m, lo, hi);
-            unpack_bin<VAR>(lo, hi, VAR == kVarB ? best : 0u, cnt, R, G, B);
+            unpack_bin<VAR>(lo, hi, VAR == kVarB ? bcount : 0u, cnt, R, G, B);
             const uint32_t mul = VAR == kVarA ? rcp_of(cnt) : 0u;
             store_pixel(d, xa, e - r, div_mean<VAR>(R, cnt, mul), div_mean<VAR>(G, cnt, mul),
                         div_mean<VAR>(B, cnt, mul), alpha);
