@@ -1613,7 +1613,6 @@ __device__ bool run_tile_cols(const ImgDesc &d, const CUtensorMap *tmap, int x0,
 #pragma unroll 8
             for (int k = 0; k < 32; ++k) {
               const uint32_t lo = static_cast<uint32_t>(acc);
-              const uint32_t hi = static_cast<uint32_t>(acc >> 32);
               uint32_t key = 0u;
               if (lv_ok) key = (VAR == kVarA ? (lo << 22) : (cnt << 5)) | tag;
               const uint32_t kmax = __reduce_max_sync(FULL, key);
