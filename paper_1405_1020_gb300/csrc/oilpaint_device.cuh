@@ -234,6 +234,19 @@ __device__ __forceinline__ void sts_zero32(uint32_t addr) {
   asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(0u));
 }
 
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
+  if (!OPK_SMEM_OK(addr, 2u)) return 0u;
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ void sts_u16(uint32_t addr, uint32_t v) {
+  if (!OPK_SMEM_OK(addr, 2u)) return;
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(static_cast<uint16_t>(v)));
+}
+
+
 // 64-bit read-modify-write of one histogram bin.  All histogram accesses are
 // volatile asm, so they keep their program order among themselves; the ring
 // reads are ordinary loads and may be scheduled around them.
@@ -801,6 +814,82 @@ __device__ __forceinline__ void binb_add(uint32_t As, uint32_t Ac, uint32_t lo, 
       "r"(Ac), "r"(lo), "r"(hi), "r"(c));
 }
 
+// Variant B bins with 16-bit counts (the K-column path: a window's count is
+// at most 89^2 = 7921, and the difference histograms' counts are kept mod
+// 2^16, which the window sums undo): binb_add, binb_add_x2 and
+// binb_addsub_chain with 2-byte count accesses (a 16-bit load zero-extends
+// into the 32-bit register; a 16-bit store keeps its low half).
+__device__ __forceinline__ void binb16_add(uint32_t As, uint32_t Ac, uint32_t lo, uint32_t hi,
+                                           uint32_t c) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 2u)) return;
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, a2;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u16 a2, [%1];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u16 [%1], a2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(lo), "r"(hi), "r"(c));
+}
+
+__device__ __forceinline__ void binb16_add_x2(uint32_t As, uint32_t Ac, uint32_t alo,
+                                              uint32_t ahi, uint32_t ac, uint32_t Bs,
+                                              uint32_t Bc, uint32_t blo, uint32_t bhi,
+                                              uint32_t bc) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 2u) || !OPK_SMEM_OK(Bs, 8u) ||
+      !OPK_SMEM_OK(Bc, 2u))
+    return;
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u16 a2, [%1];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
+      "ld.shared.u16 b2, [%6];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "add.cc.u32 b0, b0, %7;\n\t"
+      "addc.u32 b1, b1, %8;\n\t"
+      "add.u32 b2, b2, %9;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u16 [%1], a2;\n\t"
+      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
+      "st.shared.u16 [%6], b2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+}
+
+__device__ __forceinline__ void binb16_addsub_chain(uint32_t As, uint32_t Ac, uint32_t alo,
+                                                    uint32_t ahi, uint32_t ac, uint32_t Bs,
+                                                    uint32_t Bc, uint32_t blo, uint32_t bhi,
+                                                    uint32_t bc) {
+  if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 2u) || !OPK_SMEM_OK(Bs, 8u) ||
+      !OPK_SMEM_OK(Bc, 2u))
+    return;
+  asm volatile(
+      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t.reg .pred p;\n\t"
+      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
+      "ld.shared.u16 a2, [%1];\n\t"
+      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
+      "ld.shared.u16 b2, [%6];\n\t"
+      "add.cc.u32 a0, a0, %2;\n\t"
+      "addc.u32 a1, a1, %3;\n\t"
+      "add.u32 a2, a2, %4;\n\t"
+      "setp.eq.u32 p, %0, %5;\n\t"
+      "selp.b32 b0, a0, b0, p;\n\t"
+      "selp.b32 b1, a1, b1, p;\n\t"
+      "selp.b32 b2, a2, b2, p;\n\t"
+      "sub.cc.u32 b0, b0, %7;\n\t"
+      "subc.u32 b1, b1, %8;\n\t"
+      "sub.u32 b2, b2, %9;\n\t"
+      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
+      "st.shared.u16 [%1], a2;\n\t"
+      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
+      "st.shared.u16 [%6], b2;\n\t}" ::"r"(As),
+      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+}
+
 // Word format 2 (L <= 32): R @0..7 | level @8..12 | B @13..20 | G @21..28 |
 // valid @29.  Sums delta: low word one mask (R, G), high word one shift and
 // mask (B << 10); count delta: the valid bit.
@@ -810,28 +899,37 @@ __device__ __forceinline__ void dhb_delta(uint32_t w, uint32_t &lo, uint32_t &hi
   c = w >> 29;
 }
 
-template <uint32_t LS>
+// Variant B operations; counts of CW bytes (4, or 2 on the K-column path)
+// laid out like the sums at CW/8 of their stride.
+template <uint32_t LS, uint32_t CW = 4u>
 struct DeltaOpsB {
-  uint32_t cd;  // count address = (sums address >> 1) + cd
+  static_assert(CW == 2u || CW == 4u, "count width");
+  uint32_t cd;  // count address = (sums address * CW / 8) + cd
 
   // level field (bits 8..12) times the level stride LS
   __device__ __forceinline__ uint32_t saddr(uint32_t base, uint32_t w) const {
     return base + (((w & 0x1F00u) * LS) >> 8);
   }
-  __device__ __forceinline__ uint32_t caddr(uint32_t s) const { return (s >> 1) + cd; }
+  __device__ __forceinline__ uint32_t caddr(uint32_t s) const {
+    return (s >> (CW == 2u ? 2 : 1)) + cd;
+  }
+  __device__ __forceinline__ void bin_add(uint32_t s, uint32_t lo, uint32_t hi, uint32_t c) const {
+    if constexpr (CW == 2u)
+      binb16_add(s, caddr(s), lo, hi, c);
+    else
+      binb_add(s, caddr(s), lo, hi, c);
+  }
 
   __device__ __forceinline__ void add(uint32_t base, uint32_t w) const {
     uint32_t lo, hi, c;
     dhb_delta(w, lo, hi, c);
-    const uint32_t s = saddr(base, w);
-    binb_add(s, caddr(s), lo, hi, c);
+    bin_add(saddr(base, w), lo, hi, c);
   }
   __device__ __forceinline__ void sub(uint32_t base, uint32_t w) const {
     uint32_t lo, hi, c;
     dhb_delta(w, lo, hi, c);
     neg64(lo, hi);
-    const uint32_t s = saddr(base, w);
-    binb_add(s, caddr(s), lo, hi, 0u - c);
+    bin_add(saddr(base, w), lo, hi, 0u - c);
   }
   __device__ __forceinline__ void add2(uint32_t base, uint32_t w0, uint32_t w1) const {
     add(base, w0);
@@ -847,7 +945,10 @@ struct DeltaOpsB {
     dhb_delta(win, alo, ahi, ac);
     dhb_delta(wout, blo, bhi, bc);
     const uint32_t as = saddr(base, win), bs = saddr(base, wout);
-    binb_addsub_chain(as, caddr(as), alo, ahi, ac, bs, caddr(bs), blo, bhi, bc);
+    if constexpr (CW == 2u)
+      binb16_addsub_chain(as, caddr(as), alo, ahi, ac, bs, caddr(bs), blo, bhi, bc);
+    else
+      binb_addsub_chain(as, caddr(as), alo, ahi, ac, bs, caddr(bs), blo, bhi, bc);
   }
   // Two histograms: issued as two two-deep updates (a four-deep one would
   // need 20 operands and more registers than it saves latency here).
@@ -870,7 +971,10 @@ struct DeltaOpsB {
       qc = 0u - qc;
     }
     const uint32_t ps = saddr(p, wp), qs = saddr(q, wq);
-    binb_add_x2(ps, caddr(ps), plo, phi, pc, qs, caddr(qs), qlo, qhi, qc);
+    if constexpr (CW == 2u)
+      binb16_add_x2(ps, caddr(ps), plo, phi, pc, qs, caddr(qs), qlo, qhi, qc);
+    else
+      binb_add_x2(ps, caddr(ps), plo, phi, pc, qs, caddr(qs), qlo, qhi, qc);
   }
 };
 
@@ -1356,8 +1460,8 @@ __host__ __device__ constexpr int hsplit(int k, int var) {
 //        H + D_1 + ... + D_i.
 // A step costs 2(2r+1) + 4(K-1) bin updates for K outputs.  Histograms are
 // L levels of NT bins, interleaved level-major (a level's NH rows of NT bins
-// are adjacent, thread-minor); VAR B keeps its counts in
-// a second array of the same shape.  The argmax runs over running sums of counts (VAR A: the
+// are adjacent, thread-minor); VAR B keeps its 16-bit counts in a second
+// array of the same shape.  The argmax runs over running sums of counts (VAR A: the
 // histograms' low words, whose bottom 10 bits are the counts) with keys
 // (count, 31 - level), so the lowest level wins ties under max.  Pixels
 // outside the image are TMA zero fill whose delta is zero, so no thread
@@ -1386,19 +1490,19 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
   const uint32_t lstride = LS;       // between levels of one histogram
   const uint32_t hstride = NT * 8u;  // between histograms
   const uint32_t h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
-  // VAR B counts: same shape at half the stride, after the sums
+  // VAR B counts (16 bits): same shape at a quarter of the stride, after the sums
   const uint32_t cbase = sm.sums + L * LS;
-  const uint32_t cd = cbase - (sm.sums >> 1);
-  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<LS>, DeltaOpsB<LS>>::type;
+  const uint32_t cd = cbase - (sm.sums >> 2);
+  using Ops = typename std::conditional<VAR == kVarA, DeltaOpsA<LS>, DeltaOpsB<LS, 2u>>::type;
   Ops ops;
   if constexpr (VAR == kVarB) ops.cd = cd;
   auto hist = [&](int i) { return h0 + static_cast<uint32_t>(i) * hstride; };
-  auto cnt_of = [&](uint32_t s) { return (s >> 1) + cd; };
+  auto cnt_of = [&](uint32_t s) { return (s >> 2) + cd; };
 #pragma unroll
   for (int i = 0; i < NH; ++i)
     for (uint32_t lv = 0; lv < L; ++lv) {
       sts_zero64(hist(i) + lv * lstride);
-      if (VAR == kVarB) sts_zero32(cnt_of(hist(i) + lv * lstride));
+      if (VAR == kVarB) sts_u16(cnt_of(hist(i) + lv * lstride), 0u);
     }
 
   return ring_pass(
@@ -1430,9 +1534,14 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
         // count of level lv in histogram i (VAR A: the low word, count in bits 0..9)
         auto count_word = [&](int i, uint32_t lv) {
           const uint32_t a = hist(i) + lv * lstride;
-          return lds_u32(VAR == kVarA ? a : cnt_of(a));
+          if constexpr (VAR == kVarA)
+            return lds_u32(a);
+          else
+            return lds_u16(cnt_of(a));
         };
-        constexpr int CSH = VAR == kVarA ? 22 : 5;  // VAR A: drop the sums above the count
+        // the shift keeps the count's bits and drops the rest (VAR A: the
+        // sums above the 10-bit count; VAR B: the wrap of the 16-bit counts)
+        constexpr int CSH = VAR == kVarA ? 22 : 16;
         uint32_t best[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) best[i] = 0u;

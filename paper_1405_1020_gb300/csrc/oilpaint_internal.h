@@ -129,7 +129,8 @@ inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
   // (column path: cols_hist_bytes)
   if (kcols > 1) {
     const size_t nh = static_cast<size_t>(kcols) + static_cast<size_t>(hsplit(kcols, variant)) - 1u;
-    return nh * L * nt * (variant == kVarA ? 8u : 12u);
+    // variant B: 8-byte sums and a 16-bit count per bin
+    return nh * L * nt * (variant == kVarA ? 8u : 10u);
   }
   return static_cast<size_t>(L + 1u) * nt * bin_bytes(variant);
 }
