@@ -686,9 +686,10 @@ __device__ __forceinline__ void unpack_bin(uint32_t lo, uint32_t hi, uint32_t cn
 //
 // Variant B (16 <= r <= 44, word format 2), a 64-bit sums bin
 //   R:21 @0 | G:21 @21 | B:21 @42   (89^2 * 255 < 2^21)
-// plus a 32-bit count in a second array laid out like the sums with half the
-// stride, so a bin's count address is (sums address >> 1) + cd for one
-// CTA-wide constant cd.
+// plus a count in a second array laid out like the sums: 16 bits at a
+// quarter of the stride on the K-column path (a bin's count address is
+// (sums address >> 2) + cd for one CTA-wide constant cd), 32 bits at half
+// the stride on the column path.
 
 __device__ __forceinline__ void dh_delta(uint32_t w, uint32_t &lo, uint32_t &hi) {
   lo = w & 0xF003FC01u;
@@ -1441,7 +1442,8 @@ __device__ __forceinline__ void delta_step_split(const Ops &ops, const uint32_t 
 // histogram costs more occupancy than the chain gains, and a four-way split
 // of the four-column window histogram measured slower still (two more
 // histograms per thread, one resident CTA fewer per SM).  Variant B bins
-// (12 bytes) never split.
+// (10 bytes) never split: split, the K = 4 path ran 5-22% slower at r = 16..44
+// (5 instead of 7 resident CTAs per SM at r = 20, L = 20).
 constexpr int kSplit2 = 1;
 constexpr int kSplit4 = 2;
 __host__ __device__ constexpr int hsplit(int k, int var) {
