@@ -639,7 +639,7 @@ struct op_batch_s {
   uint32_t max_L;
   int device;
   DevInfo di;
-  // Images are split by radius (above 15: 12-byte bins) and by level count
+  // Images are split by radius (above 15: variant-B bins) and by level count
   // (above kBatchLevelSplit: larger histograms) into up to four groups.  Each
   // group is one persistent launch with its own configuration, shared-memory
   // size, grid, ticket queue and table segment, so images with small

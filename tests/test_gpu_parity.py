@@ -151,7 +151,7 @@ def test_fuzz(k, w, h, r, L, bpp, pad, mode, cfg):
 
 def _delta_fuzz_cases(n=56, seed=11):
     """Cases the difference-histogram path takes (L <= 32, 2 or 4 columns
-    per thread; 8-byte bins for r <= 15, 12-byte bins above): every r mod 4
+    per thread; 8-byte bins for r <= 15, variant-B bins above): every r mod 4
     (the tile's x shift), widths around the tile width, one-column and
     one-row images."""
     rng = np.random.default_rng(seed)
