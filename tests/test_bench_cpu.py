@@ -44,3 +44,9 @@ def test_reference_arm_prints_one_line_on_rank0_only():
     line = json.loads(p.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "Mpix/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_sweep_radius_list_parsing():
+    from paper_1405_1020_gb300 import sweep
+    assert sweep._parse_radii("1-10") == list(range(1, 11))
+    assert sweep._parse_radii("2,4,8") == [2, 4, 8]
