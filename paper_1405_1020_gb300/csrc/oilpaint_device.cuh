@@ -1601,22 +1601,6 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
       });
 }
 
-// Shared-memory atomic adds (the start-window histograms of the column path).
-__device__ __forceinline__ void red_add64(uint32_t addr, uint32_t lo, uint32_t hi) {
-  if (!OPK_SMEM_OK(addr, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u64 v;\n\t"
-      "mov.b64 v, {%1, %2};\n\t"
-      "red.shared.add.u64 [%0], v;\n\t}" ::"r"(addr),
-      "r"(lo), "r"(hi)
-      : "memory");
-}
-
-__device__ __forceinline__ void red_add32(uint32_t addr, uint32_t v) {
-  if (!OPK_SMEM_OK(addr, 4u)) return;
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
 // Shared-memory layout of the column path after the ring (all sizes in
 // bytes, Lp = L | 1 levels per histogram so that a column's histogram is an
 // odd number of 8-byte bins long and 32 lanes updating 32 neighbouring
