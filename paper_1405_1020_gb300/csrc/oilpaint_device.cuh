@@ -12,26 +12,33 @@
 //
 // Data path, per CTA tile of TW output columns x tile_h output rows:
 //   1. pack prepass (earlier kernel): every pixel becomes one 32-bit word
-//        level << 24 | R << 16 | G << 8 | B
+//      holding its level and R, G, B (format 0: level << 24 | R << 16 |
+//      G << 8 | B for one column per thread; formats 1 and 2 laid out so that
+//      a bin delta is one or two masks, for the K-column and column paths),
 //      so the level (section 4's quantisation) is computed once per pixel,
 //      not once per window visit;
 //   2. halo staging: chunks of `ch` packed rows, (TW + 2r) columns rounded to
 //      16 bytes, are copied by TMA (cp.async.bulk.tensor.2d) into a ring of
-//      shared-memory slots; an mbarrier per slot signals arrival;
-//   3. thread t owns output column x0 + t and a private histogram in shared
-//      memory laid out [level][thread] (so the 32 lanes of a warp always hit
-//      32 different banks whatever their levels); it slides down the tile;
-//   4. argmax over the L bins with a strict > scan from level 0;
+//      shared-memory slots; an mbarrier per slot signals arrival (bounded
+//      waits);
+//   3. the histograms slide down the tile: one per output column and thread
+//      (run_tile), or per thread a window histogram plus difference
+//      histograms covering K = 2 or 4 output columns (run_tile_delta, L <=
+//      32), or one per image column with the levels across a warp's lanes
+//      (run_tile_cols); bins are laid out so the 32 lanes of a warp hit 32
+//      different banks whatever their levels;
+//   4. argmax: the first level of the largest count (ties to the lowest), as
+//      a max over (count, reversed level) keys or a strict > scan;
 //   5. the three channel means and the byte stores.
 //
 // Bins (selected per image by the radius):
-//   variant A (r <= 15, window <= 961 pixels): one 64-bit word per bin,
-//       count:10 @54 | sumR:18 @36 | sumG:18 @18 | sumB:18 @0.
-//       No field can overflow into the next (961*255 < 2^18, 961 < 2^10), so
-//       one 64-bit add or subtract updates all four quantities.
-//   variant B (r <= 44, window <= 7921 pixels): a 64-bit word
-//       sumR:21 @42 | sumG:21 @21 | sumB:21 @0 (7921*255 < 2^21) plus a
-//       separate 32-bit count.
+//   variant A (r <= 15, window <= 961 pixels): one 64-bit word per bin whose
+//       fields (a 10-bit count and three 18-bit sums, 961*255 < 2^18) cannot
+//       overflow into each other, so one 64-bit add or subtract updates all
+//       four quantities (field order per word format, below);
+//   variant B (r <= 44, window <= 7921 pixels): a 64-bit word of three 21-bit
+//       sums (7921*255 < 2^21) plus a separate count (16 bits on the K-column
+//       path, 32 bits elsewhere).
 #pragma once
 
 #include <cuda.h>

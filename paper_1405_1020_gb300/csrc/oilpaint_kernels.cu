@@ -1,17 +1,20 @@
 // oilpaint_kernels.cu -- kernel entry points and their launchers.
 //
 //   pack_single_kernel / pack_batch_kernel  the pack prepass (one image / a
-//                                           batch; the batch form also resets
-//                                           the tile-queue counter)
+//                                           batch, one row per warp; the batch
+//                                           form also resets the groups'
+//                                           tile-queue counters)
 //   tile_plain_kernel<NT, VAR>              one CTA per output tile, one output
 //                                           column per thread (NT threads)
-//   tile_delta_kernel<NT, K>                one CTA per output tile, K output
+//   tile_delta_kernel<NT, K, VAR>           one CTA per output tile, K output
 //                                           columns per thread through
 //                                           difference histograms
+//   tile_cols_kernel<NW, TWK, VAR>          one CTA per output tile, column
+//                                           histograms swept by NW warps
 //   persistent_kernel<NT, K>                grid-sized CTAs pulling
-//                                           (image, tile) tickets from a
-//                                           device atomic until the queue of a
-//                                           whole batch is empty
+//                                           (image, tile) tickets from one
+//                                           batch group's device atomic until
+//                                           its queue is empty
 //   selftest_wait_kernel                    exercises the bounded mbarrier wait
 #include "oilpaint_internal.h"
 
