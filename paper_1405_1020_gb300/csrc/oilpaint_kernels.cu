@@ -1,9 +1,9 @@
 // oilpaint_kernels.cu -- kernel entry points and their launchers.
 //
-//   pack_single_kernel / pack_batch_kernel  the pack prepass (one image / a
-//                                           batch, one row per warp; the batch
-//                                           form also resets the groups'
-//                                           tile-queue counters)
+//   pack_single_kernel / pack_batch_kernel  the pack prepass (one image, a
+//                                           row per block / a batch, a row per
+//                                           warp; the batch form also resets
+//                                           the groups' tile-queue counters)
 //   tile_plain_kernel<NT, VAR>              one CTA per output tile, one output
 //                                           column per thread (NT threads)
 //   tile_delta_kernel<NT, K, VAR>           one CTA per output tile, K output
