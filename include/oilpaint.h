@@ -99,9 +99,10 @@ typedef struct op_s op_t;
  *                   other images on the one-column path.
  *   path            0: histograms kept per thread (the fields above);
  *                   1: column histograms with the levels across a warp's
- *                   lanes (NEXT-1 of the design notes' scope table: work per
- *                   pixel independent of r): a CTA keeps one histogram per
- *                   image column of its tile and halo, each warp sweeps
+ *                   lanes (Perreault and Hebert's constant-time column
+ *                   histograms: work per pixel independent of r): a CTA
+ *                   keeps one histogram per image column of its tile and
+ *                   halo, each warp sweeps
  *                   32 * cols_per_thread output columns of every row
  *                   (cols_per_thread 1 or 2), tile_w / cols_per_thread =
  *                   32, 64 or 128 threads; needs levels <= 32.
@@ -341,10 +342,19 @@ int op_selftest_wait_timeout(uint64_t timeout_ns, void *stream);
  * OP_NOALLOC_MAX_WORDS (e.g. 2048 x 2048); larger images return
  * OP_E_UNSUPPORTED.  Other arguments as op_create_ex / op_run; d_in and d_out
  * are device pointers the caller owns (height * stride bytes each).
- * The call is synchronous: it returns after `stream` has completed the work,
- * with OP_OK, OP_E_TIMEOUT (a bounded device wait gave up) or OP_E_CUDA.
- * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress), so make it before any stream capture.
+ * The call is synchronous: it returns after `stream` has completed the work.
+ * Returns OP_OK; OP_E_INVALID (a NULL pointer, a size, radius, level count
+ * or flag out of range, stride < width * bpp, overlapping buffers);
+ * OP_E_UNSUPPORTED (image larger than the array, or no launch configuration
+ * fits this device); OP_E_TIMEOUT (a bounded device wait gave up);
+ * OP_E_BOUNDS (bounds-checking build only); OP_E_CUDA (a CUDA call failed;
+ * the runtime's last error is cleared before returning).
+ * The first call on a device (and the first after a cudaDeviceReset) loads
+ * the library part that holds the array onto that device: the CUDA runtime
+ * then places the 16 MiB array in device memory, so that call needs that
+ * much free memory and returns OP_E_CUDA without it.  Make that first call
+ * before any stream capture.  Later calls find the array in place and
+ * allocate nothing.
  * All calls share the one array and it keeps the last call's contents;
  * calls that overlap on the GPU (other host threads, other streams) race on
  * it and must be serialised by the caller.

@@ -1,7 +1,8 @@
 """Builds the CUDA library paper_1405_1020_gb300/liboilpaint.so for sm_103a.
 
-Two translation units (kernels, C ABI) are compiled in parallel with nvcc and
-linked into one shared library with the CUDA runtime linked statically, so
+Three translation units (the kernels, the C ABI, and the allocation-free
+entry point with its device scratch array) are compiled in parallel with nvcc
+and linked into one shared library with the CUDA runtime linked statically, so
 the library needs nothing but the NVIDIA driver at run time.  The library is
 built in-tree (the package directory) and git-ignored.
 """

@@ -22,12 +22,9 @@
 using opk::ImgDesc;
 using opk::RingCfg;
 
+namespace opk {
+
 namespace {
-
-thread_local int g_last_error = OP_OK;
-constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // bounded device waits give up after 1 s
-
-// ------------------------------------------------------------ tensor maps
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -43,13 +40,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Tensor map of a packed image: w x h 32-bit words, rows ppitch words apart,
-// copied in {boxw, ch} boxes; out-of-range elements read as zero (the filter
-// never uses them: its windows are clipped to the image).
-int encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint32_t h,
-                      uint32_t ppitch, uint32_t boxw, uint32_t ch) {
+}  // namespace
+
+bool encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint32_t h,
+                       uint32_t ppitch, uint32_t boxw, uint32_t ch) {
   auto fn = encode_fn();
-  if (!fn) return OP_E_CUDA;
+  if (!fn) return false;
   cuuint64_t dims[2] = {w, h};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ppitch) * 4u};
   cuuint32_t box[2] = {boxw, ch};
@@ -57,8 +53,33 @@ int encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(packed), dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? OP_OK : OP_E_CUDA;
+  return r == CUDA_SUCCESS;
 }
+
+uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
+  double best = 1e300;
+  uint32_t best_h = H;
+  if (slots < 1) slots = 1;
+  for (uint32_t t = 1; t <= H; ++t) {
+    const uint32_t th = (H + t - 1) / t;
+    if (t > 1 && (H + th - 1) / th != t) continue;  // same tiling as a smaller t
+    const uint64_t tiles = static_cast<uint64_t>(tiles_x) * t;
+    const uint64_t waves = (tiles + slots - 1) / slots;
+    const double cost = static_cast<double>(waves) * (th + 2.0 * r);
+    if (cost < best) {
+      best = cost;
+      best_h = th;
+    }
+  }
+  return best_h;
+}
+
+}  // namespace opk
+
+namespace {
+
+thread_local int g_last_error = OP_OK;
+constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // bounded device waits give up after 1 s
 
 // ------------------------------------------------------------ device info
 
@@ -212,34 +233,12 @@ int pick_config(int r, uint32_t L, const DevInfo &di, op_config_t *out) {
   return check_config(*out, r, L, di);
 }
 
-// Tile height for an image of H rows cut into tiles_x tile columns when
-// `slots` CTAs can be resident at once: minimises waves x steps per tile,
-// where a tile of h output rows takes h + 2r steps (2r of them only fill the
-// running histogram) and a wave is `slots` tiles running side by side.
-uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
-  double best = 1e300;
-  uint32_t best_h = H;
-  if (slots < 1) slots = 1;
-  for (uint32_t t = 1; t <= H; ++t) {
-    const uint32_t th = (H + t - 1) / t;
-    if (t > 1 && (H + th - 1) / th != t) continue;  // same tiling as a smaller t
-    const uint64_t tiles = static_cast<uint64_t>(tiles_x) * t;
-    const uint64_t waves = (tiles + slots - 1) / slots;
-    const double cost = static_cast<double>(waves) * (th + 2.0 * r);
-    if (cost < best) {
-      best = cost;
-      best_h = th;
-    }
-  }
-  return best_h;
-}
-
 uint32_t effective_tile_h(const op_config_t &c, uint32_t w, uint32_t h, int r, uint32_t L,
                           const DevInfo &di) {
   if (c.tile_h) return std::min(c.tile_h, h);
   const opk::Geometry g = geometry_of(c, r, L, w);
   const int occ = std::max(1, opk::geometry_occupancy(g, smem_of(g, c, r, L)));
-  return auto_tile_h(h, g.tiles_x, r, static_cast<uint64_t>(occ) * di.sms);
+  return opk::auto_tile_h(h, g.tiles_x, r, static_cast<uint64_t>(occ) * di.sms);
 }
 
 bool valid_image(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int32_t r, uint32_t L,
@@ -508,9 +507,9 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   const op_config_t &c = op->cfg;
   const opk::Geometry g = geometry_of(c, op->r, op->L, op->w);
   if (!op->map_valid) {
-    st = encode_packed_map(&op->map, static_cast<const uint32_t *>(op->ws), op->w, op->h,
-                           op->ppitch, g.boxw, c.chunk_rows);
-    if (st != OP_OK) return st;
+    if (!opk::encode_packed_map(&op->map, static_cast<const uint32_t *>(op->ws), op->w, op->h,
+                                op->ppitch, g.boxw, c.chunk_rows))
+      return OP_E_CUDA;
     op->map_valid = true;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -946,7 +945,7 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
         const int g = grp[i];
         const double share = static_cast<double>(im.width) * im.height / gpix[g] *
                              b->grid_persist[g] * (gnum[g] > 1 ? 2.0 : 1.0);
-        th = auto_tile_h(std::max(1u, rows), geo[i].tiles_x, im.radius,
+        th = opk::auto_tile_h(std::max(1u, rows), geo[i].tiles_x, im.radius,
                          std::max<uint64_t>(1u, static_cast<uint64_t>(share)));
       }
       th = std::max(1u, std::min(th, rows));
@@ -1005,8 +1004,8 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
       d.path = 0u;
       const opk::Window win = opk::output_window(d.w, d.h, d.r, d.mode);
       opk::set_window(d, win);
-      const int st = encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc[g].ch);
-      if (st != OP_OK) return st;
+      if (!opk::encode_packed_map(&hm[k], d.packed, d.w, d.h, d.ppitch, d.boxw, b->rc[g].ch))
+        return OP_E_CUDA;
       hd[k] = d;
       htp[k + g] = static_cast<uint32_t>(tiles);
       hrp[k] = static_cast<uint32_t>(rows);

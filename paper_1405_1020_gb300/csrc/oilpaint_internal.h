@@ -167,6 +167,19 @@ inline void set_window(ImgDesc &d, const Window &o) {
   d.oy1 = o.y1;
 }
 
+// Tensor map of a packed image (defined with the C ABI): w x h 32-bit
+// words, rows ppitch words apart, copied in {boxw, ch} boxes; elements out
+// of range read as zero.  False if the driver's encoder is unavailable or
+// refuses the map.
+bool encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint32_t h,
+                       uint32_t ppitch, uint32_t boxw, uint32_t ch);
+
+// Tile height for an image of H output rows cut into tiles_x tile columns
+// when `slots` CTAs can be resident at once: minimises waves x steps per
+// tile, where a tile of h output rows takes h + 2r steps (2r of them only
+// fill the running histogram) and a wave is `slots` tiles side by side.
+uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots);
+
 // Launchers; each returns cudaSuccess or the launch error.
 cudaError_t launch_pack_single(const ImgDesc &d, int grid, cudaStream_t s);
 // nt threads per CTA (32, 64, 96, 128); kcols 1 (one column per thread,

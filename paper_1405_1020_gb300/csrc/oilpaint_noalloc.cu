@@ -12,18 +12,23 @@
 // compiled into the library.
 //
 // The scratch array is a file-scope __device__ array of kNoAllocWords 32-bit
-// words (16 MiB): every GPU that loads the library holds it until the
-// process exits.  Host code cannot use the array's name as a device address
-// (in host code it names a host-side stand-in), so the device address is
-// taken once per device with cudaGetSymbolAddress, with that device current,
-// on the first call made on it.  Every call shares the array and it keeps the
-// last call's contents; the pack prepass rewrites every word the filter then
-// reads, and the error word is cleared at the start of each call.  Calls that
-// overlap on the GPU (two host threads, two streams) race on the array.
-#include <cudaTypedefs.h>
-
+// words (16 MiB).  This file is a module of its own, and the CUDA runtime
+// loads a module (and with it places the array in device memory) the first
+// time the module is used on a device -- here, the first
+// cudaGetSymbolAddress of a call on that device, or the first after a
+// cudaDeviceReset.  That first call therefore needs 16 MiB of free device
+// memory and fails with OP_E_CUDA without it; later calls find the array in
+// place and allocate nothing.  The array stays until the process exits (or
+// the device is reset).
+//
+// Host code cannot use the array's name as a device address (in host code
+// it names a host-side stand-in), so every call asks the runtime for the
+// device address with cudaGetSymbolAddress, on the current device.  Every
+// call shares the array and it keeps the last call's contents; the pack
+// prepass rewrites every word the filter then reads, and the error word is
+// cleared at the start of each call.  Calls that overlap on the GPU (two
+// host threads, two streams) race on the array.
 #include <algorithm>
-#include <mutex>
 
 #include "oilpaint.h"
 #include "oilpaint_internal.h"
@@ -36,65 +41,13 @@ static __device__ __align__(256) uint32_t g_noalloc_error;
 namespace {
 
 constexpr size_t kNoAllocWords = OP_NOALLOC_MAX_WORDS;
-constexpr int kMaxDevices = 64;
 constexpr uint64_t kWaitTimeoutNs = 1000000000ull;
 
-struct DeviceScratch {
-  bool ready = false;
-  uint32_t *packed = nullptr;  // device address of g_noalloc_scratch
-  uint32_t *err = nullptr;     // device address of g_noalloc_error
-};
-
-std::mutex g_mu;
-DeviceScratch g_dev[kMaxDevices];
-
-// Looks the scratch addresses up for device `dev` (the current device).
-int scratch_for(int dev, DeviceScratch *out) {
-  if (dev < 0 || dev >= kMaxDevices) return OP_E_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_mu);
-  DeviceScratch &s = g_dev[dev];
-  if (!s.ready) {
-    void *p = nullptr, *e = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return OP_E_CUDA;
-    if (cudaGetSymbolAddress(&e, g_noalloc_error) != cudaSuccess) return OP_E_CUDA;
-    s.packed = static_cast<uint32_t *>(p);
-    s.err = static_cast<uint32_t *>(e);
-    s.ready = true;
-  }
-  *out = s;
-  return OP_OK;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
-// Output rows per CTA: the fewest waves of resident CTAs times the steps of
-// one tile (h output rows cost h + 2r steps).
-uint32_t pick_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
-  double best = 1e300;
-  uint32_t best_h = H;
-  for (uint32_t t = 1; t <= H; ++t) {
-    const uint32_t th = (H + t - 1) / t;
-    if (t > 1 && (H + th - 1) / th != t) continue;
-    const uint64_t waves = (static_cast<uint64_t>(tiles_x) * t + slots - 1) / slots;
-    const double cost = static_cast<double>(waves) * (th + 2.0 * r);
-    if (cost < best) {
-      best = cost;
-      best_h = th;
-    }
-  }
-  return best_h;
+// A CUDA call failed: clear the runtime's last error, so that it is not
+// reported again by a later, unrelated launch check, and return OP_E_CUDA.
+int cuda_failed() {
+  (void)cudaGetLastError();
+  return OP_E_CUDA;
 }
 
 }  // namespace
@@ -115,16 +68,24 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (static_cast<uint64_t>(ppitch) * height > kNoAllocWords) return OP_E_UNSUPPORTED;
 
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return OP_E_CUDA;
-  DeviceScratch sc;
-  int st = scratch_for(dev, &sc);
-  if (st != OP_OK) return st;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_failed();
+  // The arrays' device addresses on the current device (the first call on a
+  // device loads this file's module there; see above).
+  void *p_scratch = nullptr, *p_err = nullptr;
+  if (cudaGetSymbolAddress(&p_scratch, g_noalloc_scratch) != cudaSuccess ||
+      cudaGetSymbolAddress(&p_err, g_noalloc_error) != cudaSuccess)
+    return cuda_failed();
+  uint32_t *packed = static_cast<uint32_t *>(p_scratch);
+  uint32_t *d_err = static_cast<uint32_t *>(p_err);
   op_config_t cfg;
-  st = op_default_config(radius, levels, &cfg);
-  if (st != OP_OK) return st;
+  int st = op_default_config(radius, levels, &cfg);
+  if (st != OP_OK) {
+    if (st == OP_E_CUDA) (void)cudaGetLastError();
+    return st;
+  }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return OP_E_CUDA;
+    return cuda_failed();
 
   const int cpt = (cfg.cols_per_thread == 2 || cfg.cols_per_thread == 4)
                       ? static_cast<int>(cfg.cols_per_thread)
@@ -139,7 +100,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   opk::ImgDesc d{};
   d.in = d_in;
   d.out = d_out;
-  d.packed = sc.packed;
+  d.packed = packed;
   d.tmap = nullptr;
   d.w = width;
   d.h = height;
@@ -158,7 +119,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
     d.tile_h = std::min(cfg.tile_h, win.rows());
   } else {
     const int occ = std::max(1, opk::geometry_occupancy(g, smem));
-    d.tile_h = pick_tile_h(win.rows(), d.tiles_x, radius, static_cast<uint64_t>(occ) * sms);
+    d.tile_h = opk::auto_tile_h(win.rows(), d.tiles_x, radius, static_cast<uint64_t>(occ) * sms);
   }
   d.boxw = boxw;
   d.variant = static_cast<uint32_t>(g.variant);
@@ -167,32 +128,24 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   d.fmt = g.fmt;
   d.path = static_cast<uint32_t>(g.path);
 
-  auto fn = encode_fn();
-  if (!fn) return OP_E_CUDA;
   CUtensorMap map;
-  cuuint64_t dims[2] = {width, height};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ppitch) * 4u};
-  cuuint32_t box[2] = {boxw, cfg.chunk_rows};
-  cuuint32_t estr[2] = {1, 1};
-  if (fn(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, sc.packed, dims, strides, box, estr,
-         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return OP_E_CUDA;
+  if (!opk::encode_packed_map(&map, packed, width, height, ppitch, boxw, cfg.chunk_rows))
+    return cuda_failed();
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(sc.err, 0, sizeof(uint32_t), s) != cudaSuccess) return OP_E_CUDA;
+  if (cudaMemsetAsync(d_err, 0, sizeof(uint32_t), s) != cudaSuccess) return cuda_failed();
   const int pack_grid = opk::pack_grid_for(height, sms);
-  if (opk::launch_pack_single(d, pack_grid, s) != cudaSuccess) return OP_E_CUDA;
+  if (opk::launch_pack_single(d, pack_grid, s) != cudaSuccess) return cuda_failed();
   const dim3 grid(d.tiles_x, (win.rows() + d.tile_h - 1) / d.tile_h);
-  if (opk::launch_tile(g.nt, g.kcols, g.variant, d, map, rc, grid, smem, sc.err, kWaitTimeoutNs,
+  if (opk::launch_tile(g.nt, g.kcols, g.variant, d, map, rc, grid, smem, d_err, kWaitTimeoutNs,
                        s) != cudaSuccess)
-    return OP_E_CUDA;
+    return cuda_failed();
   uint32_t err = 0;
-  if (cudaMemcpyAsync(&err, sc.err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return OP_E_CUDA;
+    return cuda_failed();
   if (err) return OP_E_TIMEOUT;
   uint32_t bits = 0;
-  if (opk::take_check_error(&bits) != cudaSuccess) return OP_E_CUDA;
+  if (opk::take_check_error(&bits) != cudaSuccess) return cuda_failed();
   return bits ? OP_E_BOUNDS : OP_OK;
 }
