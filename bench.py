@@ -16,7 +16,8 @@ One JSON line is printed (rank 0).  Besides the headline it carries
   batched       the 64-image mixed batch, one persistent launch (CUDA graph)
                 vs one plain op_run per image,
   served        the continuous-batching server at 50/200/800 Mpix/s offered
-                (3 s per load by default; --serve-seconds 60 for the long run),
+                (60 s per load), then 10 s at 20,000 Mpix/s, above what it could
+                serve one request at a time; rounds' sizes and overlap reported,
   clocks        SM clocks and throttle reasons sampled during the timed region.
 
 --impl reference runs the CPU oracle (the only other implementation) on the
@@ -365,7 +366,8 @@ def run_ours(args):
         line["batched"] = batchbench.run(steps=max(3, args.steps // 2), warmup=2)
     if args.serve_seconds > 0:
         from paper_1405_1020_gb300 import serve
-        line["served"] = serve.bench_loads(seconds=args.serve_seconds)
+        line["served"] = serve.bench_loads(seconds=args.serve_seconds,
+                                           overload_seconds=args.overload_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(buf, args.cpu_seconds)
     op.close()
@@ -395,8 +397,11 @@ def main(argv=None):
     p.add_argument("--config", default=None, help="launch config JSON, e.g. '{\"tile_w\": 64}'")
     p.add_argument("--autotune", action="store_true", help="search the launch config first")
     p.add_argument("--skip-batch", action="store_true")
-    p.add_argument("--serve-seconds", type=float, default=3.0,
-                   help="seconds of served traffic per offered load (0 skips serving)")
+    p.add_argument("--serve-seconds", type=float, default=60.0,
+                   help="seconds of served traffic per configured offered load (0 skips "
+                        "serving)")
+    p.add_argument("--overload-seconds", type=float, default=10.0,
+                   help="seconds of served traffic at the load above single-request capacity")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--ref-rows", type=int, default=96, help="rows per reference step")

@@ -63,9 +63,13 @@ def _time_filter(op: OilPaint, src, dst, reps: int) -> float:
 
 def tune_image(width: int, height: int, bpp: int, stride: int, radius: int, levels: int,
                src: torch.Tensor | None = None, flags: int = B.OP_LEVEL_PAPER, reps: int = 5,
-               tile_hs=(0,), record: bool = True, verbose: bool = False) -> dict:
-    """Search the candidates on one image (a seeded camera-like image unless
-    `src` is given); returns {"config", "ms", "results"}."""
+               tile_hs=(0,), record: bool = True, verbose: bool = False, cands=None,
+               verify=None) -> dict:
+    """Search the candidates (`cands`, default `candidates(radius, levels,
+    tile_hs)`) on one image (a seeded camera-like image unless `src` is
+    given); every candidate must write the same bytes as the first, and
+    `verify(cfg, dst)`, if given, is called with each candidate's output.
+    Returns {"config", "ms", "results"}."""
     if src is None:
         from . import synth
         img = synth.camera_like(height, width, seed=2)
@@ -76,7 +80,7 @@ def tune_image(width: int, height: int, bpp: int, stride: int, radius: int, leve
     results = []
     op = OilPaint(width, height, radius, levels, bpp=bpp, stride=stride, flags=flags)
     try:
-        for cfg in candidates(radius, levels, tile_hs):
+        for cfg in (candidates(radius, levels, tile_hs) if cands is None else cands):
             try:
                 op.set_config(cfg)
             except B.OilPaintError as e:
@@ -86,6 +90,8 @@ def tune_image(width: int, height: int, bpp: int, stride: int, radius: int, leve
             ms = _time_filter(op, src, dst, reps)
             if op.sync_status() != B.OP_OK:
                 raise B.OilPaintError(f"device error under {cfg}")
+            if verify is not None:
+                verify(cfg, dst)
             if ref is None:
                 ref = dst.clone()
             elif not torch.equal(ref, dst):
@@ -128,7 +134,7 @@ def batch_candidates() -> list[dict]:
 
 
 def tune_batch(images: list[dict], max_radius: int, max_levels: int, reps: int = 7,
-               rounds: int = 1, verbose: bool = False) -> dict:
+               rounds: int = 1, verbose: bool = False, cands=None) -> dict:
     """Tune the configuration of each group of a batch created for
     (max_radius, max_levels) on `images` (dicts with src, w, h, stride, bpp,
     r, L; CUDA uint8 sources): coordinate descent over the groups, each
@@ -171,7 +177,7 @@ def tune_batch(images: list[dict], max_radius: int, max_levels: int, reps: int =
     best_ms = base_ms
     for _ in range(rounds):
         for k in keys:
-            for cfg in batch_candidates():
+            for cfg in (batch_candidates() if cands is None else cands):
                 B.check(B.op_batch_tune_table_set(k[0], k[1], B.op_config_t.make(**cfg)),
                         "op_batch_tune_table_set")
                 try:

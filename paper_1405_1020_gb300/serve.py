@@ -130,7 +130,20 @@ class _Round:
     rid: int
     tickets: list
     slot: int
-    done: object  # CUDA event
+    start: object  # CUDA event recorded on the round's stream before its work
+    done: object   # CUDA event recorded after it
+
+
+def overlapping_rounds(spans) -> int:
+    """How many rounds ran on the device while a round of another stream was
+    also running: spans are (slot, images, start_ms, done_ms) in one device
+    time base; two rounds overlap when each started before the other ended."""
+    n = 0
+    for i, (si, _, ai, bi) in enumerate(spans):
+        if any(sj != si and aj < bi and ai < bj
+               for j, (sj, _, aj, bj) in enumerate(spans) if j != i):
+            n += 1
+    return n
 
 
 @dataclass
@@ -142,6 +155,8 @@ class SessionStats:
     refused: int
     rounds: int
     mean_round_images: float
+    max_round_images: int
+    overlapping_rounds: int
     achieved_mpix_s: float
     p50_ms: float
     p99_ms: float
@@ -222,6 +237,7 @@ class OilPaintServer:
         in_flight: dict[int, _Round] = {}
         rounds = 0
         round_sizes = []
+        spans = []  # (stream slot, images, start ms, done ms) per finished round
         while not (client_done and not adm.waiting and not adm.admitted and not in_flight):
             busy = False
             while True:
@@ -241,6 +257,8 @@ class OilPaintServer:
                     continue
                 rnd = adm.next_round()
                 with torch.cuda.stream(stream):
+                    start = torch.cuda.Event(enable_timing=True)
+                    start.record(stream)
                     descs = self._descs(rnd)
                     b = self.batches[slot]
                     b.set(descs, stream)
@@ -252,14 +270,16 @@ class OilPaintServer:
                     done.record(stream)
                 for t in rnd:
                     t.round_id = rounds
-                in_flight[slot] = _Round(rounds, rnd, slot, done)
+                in_flight[slot] = _Round(rounds, rnd, slot, start, done)
                 rounds += 1
                 round_sizes.append(len(rnd))
                 busy = True
             for slot in list(in_flight):
                 rd = in_flight[slot]
                 if rd.done.query():
-                    t_done = t0 + ref.elapsed_time(rd.done) / 1e3
+                    done_ms = ref.elapsed_time(rd.done)
+                    spans.append((slot, len(rd.tickets), ref.elapsed_time(rd.start), done_ms))
+                    t_done = t0 + done_ms / 1e3
                     for t in rd.tickets:
                         t.t_done = t_done
                         adm.release(t)
@@ -283,7 +303,8 @@ class OilPaintServer:
             if st != 0:
                 raise RuntimeError(f"device error status {st} in a served round")
         info = {"t0": t0, "t_end": t_end, "rounds": rounds, "round_sizes": round_sizes,
-                "refused": len(adm.refused), "peak_reserved": adm.peak_reserved}
+                "round_spans": spans, "refused": len(adm.refused),
+                "peak_reserved": adm.peak_reserved}
         return tickets, info
 
     def close(self):
@@ -311,6 +332,8 @@ def summarize(tickets, info, offered_mpix_s: float, warmup_s: float) -> SessionS
         requests=len(tickets), completed=len(done), refused=info["refused"],
         rounds=info["rounds"],
         mean_round_images=statistics.mean(info["round_sizes"]) if info["round_sizes"] else 0.0,
+        max_round_images=max(info["round_sizes"], default=0),
+        overlapping_rounds=overlapping_rounds(info.get("round_spans", [])),
         achieved_mpix_s=px / span / 1e6 if span > 0 else 0.0,
         p50_ms=pct(50), p99_ms=pct(99), mean_ms=statistics.mean(lat) if lat else float("nan"),
         peak_reserved_gb=info["peak_reserved"] / 1e9)
@@ -349,24 +372,39 @@ def check_samples(server: OilPaintServer, tickets) -> int:
     return n
 
 
-def bench_loads(seconds: float = 5.0, warmup_s: float = 1.0, loads=(50.0, 200.0, 800.0),
+# Offered load above what the server could take one request at a time: a
+# 4.36 MP mean request alone takes about 0.35 ms end to end (about
+# 12,000 Mpix/s), so at 20,000 Mpix/s requests queue up and only rounds of
+# several requests, overlapping on two streams, keep up.
+OVERLOAD_MPIX_S = 20000.0
+
+
+def bench_loads(seconds: float = 60.0, warmup_s: float = 1.0, loads=(50.0, 200.0, 800.0),
+                overload_mpix_s: float | None = OVERLOAD_MPIX_S, overload_seconds: float = 10.0,
                 seed: int = 4, sample_every: int = 100) -> dict:
     """Serves Poisson traffic at each offered load (Mpix/s) for `seconds` after
-    `warmup_s`; returns p50/p99 latency and achieved Mpix/s per load."""
+    `warmup_s`, then at `overload_mpix_s` for `overload_seconds`; returns p50/p99
+    latency, achieved Mpix/s and the rounds' sizes and overlap per load.  Every
+    `sample_every`-th request is re-run alone and must give the same bytes."""
     pool = make_pool()
     server = OilPaintServer(pool)
     mean_px = (24e6 - 0.1e6) / math.log(24e6 / 0.1e6)  # mean of log-uniform 0.1..24 MP
     out = {"workload": "Poisson single-image requests, 0.1-24 MP log-uniform, r uniform 1..20, "
                        "L=20, RGB crops of a device-resident camera-like pool",
            "hbm_cap_gb": 40, "seconds_per_load": seconds, "warmup_s": warmup_s, "loads": []}
+    plan = [(load, seconds, "configured") for load in loads]
+    if overload_mpix_s:
+        plan.append((overload_mpix_s, overload_seconds, "above single-request capacity"))
     try:
-        for k, load in enumerate(loads):
+        for k, (load, secs, kind) in enumerate(plan):
             rate = load * 1e6 / mean_px
-            reqs = synth.poisson_requests(rate, seconds + warmup_s, seed=seed + k,
+            reqs = synth.poisson_requests(rate, secs + warmup_s, seed=seed + k,
                                           pool_shapes=(POOL_SHAPE,))
-            tickets, info = server.serve(reqs, sample_every=sample_every)
+            every = sample_every if kind == "configured" else 10 * sample_every
+            tickets, info = server.serve(reqs, sample_every=every)
             st = summarize(tickets, info, load, warmup_s)
-            d = st.as_dict()
+            d = {"kind": kind, **st.as_dict()}
+            d["seconds"] = secs
             d["rate_req_s"] = round(rate, 2)
             d["resampled_identical"] = check_samples(server, tickets)
             out["loads"].append(d)

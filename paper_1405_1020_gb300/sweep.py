@@ -5,10 +5,12 @@
 For every radius: pack + filter time per image (CUDA events around op_run on
 the launching stream, a 512 MiB write between steps to flush L2, the
 committed tuning table's configuration), Mpix/s, the filter's share, and two
-rooflines of the filter: the integer-ALU one of the method's op count
-(16r + L + 11 per pixel, 152 SMs x 128 lanes x the SM clock) and HBM
-(algorithmic bytes 3 + 3 per RGB pixel plus the packed word's 4 + 4, against
-the measured copy bandwidth).  Prints one JSON line.
+rooflines: the filter against the integer-ALU peak of the method's op count
+(16r + L + 11 per pixel, 152 SMs x 128 lanes x the SM clock), and the whole
+step against HBM with the algorithmic bytes only -- 3 bytes read and 3
+written per RGB pixel; the packed words' round trip (4 + 4 bytes per pixel)
+is a choice of this implementation, not work the method needs, so it is
+reported beside (`moved_bytes_frac`), not counted.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -75,7 +77,8 @@ def run(radii=range(1, 11), steps: int = 50, warmup: int = 5, levels: int = 20) 
             "r": r, "ms": round(ms, 4), "filter_ms": round(fms, 4),
             "mpix_s": round(px / ms / 1e3, 1),
             "alu_frac": round(ops * px / (fms / 1e3) / int_peak, 4),
-            "hbm_frac": round((3 + 3 + 4 + 4) * px / (ms / 1e3) / (hbm * 1e9), 4),
+            "hbm_frac": round((3 + 3) * px / (ms / 1e3) / (hbm * 1e9), 4),
+            "moved_bytes_frac": round((3 + 3 + 4 + 4) * px / (ms / 1e3) / (hbm * 1e9), 4),
             "config": {k: cfg[k] for k in ("tile_w", "chunk_rows", "cols_per_thread", "path")},
         })
     return {"workload": "1920x1080 blobs RGB (seed 1), L=20", "steps": steps,

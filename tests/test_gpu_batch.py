@@ -7,7 +7,7 @@ import torch
 import __graft_entry__
 import oracle
 from paper_1405_1020_gb300 import binding as B
-from paper_1405_1020_gb300 import synth
+from paper_1405_1020_gb300 import batchbench, synth
 from paper_1405_1020_gb300.filter import TUNING_TABLE, Batch, OilPaint, load_tuning
 from tests.pins import OUT_FILL
 
@@ -303,3 +303,31 @@ def test_batch_tune_table_entry_is_used_where_it_fits():
         B.op_batch_tune_table_set(15, 20, None)
         B.op_batch_tune_table_set(44, 32, None)
         load_tuning(TUNING_TABLE)
+
+
+def test_benchmark_batch_64_images_equal_oracle():
+    """The measured mixed batch (64 camera-like RGB images, log-uniform
+    320x240..4000x3000 pixels, r in {2,4,8,12,20}, L in {16,20,32}), run the
+    way the benchmark runs it -- one graph replay of the grouped persistent
+    launches -- against the oracle on every byte of every image."""
+    images = batchbench.make_batch(synth.batch_specs(n=64), batchbench.make_pool())
+    outs = [torch.full_like(im["src"], OUT_FILL) for im in images]
+    torch.cuda.synchronize()
+    pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
+    b = Batch(64, pix + 4096, max(im["r"] for im in images), max(im["L"] for im in images))
+    stream = torch.cuda.Stream()
+    try:
+        b.set([(im["src"], o, im["w"], im["h"], im["stride"], 3, im["r"], im["L"])
+               for im, o in zip(images, outs)], stream)
+        b.capture(stream)
+        b.launch_graph(stream)
+        assert b.sync_status(stream) == B.OP_OK
+        assert len(b.groups()) == 4
+    finally:
+        b.close()
+    for k, (im, o) in enumerate(zip(images, outs)):
+        buf = im["src"].cpu().numpy()
+        want = np.full(buf.size, OUT_FILL, np.uint8)
+        oracle.oilpaint(buf, im["w"], im["h"], im["stride"], 3, im["r"], im["L"], out=want)
+        assert np.array_equal(o.cpu().numpy(), want), (
+            f"image {k} ({im['w']}x{im['h']} r={im['r']} L={im['L']}) differs from the oracle")

@@ -84,35 +84,17 @@ def camera_12mp():
     return buf, stride
 
 
-def _sample_rows(h, r, n, seed):
-    rng = np.random.default_rng(seed)
-    rows = set(range(0, min(h, r + 2))) | set(range(max(0, h - r - 2), h))
-    rows |= set(int(v) for v in rng.integers(0, h, n))
-    return sorted(rows)
-
-
 @pytest.mark.parametrize("L", [20, 64, 256])
-def test_camera_12mp_rgba_r15_sampled_rows(camera_12mp, L):
-    """4000x3000 RGBA-stride camera-like (seed 2), r=15: the whole GPU output
-    against oracle rows covering both borders plus random rows."""
+def test_camera_12mp_rgba_r15_whole_image(camera_12mp, L):
+    """4000x3000 RGBA-stride camera-like (seed 2), r=15, L = 20 (the measured
+    workload, in the launch configuration the benchmark uses), 64 and 256:
+    every byte of the GPU output against the oracle's whole image."""
     buf, stride = camera_12mp
     w, h, r = 4000, 3000, 15
     got = gpu_filter(buf, w, h, stride, 4, r, L)
-    rows = _sample_rows(h, r, 24, seed=L)
-    want = np.full(buf.size, OUT_FILL, np.uint8)
-    for y in rows:
-        oracle.oilpaint_rows(buf, w, h, stride, 4, r, L, y, y + 1, out=want)
-    g = got[: h * stride].reshape(h, stride)
-    e = want[: h * stride].reshape(h, stride)
-    for y in rows:
-        assert np.array_equal(g[y], e[y]), f"row {y} differs (L={L})"
-    # random single pixels anywhere
-    rng = np.random.default_rng(100 + L)
-    xs = rng.integers(0, w, 300)
-    ys = rng.integers(0, h, 300)
-    rgb = oracle.oilpaint_pixels(buf, w, h, stride, 4, r, L, xs, ys)
+    want = cpu_filter(buf, w, h, stride, 4, r, L)
+    assert_same(got, want, w, h, stride, 4, f"12 MP r=15 L={L}")
     px = oracle.view_pixels(got, w, h, stride, 4)
-    assert np.array_equal(px[ys, xs, :3], rgb)
     assert (px[..., 3] == 255).all()
 
 

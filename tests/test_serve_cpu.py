@@ -65,3 +65,14 @@ def test_poisson_requests_shape():
     assert all(r.x0 + r.width <= 6600 and r.y0 + r.height <= 4400 for r in rs)
     assert all(1 <= r.radius <= 20 for r in rs)
     assert [r.t_arrival for r in rs] == sorted(r.t_arrival for r in rs)
+
+
+def test_overlapping_rounds_counts_cross_stream_overlap_only():
+    # (stream slot, images, start ms, done ms)
+    spans = [(0, 3, 0.0, 2.0), (1, 2, 1.0, 3.0),   # overlap across streams
+             (0, 1, 2.5, 4.0),                     # overlaps round 1
+             (0, 4, 5.0, 6.0), (0, 1, 5.5, 7.0),   # same stream: not counted
+             (1, 2, 7.0, 8.0)]                     # starts when the last ends
+    assert serve.overlapping_rounds(spans) == 3
+    assert serve.overlapping_rounds([]) == 0
+    assert serve.overlapping_rounds([(0, 1, 0.0, 1.0), (1, 1, 1.0, 2.0)]) == 0
