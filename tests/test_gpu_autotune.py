@@ -89,7 +89,9 @@ def test_tune_batch_winner_is_used_and_equals_oracle():
         res = autotune.tune_batch(images, 9, 20, reps=3, cands=cands)
         assert list(res["groups"]) == ["9,20"]
         best = res["groups"]["9,20"]["config"]
-        assert best in cands
+        # the winner is a candidate, or the group's untuned default when no
+        # candidate beat it; either way it is recorded in the batch table
+        assert best in cands or res["ms"] == res["ms_untuned"]
         assert res["ms"] <= res["ms_untuned"]
         pix = Batch.padded_pixels([(im["w"], im["h"]) for im in images])
         b = Batch(len(images), pix + 4096, 9, 20)
