@@ -46,13 +46,27 @@ bool encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uin
                        uint32_t ppitch, uint32_t boxw, uint32_t ch) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {w, h};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ppitch) * 4u};
-  cuuint32_t box[2] = {boxw, ch};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(packed), dims,
-                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r;
+  if (boxw <= kMaxBox2dWords) {
+    cuuint64_t dims[2] = {w, h};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ppitch) * 4u};
+    cuuint32_t box[2] = {boxw, ch};
+    cuuint32_t estr[2] = {1, 1};
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(packed), dims, strides,
+           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    // {4 words, ppitch / 4 groups, rows}: the same rows, read in groups of
+    // four words, so that a box row may be up to 4 * 256 words wide
+    if (boxw % 4u || boxw > kMaxBoxWords || ppitch % 4u) return false;
+    cuuint64_t dims[3] = {4, ppitch / 4u, h};
+    cuuint64_t strides[2] = {16, static_cast<cuuint64_t>(ppitch) * 4u};
+    cuuint32_t box[3] = {4, boxw / 4u, ch};
+    cuuint32_t estr[3] = {1, 1, 1};
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t *>(packed), dims, strides,
+           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   return r == CUDA_SUCCESS;
 }
 
@@ -128,8 +142,9 @@ std::map<std::pair<int, uint32_t>, op_config_t> g_batch_tune;
 
 // Output columns per thread and threads per CTA of a configuration.
 int cols_per_thread(const op_config_t &c) {
-  return (c.cols_per_thread == 2 || c.cols_per_thread == 4) ? static_cast<int>(c.cols_per_thread)
-                                                           : 1;
+  return (c.cols_per_thread == 2 || c.cols_per_thread == 4 || c.cols_per_thread == 8)
+             ? static_cast<int>(c.cols_per_thread)
+             : 1;
 }
 uint32_t threads_of(const op_config_t &c) {
   return c.tile_w / static_cast<uint32_t>(cols_per_thread(c));
@@ -139,12 +154,13 @@ uint32_t threads_of(const op_config_t &c) {
 bool config_in_range(const op_config_t &c) {
   if (c.path > 1u) return false;
   if (c.cols_per_thread != 0 && c.cols_per_thread != 1 && c.cols_per_thread != 2 &&
-      c.cols_per_thread != 4)
+      c.cols_per_thread != 4 && c.cols_per_thread != 8)
     return false;
   const uint32_t cpt = static_cast<uint32_t>(cols_per_thread(c));
   if (c.tile_w % cpt) return false;
   const uint32_t nt = c.tile_w / cpt;
   if (nt != 32 && nt != 64 && nt != 96 && nt != 128) return false;
+  if (cpt == 8u && (nt > 64 || c.path != 0u)) return false;  // 32 or 64 threads x 8
   if (c.path == 1u && (cpt == 4u || nt == 96u)) return false;  // 1, 2 or 4 warps x 32 or 64
   if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4) return false;
   return c.tile_h <= OP_MAX_DIM;
@@ -201,7 +217,7 @@ int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
   // the path and columns asked for must apply (K columns and the column
   // histograms need L <= 32)
   if (g.path != static_cast<int>(c.path) || g.kcols != cols_per_thread(c)) return OP_E_UNSUPPORTED;
-  if (g.boxw > 256u) return OP_E_UNSUPPORTED;
+  if (g.boxw > opk::kMaxBoxWords) return OP_E_UNSUPPORTED;
   if (smem_of(g, c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
   return OP_OK;
 }
@@ -695,10 +711,10 @@ constexpr uint32_t kHdrWords = kHdrTotal + 1;
 // L levels in one persistent CTA; its shared memory and CTAs per SM if so.
 bool batch_group_fits(const op_config_t &c, int32_t r, uint32_t L, const DevInfo &di,
                       size_t *smem, int *occ) {
-  if (!config_in_range(c) || c.path != 0u) return false;
+  if (!config_in_range(c) || c.path != 0u || cols_per_thread(c) > 4) return false;
   const BatchNeeds nd = batch_needs(c, r, L);
   const size_t sm = batch_smem(c, nd);
-  if (nd.boxw > 256u || sm > di.smem_optin - 1024u) return false;
+  if (nd.boxw > opk::kMaxBoxWords || sm > di.smem_optin - 1024u) return false;
   const int o = opk::tile_occupancy(threads_of(c), true, cols_per_thread(c), -1, sm);
   if (o < 1) return false;
   *smem = sm;

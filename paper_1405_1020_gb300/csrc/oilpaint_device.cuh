@@ -98,6 +98,16 @@ constexpr uint32_t kModeLiteral = 2u;
 // (5-bit level field next to the valid bit).
 constexpr int kDeltaMaxRadius = 44;
 constexpr uint32_t kDeltaMaxLevels = 32;
+// Eight columns per thread (run_tile_delta8): variant-A bins, 4 <= r <= 15.
+constexpr int kDelta8MinRadius = 4;
+constexpr int kDelta8MaxRadius = 15;
+
+// Halo boxes up to kMaxBox2dWords words wide are 2-D TMA copies; wider ones
+// (up to kMaxBoxWords) use the 3-D view of the packed image (tma_load_3d),
+// which reads the padding words at the end of each packed row: the pack
+// prepass writes them as zero.
+constexpr uint32_t kMaxBox2dWords = 256;
+constexpr uint32_t kMaxBoxWords = 1024;
 
 // Geometry of the shared-memory halo ring, fixed per launch.  Chunk k of a
 // tile brings the ch rows entering the window during its steps and the ch
@@ -213,6 +223,19 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// 3-D tiled TMA load: the packed image seen as {4 words, ppitch / 4 groups,
+// rows}, a box of {4, boxw / 4, ch} at group g, row y.  It lands in shared
+// memory exactly as the 2-D box of boxw words would, and serves halo rows
+// wider than the 256 elements a box dimension may hold.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int32_t g,
+                                            int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(g), "r"(y), "r"(bar)
       : "memory");
 }
 
@@ -507,6 +530,9 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
   uint32_t *dst = d.packed + static_cast<size_t>(y) * d.ppitch;
   const uint32_t L = d.L, mode = d.mode, w = d.w;
   const uint32_t fmt = d.fmt;
+  // the words after the last pixel, up to the 16-byte row pitch, are zero
+  // (3-D halo copies read them; zero is the word of no pixel)
+  if (tid < d.ppitch - w) dst[w + tid] = 0u;
   auto word = [&](uint32_t R, uint32_t G, uint32_t B) {
     return fmt == 1u   ? pack_word_delta(R, G, B, L, mode)
            : fmt == 2u ? pack_word_delta_b(R, G, B, L, mode)
@@ -1120,8 +1146,13 @@ __device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *t
     }
 #endif
     mbar_arrive_expect_tx(bar, 2u * box_bytes);
-    tma_load_2d(dst, tmap, xs, E0 + k * ch, bar);
-    tma_load_2d(dst + rc.half_bytes, tmap, xs, E0 + k * ch - 2 * r - 1, bar);
+    if (boxw > kMaxBox2dWords) {  // xs is a multiple of 4: a whole group
+      tma_load_3d(dst, tmap, xs >> 2, E0 + k * ch, bar);
+      tma_load_3d(dst + rc.half_bytes, tmap, xs >> 2, E0 + k * ch - 2 * r - 1, bar);
+    } else {
+      tma_load_2d(dst, tmap, xs, E0 + k * ch, bar);
+      tma_load_2d(dst + rc.half_bytes, tmap, xs, E0 + k * ch - 2 * r - 1, bar);
+    }
   };
 
   __syncthreads();  // the previous tile no longer reads the ring
@@ -1604,6 +1635,389 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
             const uint32_t B = (hi >> 10) & 0x1FFFFFu;
             store_pixel(d, x, y, R / cnt, G / cnt, B / cnt, alpha[i]);
           }
+        }
+      });
+}
+
+// ------------------------------------------------ eight columns per thread
+//
+// K = 8 output columns per thread (run_tile_delta8): variant-A bins and word
+// format 1, 4 <= r <= 15, L <= 32.  As in run_tile_delta, thread t owns
+// columns xa .. xa+7 (xa = x0 + 8t) and keeps H, the histogram of the window
+// of column xa, and D_1 .. D_7, the histograms of column xa+i+r minus column
+// xa+i-1-r: 2(2r+1) + 28 bin updates per 8 outputs (11.25 per output at
+// r = 15, against 18.5 with four columns).  With eight windows the argmax
+// would read eight count words per level, so the counts of D_1 .. D_7 are
+// kept a second time, as signed bytes packed into two words per level and
+// thread (DC: D_1..D_4 at bits 8(i-1) of word 0, D_5..D_7 at bits 8(i-5) of
+// word 1; a pixel adds its valid bit there, so the zero words outside the
+// image count nothing), and a level costs three loads: H's low word and the
+// two DC words.
+// A D_i count lies in [-31, 31] (two columns of at most 31 pixels), so the
+// prefix sums of the bytes of one word lie in [-124, 124]: multiplying the
+// word by 0x01010101 replaces each byte by the sum of the bytes up to it (the
+// word is linear in its signed bytes mod 2^32), and adding 0x80808080 then
+// maps every prefix to an unsigned byte with no carry between bytes.
+//
+// Shared memory (after the ring): 64-bit bins [level][histogram 0..7][thread]
+// (H is histogram 0, D_i histogram i), then the DC words [level][word][thread].
+
+#define OPK_BLK_HD_HEAD                                                     \
+  "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1, e, f;\n\t.reg .pred p, q;\n\t" \
+  "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"                                    \
+  "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"                                    \
+  "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"                                    \
+  "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"                                    \
+  "ld.shared.u32 e, [%12];\n\t"                                             \
+  "ld.shared.u32 f, [%13];\n\t"                                             \
+  "add.cc.u32 a0, a0, %1;\n\t"                                              \
+  "addc.u32 a1, a1, %2;\n\t"                                                \
+  "add.cc.u32 c0, c0, %7;\n\t"                                              \
+  "addc.u32 c1, c1, %8;\n\t"                                                \
+  "add.u32 e, e, %14;\n\t"                                                  \
+  "setp.eq.u32 p, %0, %3;\n\t"                                              \
+  "setp.eq.u32 q, %6, %9;\n\t"                                              \
+  "selp.b32 b0, a0, b0, p;\n\t"                                             \
+  "selp.b32 b1, a1, b1, p;\n\t"                                             \
+  "selp.b32 d0, c0, d0, q;\n\t"                                             \
+  "selp.b32 d1, c1, d1, q;\n\t"                                             \
+  "selp.b32 f, e, f, q;\n\t"
+#define OPK_BLK_HD_TAIL                                                     \
+  "sub.cc.u32 d0, d0, %10;\n\t"                                             \
+  "subc.u32 d1, d1, %11;\n\t"                                               \
+  "sub.u32 f, f, %15;\n\t"                                                  \
+  "st.shared.v2.u32 [%0], {a0, a1};\n\t"                                    \
+  "st.shared.v2.u32 [%3], {b0, b1};\n\t"                                    \
+  "st.shared.v2.u32 [%6], {c0, c1};\n\t"                                    \
+  "st.shared.v2.u32 [%9], {d0, d1};\n\t"                                    \
+  "st.shared.u32 [%12], e;\n\t"                                             \
+  "st.shared.u32 [%13], f;\n\t}"
+
+// +(alo, ahi) at A, then -(blo, bhi) (SUB) or +(blo, bhi) at B, on one
+// histogram (A may equal B); with it +(clo, chi) at C and -(dlo, dhi) at D
+// on a second histogram and +sc at count word E, -sd at F, where E == F
+// exactly when C == D.  All six loads are issued first.
+template <bool SUB>
+__device__ __forceinline__ void bin_pair_dpair(uint32_t A, uint32_t alo, uint32_t ahi, uint32_t B,
+                                               uint32_t blo, uint32_t bhi, uint32_t C,
+                                               uint32_t clo, uint32_t chi, uint32_t D,
+                                               uint32_t dlo, uint32_t dhi, uint32_t E, uint32_t F,
+                                               uint32_t sc, uint32_t sd) {
+  if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u) ||
+      !OPK_SMEM_OK(E, 4u) || !OPK_SMEM_OK(F, 4u))
+    return;
+  if constexpr (SUB) {
+    asm volatile(OPK_BLK_HD_HEAD
+                 "sub.cc.u32 b0, b0, %4;\n\t"
+                 "subc.u32 b1, b1, %5;\n\t" OPK_BLK_HD_TAIL ::"r"(A),
+                 "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi),
+                 "r"(D), "r"(dlo), "r"(dhi), "r"(E), "r"(F), "r"(sc), "r"(sd));
+  } else {
+    asm volatile(OPK_BLK_HD_HEAD
+                 "add.cc.u32 b0, b0, %4;\n\t"
+                 "addc.u32 b1, b1, %5;\n\t" OPK_BLK_HD_TAIL ::"r"(A),
+                 "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi),
+                 "r"(D), "r"(dlo), "r"(dhi), "r"(E), "r"(F), "r"(sc), "r"(sd));
+  }
+}
+#undef OPK_BLK_HD_HEAD
+#undef OPK_BLK_HD_TAIL
+
+// +(clo, chi) at C, -(dlo, dhi) at D (one histogram, C may equal D), +sc
+// at count word E, -sd at F (E == F exactly when C == D): four loads first.
+__device__ __forceinline__ void bin_dpair(uint32_t C, uint32_t clo, uint32_t chi, uint32_t D,
+                                          uint32_t dlo, uint32_t dhi, uint32_t E, uint32_t F,
+                                          uint32_t sc, uint32_t sd) {
+  if (!OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u) || !OPK_SMEM_OK(E, 4u) || !OPK_SMEM_OK(F, 4u))
+    return;
+  asm volatile(
+      "{\n\t.reg .u32 c0, c1, d0, d1, e, f;\n\t.reg .pred q;\n\t"
+      "ld.shared.v2.u32 {c0, c1}, [%0];\n\t"
+      "ld.shared.v2.u32 {d0, d1}, [%3];\n\t"
+      "ld.shared.u32 e, [%6];\n\t"
+      "ld.shared.u32 f, [%7];\n\t"
+      "add.cc.u32 c0, c0, %1;\n\t"
+      "addc.u32 c1, c1, %2;\n\t"
+      "add.u32 e, e, %8;\n\t"
+      "setp.eq.u32 q, %0, %3;\n\t"
+      "selp.b32 d0, c0, d0, q;\n\t"
+      "selp.b32 d1, c1, d1, q;\n\t"
+      "selp.b32 f, e, f, q;\n\t"
+      "sub.cc.u32 d0, d0, %4;\n\t"
+      "subc.u32 d1, d1, %5;\n\t"
+      "sub.u32 f, f, %9;\n\t"
+      "st.shared.v2.u32 [%0], {c0, c1};\n\t"
+      "st.shared.v2.u32 [%3], {d0, d1};\n\t"
+      "st.shared.u32 [%6], e;\n\t"
+      "st.shared.u32 [%7], f;\n\t}" ::"r"(C),
+      "r"(clo), "r"(chi), "r"(D), "r"(dlo), "r"(dhi), "r"(E), "r"(F), "r"(sc), "r"(sd));
+}
+
+// Addresses of one thread's K = 8 histograms and count words.
+template <int NT>
+struct Delta8 {
+  static constexpr uint32_t kHS = NT * 8u;    // between histograms
+  static constexpr uint32_t kLS = 8u * kHS;   // between levels (bins)
+  static constexpr uint32_t kDLS = NT * 8u;   // between levels (DC words: two per thread)
+  static constexpr uint32_t kDW = NT * 4u;    // between a level's two DC words
+  uint32_t h0;   // H's level-0 bin of this thread
+  uint32_t dc0;  // this thread's first DC word of level 0
+
+  // bin of word w's level in histogram i (level field at bits 1..5: w & 0x3E
+  // is twice the level)
+  __device__ __forceinline__ uint32_t bin(int i, uint32_t w) const {
+    return h0 + static_cast<uint32_t>(i) * kHS + (w & 0x3Eu) * (kLS / 2u);
+  }
+  // DC word holding D_i's count at word w's level
+  __device__ __forceinline__ uint32_t dc(int i, uint32_t w) const {
+    return dc0 + static_cast<uint32_t>((i - 1) >> 2) * kDW + (w & 0x3Eu) * (kDLS / 2u);
+  }
+  // D_i's count delta of word w in its DC word: the valid bit (bit 0: 1 for
+  // an image pixel, 0 for the zero words outside the image) moved to D_i's byte
+  static __device__ __forceinline__ uint32_t cnt_of(int i, uint32_t w) {
+    return (w & 1u) << (8 * ((i - 1) & 3));
+  }
+  // H: +e -l (or, filling, +e +l); D_i: +a -b
+  template <bool SUB>
+  __device__ __forceinline__ void hd(uint32_t e, uint32_t l, int i, uint32_t a, uint32_t b) const {
+    uint32_t elo, ehi, llo, lhi, alo, ahi, blo, bhi;
+    dh_delta(e, elo, ehi);
+    dh_delta(l, llo, lhi);
+    dh_delta(a, alo, ahi);
+    dh_delta(b, blo, bhi);
+    bin_pair_dpair<SUB>(bin(0, e), elo, ehi, bin(0, l), llo, lhi, bin(i, a), alo, ahi, bin(i, b),
+                        blo, bhi, dc(i, a), dc(i, b), cnt_of(i, a), cnt_of(i, b));
+  }
+  // H: +e -l
+  __device__ __forceinline__ void h(uint32_t e, uint32_t l) const {
+    uint32_t elo, ehi, llo, lhi;
+    dh_delta(e, elo, ehi);
+    dh_delta(l, llo, lhi);
+    bin_addsub64_chain(bin(0, e), elo, ehi, bin(0, l), llo, lhi);
+  }
+  // H: +a +b
+  __device__ __forceinline__ void h_add2(uint32_t a, uint32_t b) const {
+    uint32_t alo, ahi, blo, bhi;
+    dh_delta(a, alo, ahi);
+    dh_delta(b, blo, bhi);
+    bin_add64x2_chain(bin(0, a), alo, ahi, bin(0, b), blo, bhi);
+  }
+  // H: +a
+  __device__ __forceinline__ void h_add(uint32_t a) const {
+    uint32_t alo, ahi;
+    dh_delta(a, alo, ahi);
+    bin_add64(bin(0, a), alo, ahi);
+  }
+  // D_i: +a -b
+  __device__ __forceinline__ void d(int i, uint32_t a, uint32_t b) const {
+    uint32_t alo, ahi, blo, bhi;
+    dh_delta(a, alo, ahi);
+    dh_delta(b, blo, bhi);
+    bin_dpair(bin(i, a), alo, ahi, bin(i, b), blo, bhi, dc(i, a), dc(i, b), cnt_of(i, a),
+              cnt_of(i, b));
+  }
+};
+
+// One step of run_tile_delta8 from the ring words 0 .. 2r+7 of the entering
+// row pe and (RM) the leaving row pl.  Word j feeds H when j <= 2r, D_{j+1}
+// negatively (its left column leaves the window) when j <= 6, and D_{j-2r}
+// positively (its right column enters) when j >= 2r+1; with r >= 4 the left
+// words 0..7 all lie in H.  The words are read as 16-byte groups: groups 0
+// and 1 (the left words), the groups from M = (2r+1)/4 on (the right words:
+// with r even 2r+1 = 4M+1, so D_1..D_3 are words 1..3 of group M and
+// D_4..D_7 group M+1; with r odd 2r+1 = 4M+3, D_1 is word 3 of group M,
+// D_2..D_5 group M+1, D_6 and D_7 words 0 and 1 of group M+2), and the
+// middle groups 2 .. M-1, all H.
+template <int NT, bool ODD, bool RM>
+__device__ __forceinline__ void delta8_step(const Delta8<NT> &o, const uint32_t *pe,
+                                            const uint32_t *pl, int r) {
+  auto ld = [](const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); };
+  const int M = (2 * r + 1) >> 2;
+  const uint4 e0 = ld(pe), e1 = ld(pe + 4);
+  const uint4 t0 = ld(pe + 4 * M), t1 = ld(pe + 4 * M + 4);
+  uint4 t2 = make_uint4(0u, 0u, 0u, 0u);
+  if (ODD) t2 = ld(pe + 4 * M + 8);
+  // the right words of D_1 .. D_7 (entering row)
+  uint32_t re[8];
+  if (ODD) {
+    re[1] = t0.w; re[2] = t1.x; re[3] = t1.y; re[4] = t1.z; re[5] = t1.w; re[6] = t2.x;
+    re[7] = t2.y;
+  } else {
+    re[1] = t0.y; re[2] = t0.z; re[3] = t0.w; re[4] = t1.x; re[5] = t1.y; re[6] = t1.z;
+    re[7] = t1.w;
+  }
+  re[0] = 0u;
+  if constexpr (RM) {
+    const uint4 l0 = ld(pl), l1 = ld(pl + 4);
+    const uint4 u0 = ld(pl + 4 * M), u1 = ld(pl + 4 * M + 4);
+    uint4 u2 = make_uint4(0u, 0u, 0u, 0u);
+    if (ODD) u2 = ld(pl + 4 * M + 8);
+    // left words 0..6: H +e -l, D_{j+1} +l -e
+    o.template hd<true>(e0.x, l0.x, 1, l0.x, e0.x);
+    o.template hd<true>(e0.y, l0.y, 2, l0.y, e0.y);
+    o.template hd<true>(e0.z, l0.z, 3, l0.z, e0.z);
+    o.template hd<true>(e0.w, l0.w, 4, l0.w, e0.w);
+    o.template hd<true>(e1.x, l1.x, 5, l1.x, e1.x);
+    o.template hd<true>(e1.y, l1.y, 6, l1.y, e1.y);
+    o.template hd<true>(e1.z, l1.z, 7, l1.z, e1.z);
+    o.h(e1.w, l1.w);
+    // middle groups: H only
+#pragma unroll 2
+    for (int g = 2; g < M; ++g) {
+      const uint4 a = ld(pe + 4 * g), b = ld(pl + 4 * g);
+      o.h(a.x, b.x);
+      o.h(a.y, b.y);
+      o.h(a.z, b.z);
+      o.h(a.w, b.w);
+    }
+    // the last window words of H, each with a right D pair, then the other
+    // right D pairs
+    if (ODD) {
+      o.template hd<true>(t0.x, u0.x, 1, t0.w, u0.w);
+      o.template hd<true>(t0.y, u0.y, 2, t1.x, u1.x);
+      o.template hd<true>(t0.z, u0.z, 3, t1.y, u1.y);
+      o.d(4, t1.z, u1.z);
+      o.d(5, t1.w, u1.w);
+      o.d(6, t2.x, u2.x);
+      o.d(7, t2.y, u2.y);
+    } else {
+      o.template hd<true>(t0.x, u0.x, 1, t0.y, u0.y);
+      o.d(2, t0.z, u0.z);
+      o.d(3, t0.w, u0.w);
+      o.d(4, t1.x, u1.x);
+      o.d(5, t1.y, u1.y);
+      o.d(6, t1.z, u1.z);
+      o.d(7, t1.w, u1.w);
+    }
+  } else {
+    // filling: H +e for every window word, D_i +(right word) -(left word)
+    o.template hd<false>(e0.x, e0.y, 1, re[1], e0.x);
+    o.template hd<false>(e0.z, e0.w, 2, re[2], e0.y);
+    o.template hd<false>(e1.x, e1.y, 3, re[3], e0.z);
+    o.template hd<false>(e1.z, e1.w, 4, re[4], e0.w);
+    o.d(5, re[5], e1.x);
+    o.d(6, re[6], e1.y);
+    o.d(7, re[7], e1.z);
+#pragma unroll 2
+    for (int g = 2; g < M; ++g) {
+      const uint4 a = ld(pe + 4 * g);
+      o.h_add2(a.x, a.y);
+      o.h_add2(a.z, a.w);
+    }
+    if (ODD) {
+      o.h_add2(t0.x, t0.y);
+      o.h_add(t0.z);
+    } else {
+      o.h_add(t0.x);
+    }
+  }
+}
+
+// K = 8 output columns per thread (see above); the tile [x0, x0 + 8 NT) x
+// [y0, y1), x0 - r a multiple of 4 (tiles start at d.xshift), so every
+// thread's window starts on a 16-byte boundary of the ring.  Pixels outside
+// the image are zero words (TMA fill, and the zeroed row padding), whose
+// delta is zero.
+template <int NT>
+__device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
+                                const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
+                                uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
+                                bool tmap_global = false) {
+  using O = Delta8<NT>;
+  const int t = threadIdx.x;
+  const int r = d.r;
+  const uint32_t L = d.L;
+  const int xa = x0 + 8 * t;
+  const int xs = x0 - r;  // a multiple of 4 by the choice of d.xshift
+  const int jl = 8 * t;
+  const int E0 = y0 - r;
+  const int nsteps = (y1 - y0) + 2 * r;
+  O o;
+  o.h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
+  o.dc0 = sm.sums + L * O::kLS + static_cast<uint32_t>(t) * 4u;
+  for (uint32_t lv = 0; lv < L; ++lv) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sts_zero64(o.h0 + lv * O::kLS + static_cast<uint32_t>(i) * O::kHS);
+    sts_zero32(o.dc0 + lv * O::kDLS);
+    sts_zero32(o.dc0 + lv * O::kDLS + O::kDW);
+  }
+  const bool odd = (r & 1) != 0;
+
+  return ring_pass(
+      d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
+      y1, [&](int s, const uint32_t *rowe, const uint32_t *rowl) {
+        const bool rm = s >= 2 * r + 1;  // the leaving row was added by this tile
+        const bool out_now = s >= 2 * r;
+        const int y = E0 + s - r;
+        const uint32_t *pe = rowe + jl;
+        const uint32_t *pl = rowl + jl;
+        uint32_t alpha[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int x = xa + i;
+          alpha[i] = (out_now && d.bpp == 4 && x >= d.ox0 && x < d.ox1) ? load_alpha(d, x, y) : 0u;
+        }
+        if (odd) {
+          if (rm)
+            delta8_step<NT, true, true>(o, pe, pl, r);
+          else
+            delta8_step<NT, true, false>(o, pe, pl, r);
+        } else {
+          if (rm)
+            delta8_step<NT, false, true>(o, pe, pl, r);
+          else
+            delta8_step<NT, false, false>(o, pe, pl, r);
+        }
+        if (!out_now) return;
+        // keys (count << 22) | (31 - level): the lowest level wins ties under max
+        uint32_t best[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) best[i] = 0u;
+        for (uint32_t lv = 0; lv < L; ++lv) {
+          const uint32_t c = lds_u32(o.h0 + lv * O::kLS);  // count in bits 0..9
+          const uint32_t da = lds_u32(o.dc0 + lv * O::kDLS);
+          const uint32_t db = lds_u32(o.dc0 + lv * O::kDLS + O::kDW);
+          const uint32_t k0 = (c << 22) | (31u - lv);
+          best[0] = max(best[0], k0);
+          // byte k of pa: 128 + the count of D_1 + .. + D_{k+1}; of pb:
+          // 128 + the count of D_5 + .. + D_{k+5}
+          const uint32_t pa = da * 0x01010101u + 0x80808080u;
+          const uint32_t pb = db * 0x01010101u + 0x80808080u;
+          const uint32_t kb = k0 - (128u << 22);
+          const uint32_t k4 = kb + ((pa >> 24) << 22);
+#pragma unroll
+          for (int i = 1; i <= 3; ++i) best[i] = max(best[i], kb + (((pa >> (8 * (i - 1))) & 0xFFu) << 22));
+          best[4] = max(best[4], k4);
+          const uint32_t kb4 = k4 - (128u << 22);
+#pragma unroll
+          for (int i = 5; i <= 7; ++i) best[i] = max(best[i], kb4 + (((pb >> (8 * (i - 5))) & 0xFFu) << 22));
+        }
+        // the reciprocals first, so that their latency overlaps the loads
+        // of the winning bins
+        uint32_t mulv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) mulv[i] = rcp_of(best[i] >> 22);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int x = xa + i;
+          if (x < d.ox0 || x >= d.ox1) continue;
+          const uint32_t m = 31u - (best[i] & 31u);
+          if ((best[i] >> 22) == 0u) continue;  // no level below L (literal mode only)
+          uint64_t v = 0;
+#pragma unroll
+          for (int j = 0; j <= i; ++j) {
+            uint32_t lo, hi;
+            lds_v2(o.h0 + m * O::kLS + static_cast<uint32_t>(j) * O::kHS, lo, hi);
+            v += static_cast<uint64_t>(hi) << 32 | lo;
+          }
+          const uint32_t lo = static_cast<uint32_t>(v);
+          const uint32_t hi = static_cast<uint32_t>(v >> 32);
+          const uint32_t R = (lo >> 10) & 0x3FFFFu;
+          const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
+          const uint32_t B = hi >> 14;
+          const uint32_t mul = mulv[i];
+          store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul), __umulhi(B << 1, mul),
+                      alpha[i]);
         }
       });
 }

@@ -46,6 +46,12 @@ inline bool delta_eligible(int r, uint32_t L) {
   return r >= 0 && r <= kDeltaMaxRadius && L >= 1 && L <= kDeltaMaxLevels;
 }
 
+// Eight columns per thread: variant-A bins, and r >= 4 so that the left
+// difference words 0..6 all lie inside the window.
+inline bool delta8_eligible(int r, uint32_t L) {
+  return r >= kDelta8MinRadius && r <= kDelta8MaxRadius && L >= 1 && L <= kDeltaMaxLevels;
+}
+
 // Box width (words) of a difference-histogram tile: thread t reads K-word
 // groups from ring index K*t up to the group holding word 2r+K-1.
 inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
@@ -84,7 +90,10 @@ inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, u
     g.xshift = (r & 3) ? (r & 3) - 4 : 0;
     g.boxw = (g.tile_w + 2u * static_cast<uint32_t>(r) + 3u) & ~3u;
   } else {
-    g.kcols = (kcols_wanted > 1 && delta_eligible(r, L)) ? kcols_wanted : 1;
+    g.kcols = (kcols_wanted == 8 ? delta8_eligible(r, L)
+                                 : (kcols_wanted > 1 && delta_eligible(r, L)))
+                  ? kcols_wanted
+                  : 1;
     g.tile_w = nt * static_cast<uint32_t>(g.kcols);
     if (g.kcols > 1) {
       // first tile at x0 = xshift with x0 - r a multiple of 4
@@ -124,9 +133,11 @@ inline int pack_grid_for(uint32_t rows, int sms) {
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
 // per thread, bins of the variant's size; 2 or 4: kcols histograms, one
 // more where the window histogram is split, of L levels per thread, bins of
-// 8 bytes (variant A) or 8 + 4 bytes (variant B)).
+// 8 bytes (variant A) or 8 + 2 bytes (variant B); 8: eight histograms of
+// 8-byte bins and two count words per level and thread).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
   // (column path: cols_hist_bytes)
+  if (kcols == 8) return static_cast<size_t>(8u * 8u + 8u) * L * nt;
   if (kcols > 1) {
     const size_t nh = static_cast<size_t>(kcols) + static_cast<size_t>(hsplit(kcols, variant)) - 1u;
     // variant B: 8-byte sums and a 16-bit count per bin

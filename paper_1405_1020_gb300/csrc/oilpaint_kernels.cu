@@ -8,7 +8,8 @@
 //                                           column per thread (NT threads)
 //   tile_delta_kernel<NT, K, VAR>           one CTA per output tile, K output
 //                                           columns per thread through
-//                                           difference histograms
+//                                           difference histograms (K = 8:
+//                                           run_tile_delta8, variant A)
 //   tile_cols_kernel<NW, TWK, VAR>          one CTA per output tile, column
 //                                           histograms swept by NW warps
 //   persistent_kernel<NT, K>                grid-sized CTAs pulling
@@ -84,7 +85,10 @@ __global__ void __launch_bounds__(NT, 1)
   const int x0 = d.xshift + static_cast<int>(blockIdx.x) * NT * K;
   const int y0 = d.oy0 + static_cast<int>(blockIdx.y * d.tile_h);
   const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
-  run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+  if constexpr (K == 8)
+    run_tile_delta8<NT>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+  else
+    run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
 template <int NW, int TWK, int VAR>
@@ -206,7 +210,10 @@ template <int NT>
 static void delta_n(int k, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
                     dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
   const bool a = d.variant == static_cast<uint32_t>(kVarA);
-  if (k == 4) {
+  if (k == 8) {  // variant A, 32 or 64 threads (checked by the host)
+    if constexpr (NT <= 64)
+      if (a) tile_delta_kernel<NT, 8, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
+  } else if (k == 4) {
     if (a)
       tile_delta_kernel<NT, 4, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
     else
@@ -250,7 +257,8 @@ cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
     }
     return cudaGetLastError();
   }
-  if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
+  if (kcols != 1 && kcols != 2 && kcols != 4 && kcols != 8) return cudaErrorInvalidValue;
+  if (kcols == 8 && (nt > 64 || variant != kVarA)) return cudaErrorInvalidValue;
   switch (nt) {
     case 32:
       kcols == 1 ? plain_n<32>(variant, d, map, rc, grid, smem, err, timeout_ns, s)
@@ -347,6 +355,8 @@ static cudaError_t set_limit_n(int b) {
   if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kVarA>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 2, kVarB>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kVarB>, a, b)) != cudaSuccess) return e;
+  if constexpr (NT <= 64)
+    if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 8, kVarA>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 1>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 2>, a, b)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(persistent_kernel<NT, 4>, a, b);
@@ -386,6 +396,11 @@ static int occupancy_n(bool persistent, int kcols, int variant, size_t smem) {
     if (kcols == 4) return occ_of(persistent_kernel<NT, 4>, NT, smem);
     if (kcols == 2) return occ_of(persistent_kernel<NT, 2>, NT, smem);
     return occ_of(persistent_kernel<NT, 1>, NT, smem);
+  }
+  if (kcols == 8) {
+    if constexpr (NT <= 64)
+      if (variant == kVarA) return occ_of(tile_delta_kernel<NT, 8, kVarA>, NT, smem);
+    return 0;
   }
   if (kcols == 4)
     return variant == kVarA ? occ_of(tile_delta_kernel<NT, 4, kVarA>, NT, smem)

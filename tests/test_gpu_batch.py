@@ -284,8 +284,9 @@ def test_batch_tune_table_entry_is_used_where_it_fits():
     batch tuning table when the entry fits the group's largest image in one
     CTA, and falls back to another configuration when it does not."""
     want = {"tile_w": 64, "chunk_rows": 4, "prefetch": 1, "cols_per_thread": 1}
-    # 4 columns of 128 threads at r = 44: the halo box is wider than 256 columns
-    wide = {"tile_w": 512, "chunk_rows": 2, "prefetch": 1, "cols_per_thread": 4}
+    # 4 columns of 128 threads at r = 44 with 32-row halo chunks, 4 in flight:
+    # the ring of halo copies alone exceeds a CTA's shared memory
+    wide = {"tile_w": 512, "chunk_rows": 32, "prefetch": 4, "cols_per_thread": 4}
     try:
         B.check(B.op_batch_tune_table_set(15, 20, B.op_config_t.make(**want)), "set")
         b = Batch(4, 100000, 20, 20)

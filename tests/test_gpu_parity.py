@@ -162,8 +162,8 @@ def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
     try:
         check_case(img, r, L, bpp, pad, mode, cfg)
     except B.OilPaintError as e:
-        # refused only when the halo box is wider than 256 columns or the
-        # ring of halo copies plus K histograms exceeds a CTA's shared memory
+        # refused only when the ring of halo copies plus the K histograms
+        # exceeds a CTA's shared memory (an upper estimate of it here)
         assert e.status == B.OP_E_UNSUPPORTED, e
         K, nt = cfg["cols_per_thread"], cfg["tile_w"] // cfg["cols_per_thread"]
         ng = (2 * r + K - 1) // K + 1
@@ -173,7 +173,71 @@ def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
         hist = (nh * L + 1) * nt * (8 if r <= 15 else 12)
         slots = cfg["prefetch"] + 1
         smem = 128 + -(-slots * 8 // 128) * 128 + 2 * half * slots + hist
-        assert boxw > 256 or smem > 226 * 1024, (cfg, r, L, smem)
+        assert smem > 226 * 1024, (cfg, r, L, smem)
+
+
+def _delta8_cases(n=64, seed=17):
+    """Eight columns per thread (4 <= r <= 15, L <= 32): both r parities (the
+    right difference words start at word 1 or 3 of a 16-byte group), widths
+    around the 256- and 512-column tiles, one-row and short images, both
+    level modes and literal mode, tile heights, halo chunk heights and
+    prefetch depths."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n):
+        w = int(rng.choice([1, 3, 8, 9, 31, 200, 255, 256, 257, 263, 500, 511, 512, 513, 700, 1030]))
+        h = int(rng.choice([1, 2, 5, 16, 33, 90, 161]))
+        r = int(rng.integers(4, 16))
+        L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32]))
+        bpp = int(rng.choice([3, 4]))
+        pad = int(rng.choice([0, 1, 4, 13]))
+        mode = int(rng.choice([0, 1, B.OP_LITERAL, B.OP_LITERAL | 1]))
+        nt = int(rng.choice([32, 64]))
+        cfg = {"tile_w": nt * 8, "tile_h": int(rng.choice([0, 1, 3, 16, 64])),
+               "chunk_rows": int(rng.choice([1, 2, 3, 8])), "prefetch": int(rng.integers(1, 3)),
+               "cols_per_thread": 8}
+        cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
+    return cases
+
+
+@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _delta8_cases())
+def test_fuzz_eight_columns(k, w, h, r, L, bpp, pad, mode, cfg):
+    img = synth.camera_like(h, w, seed=1700 + k, npoly=12, rad_range=(1, 60)) if k % 2 else \
+        synth.uniform_rgb(h, w, seed=1700 + k)
+    if k % 3 == 0:  # runs of white pixels (level L - 1, or level L in literal mode)
+        img[np.random.default_rng(k).random((h, w)) < 0.2] = 255
+    try:
+        check_case(img, r, L, bpp, pad, mode, cfg)
+    except B.OilPaintError as e:
+        # refused only when the halo ring plus the histograms (eight of 8-byte
+        # bins and two count words per level and thread) exceed a CTA's
+        # shared memory
+        assert e.status == B.OP_E_UNSUPPORTED, e
+        nt = cfg["tile_w"] // 8
+        boxw = 8 * (nt - 1 + (2 * r + 7) // 8 + 1)
+        half = -(-boxw * cfg["chunk_rows"] * 4 // 128) * 128
+        slots = cfg["prefetch"] + 1
+        smem = 128 + -(-slots * 8 // 128) * 128 + 2 * half * slots + 72 * L * nt
+        assert smem > 226 * 1024, (cfg, r, L, smem)
+
+
+@pytest.mark.parametrize("r", list(range(4, 16)))
+def test_eight_columns_every_radius(r):
+    """Every radius the eight-column path takes, 32 and 64 threads, RGB and
+    RGBA, on an image whose width is not a tile multiple."""
+    img = synth.camera_like(97, 601, seed=40 + r, npoly=30, rad_range=(3, 150))
+    for nt, bpp, pad, ch in ((32, 4, 0, 2), (64, 3, 5, 1)):
+        check_case(img, r, 20, bpp=bpp, pad=pad,
+                   config={"tile_w": 8 * nt, "cols_per_thread": 8, "chunk_rows": ch})
+
+
+@pytest.mark.parametrize("r,L", [(3, 20), (16, 20), (15, 33), (0, 1)])
+def test_eight_columns_refused_outside_its_range(r, L):
+    op = OilPaint(300, 40, r, L)
+    with pytest.raises(B.OilPaintError) as e:
+        op.set_config({"tile_w": 256, "cols_per_thread": 8})
+    assert e.value.status == B.OP_E_UNSUPPORTED
+    op.close()
 
 
 def _column_path_cases(n=48, seed=13):
@@ -253,9 +317,11 @@ def test_every_config_gives_the_same_bytes():
     h, w = img.shape[:2]
     buf, stride = synth.to_strided(img, bpp=3, stride=w * 3 + 2)
     want = cpu_filter(buf, w, h, stride, 3, 9, 20)
-    ran = 0
+    ran = ran8 = 0
     for nt in (32, 64, 96, 128):
-        for cpt in (1, 2, 4):
+        for cpt in (1, 2, 4, 8):
+            if cpt == 8 and nt > 64:
+                continue
             for ch in (1, 4, 8, 16):
                 for pf in (1, 2, 4):
                     for th in (0, 1, 23, 233):
@@ -264,13 +330,17 @@ def test_every_config_gives_the_same_bytes():
                         try:
                             got = gpu_filter(buf, w, h, stride, 3, 9, 20, config=cfg)
                         except B.OilPaintError as e:
-                            # halo wider than one TMA box
+                            # the ring of halo copies does not fit shared memory
                             assert e.status == B.OP_E_UNSUPPORTED, e
+                            assert ch * pf >= 16, cfg
                             continue
                         assert_same(got, want, w, h, stride, 3, str(cfg))
                         ran += 1
-    # r = 9: boxes of 32..96 threads x 1, 32..96 x 2 and 32 x 4 columns fit
-    assert ran == (4 + 3 + 1) * 4 * 3 * 4
+                        ran8 += cpt == 8
+    # every one-column configuration (4 x 4 x 3 x 4) and every configuration
+    # whose halo ring is small -- chunk rows x prefetch < 16: 6 of the 12
+    # pairs -- runs (10 thread and column combinations of 2, 4 or 8 columns)
+    assert ran >= 4 * 4 * 3 * 4 + 10 * 6 * 4 and ran8 >= 2 * 6 * 4
 
 
 @pytest.mark.parametrize("cpt", [1, 2, 4])
@@ -309,17 +379,17 @@ def test_border_threads_several_columns(w, h, r, L):
         check_case(img, r, L, bpp=3, config={"tile_w": k * nt, "cols_per_thread": k})
 
 
-def test_tile_w_256_only_without_halo():
-    op = OilPaint(300, 20, 0, 20)
-    op.set_config({"tile_w": 256, "cols_per_thread": 2})  # r = 0: the 256-word box fits
-    op.close()
-    op = OilPaint(300, 20, 1, 20)
-    with pytest.raises(B.OilPaintError) as e:
-        op.set_config({"tile_w": 256, "cols_per_thread": 2})
-    assert e.value.status == B.OP_E_UNSUPPORTED
-    op.close()
-    check_case(synth.uniform_rgb(40, 600, seed=3), 0, 20,
-               config={"tile_w": 256, "cols_per_thread": 2})
+def test_wide_halo_boxes():
+    """Halo rows wider than the 256 elements of a TMA box dimension are copied
+    through the three-dimensional view of the packed image (the padding words
+    at the end of each packed row read as zero)."""
+    for w, r, cfg in ((300, 1, {"tile_w": 256, "cols_per_thread": 2}),
+                      (601, 15, {"tile_w": 512, "cols_per_thread": 4, "chunk_rows": 1}),
+                      (1029, 13, {"tile_w": 512, "cols_per_thread": 8, "chunk_rows": 2}),
+                      (333, 20, {"tile_w": 512, "cols_per_thread": 4, "chunk_rows": 1})):
+        check_case(synth.camera_like(40, w, seed=w, npoly=20, rad_range=(2, 80)), r, 20,
+                   config=cfg, what=f"{w} wide, r={r}, {cfg}")
+        check_case(synth.uniform_rgb(23, w, seed=w), r, 20, bpp=4, pad=12, config=cfg)
 
 
 def test_run_host_matches_oracle():
