@@ -1642,313 +1642,365 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
 // ------------------------------------------------ eight columns per thread
 //
 // K = 8 output columns per thread (run_tile_delta8): variant-A bins and word
-// format 1, 4 <= r <= 15, L <= 32.  As in run_tile_delta, thread t owns
-// columns xa .. xa+7 (xa = x0 + 8t) and keeps H, the histogram of the window
-// of column xa, and D_1 .. D_7, the histograms of column xa+i+r minus column
-// xa+i-1-r: 2(2r+1) + 28 bin updates per 8 outputs (11.25 per output at
-// r = 15, against 18.5 with four columns).  With eight windows the argmax
-// would read eight count words per level, so the counts of D_1 .. D_7 are
-// kept a second time, as signed bytes packed into two words per level and
-// thread (DC: D_1..D_4 at bits 8(i-1) of word 0, D_5..D_7 at bits 8(i-5) of
-// word 1; a pixel adds its valid bit there, so the zero words outside the
-// image count nothing), and a level costs three loads: H's low word and the
-// two DC words.
-// A D_i count lies in [-31, 31] (two columns of at most 31 pixels), so the
-// prefix sums of the bytes of one word lie in [-124, 124]: multiplying the
-// word by 0x01010101 replaces each byte by the sum of the bytes up to it (the
-// word is linear in its signed bytes mod 2^32), and adding 0x80808080 then
-// maps every prefix to an unsigned byte with no carry between bytes.
+// format 1, 4 <= r <= 15, L <= 32, the radius a template parameter so that a
+// step is straight-line code.  Thread t owns columns xa .. xa+7 (xa = x0 + 8t)
+// and keeps the histogram of the window of column xa, split by the parity of
+// the window column into He and Ho (two independent update chains), and
+// D_1 .. D_7, the histograms of column xa+i+r minus column xa+i-1-r:
+// 2(2r+1) + 28 bin updates per 8 outputs (11.25 per output at r = 15,
+// against 18.5 with four columns).  With eight windows the argmax would read
+// nine count words per level, so the counts of D_1 .. D_7 are kept a second
+// time, as signed bytes packed into two words per level and thread (DC:
+// D_1..D_4 at bits 8(i-1) of word 0, D_5..D_7 at bits 8(i-5) of word 1; a
+// pixel adds its valid bit there, so the zero words outside the image count
+// nothing), and a level costs four loads: the low words of He and Ho and the
+// two DC words.  A D_i count lies in [-31, 31] (two columns of at most 31
+// pixels), so the prefix sums of the bytes of one word lie in [-124, 124]:
+// multiplying the word by 0x01010101 replaces each byte by the sum of the
+// bytes up to it (the word is linear in its signed bytes mod 2^32), and
+// adding 0x80808080 then maps every prefix to an unsigned byte with no carry
+// between bytes.
 //
-// Shared memory (after the ring): 64-bit bins [level][histogram 0..7][thread]
-// (H is histogram 0, D_i histogram i), then the DC words [level][word][thread].
+// The updates are issued in blocks of up to three bin pairs (one on He, one
+// on Ho, one on a D_i with its pair of DC words), all loads first.  The two
+// bins of a pair may coincide; the second's delta then includes the first's
+// (decided from the addresses alone, before the loads), so that the second
+// store, which lands last, holds both updates and no bin's load-add-store
+// chain waits on another's.
+//
+// Shared memory (after the ring): 64-bit bins [level][histogram][thread],
+// histograms He, Ho, D_1..D_7 numbered 0..8, then the DC words
+// [level][word][thread].
 
-#define OPK_BLK_HD_HEAD                                                     \
-  "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1, e, f;\n\t.reg .pred p, q;\n\t" \
-  "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"                                    \
-  "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"                                    \
-  "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"                                    \
-  "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"                                    \
-  "ld.shared.u32 e, [%12];\n\t"                                             \
-  "ld.shared.u32 f, [%13];\n\t"                                             \
-  "add.cc.u32 a0, a0, %1;\n\t"                                              \
-  "addc.u32 a1, a1, %2;\n\t"                                                \
-  "add.cc.u32 c0, c0, %7;\n\t"                                              \
-  "addc.u32 c1, c1, %8;\n\t"                                                \
-  "add.u32 e, e, %14;\n\t"                                                  \
-  "setp.eq.u32 p, %0, %3;\n\t"                                              \
-  "setp.eq.u32 q, %6, %9;\n\t"                                              \
-  "selp.b32 b0, a0, b0, p;\n\t"                                             \
-  "selp.b32 b1, a1, b1, p;\n\t"                                             \
-  "selp.b32 d0, c0, d0, q;\n\t"                                             \
-  "selp.b32 d1, c1, d1, q;\n\t"                                             \
-  "selp.b32 f, e, f, q;\n\t"
-#define OPK_BLK_HD_TAIL                                                     \
-  "sub.cc.u32 d0, d0, %10;\n\t"                                             \
-  "subc.u32 d1, d1, %11;\n\t"                                               \
-  "sub.u32 f, f, %15;\n\t"                                                  \
-  "st.shared.v2.u32 [%0], {a0, a1};\n\t"                                    \
-  "st.shared.v2.u32 [%3], {b0, b1};\n\t"                                    \
-  "st.shared.v2.u32 [%6], {c0, c1};\n\t"                                    \
-  "st.shared.v2.u32 [%9], {d0, d1};\n\t"                                    \
-  "st.shared.u32 [%12], e;\n\t"                                             \
-  "st.shared.u32 [%13], f;\n\t}"
+constexpr int kD8Hists = 9;
 
-// +(alo, ahi) at A, then -(blo, bhi) (SUB) or +(blo, bhi) at B, on one
-// histogram (A may equal B); with it +(clo, chi) at C and -(dlo, dhi) at D
-// on a second histogram and +sc at count word E, -sd at F, where E == F
-// exactly when C == D.  All six loads are issued first.
+// A 64-bit bin update (shared address, delta) and a 32-bit one.
+struct Upd64 {
+  uint32_t a, lo, hi;
+};
+struct Upd32 {
+  uint32_t a, v;
+};
+
+#define OPK_LD64(r, a) "ld.shared.v2.u32 {" r "0, " r "1}, [" a "];\n\t"
+#define OPK_ST64(r, a) "st.shared.v2.u32 [" a "], {" r "0, " r "1};\n\t"
+#define OPK_ADD64(r, lo, hi) \
+  "add.cc.u32 " r "0, " r "0, " lo ";\n\taddc.u32 " r "1, " r "1, " hi ";\n\t"
+#define OPK_SUB64(r, lo, hi) \
+  "sub.cc.u32 " r "0, " r "0, " lo ";\n\tsubc.u32 " r "1, " r "1, " hi ";\n\t"
+
+// Pairs (A, B) on He, (C, D) on Ho and (E, F) on a D_i with its count words
+// (G, H): A, C, E, G add; B and D subtract (SUB) or add; F and H subtract.
 template <bool SUB>
-__device__ __forceinline__ void bin_pair_dpair(uint32_t A, uint32_t alo, uint32_t ahi, uint32_t B,
-                                               uint32_t blo, uint32_t bhi, uint32_t C,
-                                               uint32_t clo, uint32_t chi, uint32_t D,
-                                               uint32_t dlo, uint32_t dhi, uint32_t E, uint32_t F,
-                                               uint32_t sc, uint32_t sd) {
-  if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u) ||
-      !OPK_SMEM_OK(E, 4u) || !OPK_SMEM_OK(F, 4u))
+__device__ __forceinline__ void blk_hhd(const Upd64 &A, const Upd64 &B, const Upd64 &C,
+                                        const Upd64 &D, const Upd64 &E, const Upd64 &F,
+                                        const Upd32 &G, const Upd32 &H) {
+  if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u) || !OPK_SMEM_OK(C.a, 8u) ||
+      !OPK_SMEM_OK(D.a, 8u) || !OPK_SMEM_OK(E.a, 8u) || !OPK_SMEM_OK(F.a, 8u) ||
+      !OPK_SMEM_OK(G.a, 4u) || !OPK_SMEM_OK(H.a, 4u))
     return;
-  if constexpr (SUB) {
-    asm volatile(OPK_BLK_HD_HEAD
-                 "sub.cc.u32 b0, b0, %4;\n\t"
-                 "subc.u32 b1, b1, %5;\n\t" OPK_BLK_HD_TAIL ::"r"(A),
-                 "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi),
-                 "r"(D), "r"(dlo), "r"(dhi), "r"(E), "r"(F), "r"(sc), "r"(sd));
-  } else {
-    asm volatile(OPK_BLK_HD_HEAD
-                 "add.cc.u32 b0, b0, %4;\n\t"
-                 "addc.u32 b1, b1, %5;\n\t" OPK_BLK_HD_TAIL ::"r"(A),
-                 "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi),
-                 "r"(D), "r"(dlo), "r"(dhi), "r"(E), "r"(F), "r"(sc), "r"(sd));
-  }
-}
-#undef OPK_BLK_HD_HEAD
-#undef OPK_BLK_HD_TAIL
-
-// +(clo, chi) at C, -(dlo, dhi) at D (one histogram, C may equal D), +sc
-// at count word E, -sd at F (E == F exactly when C == D): four loads first.
-__device__ __forceinline__ void bin_dpair(uint32_t C, uint32_t clo, uint32_t chi, uint32_t D,
-                                          uint32_t dlo, uint32_t dhi, uint32_t E, uint32_t F,
-                                          uint32_t sc, uint32_t sd) {
-  if (!OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u) || !OPK_SMEM_OK(E, 4u) || !OPK_SMEM_OK(F, 4u))
-    return;
-  asm volatile(
-      "{\n\t.reg .u32 c0, c1, d0, d1, e, f;\n\t.reg .pred q;\n\t"
-      "ld.shared.v2.u32 {c0, c1}, [%0];\n\t"
-      "ld.shared.v2.u32 {d0, d1}, [%3];\n\t"
-      "ld.shared.u32 e, [%6];\n\t"
-      "ld.shared.u32 f, [%7];\n\t"
-      "add.cc.u32 c0, c0, %1;\n\t"
-      "addc.u32 c1, c1, %2;\n\t"
-      "add.u32 e, e, %8;\n\t"
-      "setp.eq.u32 q, %0, %3;\n\t"
-      "selp.b32 d0, c0, d0, q;\n\t"
-      "selp.b32 d1, c1, d1, q;\n\t"
-      "selp.b32 f, e, f, q;\n\t"
-      "sub.cc.u32 d0, d0, %4;\n\t"
-      "subc.u32 d1, d1, %5;\n\t"
-      "sub.u32 f, f, %9;\n\t"
-      "st.shared.v2.u32 [%0], {c0, c1};\n\t"
-      "st.shared.v2.u32 [%3], {d0, d1};\n\t"
-      "st.shared.u32 [%6], e;\n\t"
-      "st.shared.u32 [%7], f;\n\t}" ::"r"(C),
-      "r"(clo), "r"(chi), "r"(D), "r"(dlo), "r"(dhi), "r"(E), "r"(F), "r"(sc), "r"(sd));
+#define OPK_HHD_BODY(OPB, OPD)                                                                 \
+  "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1, e0, e1, f0, f1, g, h;\n\t" OPK_LD64(         \
+      "a", "%0") OPK_LD64("b", "%3") OPK_LD64("c", "%6") OPK_LD64("d", "%9")                   \
+      OPK_LD64("e", "%12") OPK_LD64("f", "%15") "ld.shared.u32 g, [%18];\n\t"                  \
+      "ld.shared.u32 h, [%20];\n\t" OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5")            \
+      OPK_ADD64("c", "%7", "%8") OPD("d", "%10", "%11") OPK_ADD64("e", "%13", "%14")           \
+      OPK_SUB64("f", "%16", "%17") "add.u32 g, g, %19;\n\tsub.u32 h, h, %21;\n\t"              \
+      OPK_ST64("a", "%0") OPK_ST64("b", "%3") OPK_ST64("c", "%6") OPK_ST64("d", "%9")          \
+      OPK_ST64("e", "%12") OPK_ST64("f", "%15") "st.shared.u32 [%18], g;\n\t"                  \
+      "st.shared.u32 [%20], h;\n\t}"
+#define OPK_HHD_ARGS                                                                           \
+  "r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo), "r"(B.hi), "r"(C.a), "r"(C.lo),        \
+      "r"(C.hi), "r"(D.a), "r"(D.lo), "r"(D.hi), "r"(E.a), "r"(E.lo), "r"(E.hi), "r"(F.a),     \
+      "r"(F.lo), "r"(F.hi), "r"(G.a), "r"(G.v), "r"(H.a), "r"(H.v)
+  if constexpr (SUB)
+    asm volatile(OPK_HHD_BODY(OPK_SUB64, OPK_SUB64)::OPK_HHD_ARGS);
+  else
+    asm volatile(OPK_HHD_BODY(OPK_ADD64, OPK_ADD64)::OPK_HHD_ARGS);
+#undef OPK_HHD_BODY
+#undef OPK_HHD_ARGS
 }
 
-// Addresses of one thread's K = 8 histograms and count words.
+// Pairs (A, B) and (C, D) on two histograms.
+template <bool SUB>
+__device__ __forceinline__ void blk_hh(const Upd64 &A, const Upd64 &B, const Upd64 &C,
+                                       const Upd64 &D) {
+  if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u) || !OPK_SMEM_OK(C.a, 8u) ||
+      !OPK_SMEM_OK(D.a, 8u))
+    return;
+#define OPK_HH_BODY(OPB)                                                                       \
+  "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t" OPK_LD64("a", "%0") OPK_LD64("b", "%3") \
+      OPK_LD64("c", "%6") OPK_LD64("d", "%9") OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5")  \
+      OPK_ADD64("c", "%7", "%8") OPB("d", "%10", "%11") OPK_ST64("a", "%0")                    \
+      OPK_ST64("b", "%3") OPK_ST64("c", "%6") OPK_ST64("d", "%9") "}"
+#define OPK_HH_ARGS                                                                            \
+  "r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo), "r"(B.hi), "r"(C.a), "r"(C.lo),        \
+      "r"(C.hi), "r"(D.a), "r"(D.lo), "r"(D.hi)
+  if constexpr (SUB)
+    asm volatile(OPK_HH_BODY(OPK_SUB64)::OPK_HH_ARGS);
+  else
+    asm volatile(OPK_HH_BODY(OPK_ADD64)::OPK_HH_ARGS);
+#undef OPK_HH_BODY
+#undef OPK_HH_ARGS
+}
+
+// Pair (A, B) on He or Ho, pair (E, F) on a D_i with its count words (G, H).
+template <bool SUB>
+__device__ __forceinline__ void blk_hd(const Upd64 &A, const Upd64 &B, const Upd64 &E,
+                                       const Upd64 &F, const Upd32 &G, const Upd32 &H) {
+  if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u) || !OPK_SMEM_OK(E.a, 8u) ||
+      !OPK_SMEM_OK(F.a, 8u) || !OPK_SMEM_OK(G.a, 4u) || !OPK_SMEM_OK(H.a, 4u))
+    return;
+#define OPK_HD_BODY(OPB)                                                                       \
+  "{\n\t.reg .u32 a0, a1, b0, b1, e0, e1, f0, f1, g, h;\n\t" OPK_LD64("a", "%0")               \
+      OPK_LD64("b", "%3") OPK_LD64("e", "%6") OPK_LD64("f", "%9") "ld.shared.u32 g, [%12];\n\t" \
+      "ld.shared.u32 h, [%14];\n\t" OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5")            \
+      OPK_ADD64("e", "%7", "%8") OPK_SUB64("f", "%10", "%11")                                  \
+      "add.u32 g, g, %13;\n\tsub.u32 h, h, %15;\n\t" OPK_ST64("a", "%0") OPK_ST64("b", "%3")   \
+      OPK_ST64("e", "%6") OPK_ST64("f", "%9") "st.shared.u32 [%12], g;\n\t"                    \
+      "st.shared.u32 [%14], h;\n\t}"
+#define OPK_HD_ARGS                                                                            \
+  "r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo), "r"(B.hi), "r"(E.a), "r"(E.lo),        \
+      "r"(E.hi), "r"(F.a), "r"(F.lo), "r"(F.hi), "r"(G.a), "r"(G.v), "r"(H.a), "r"(H.v)
+  if constexpr (SUB)
+    asm volatile(OPK_HD_BODY(OPK_SUB64)::OPK_HD_ARGS);
+  else
+    asm volatile(OPK_HD_BODY(OPK_ADD64)::OPK_HD_ARGS);
+#undef OPK_HD_BODY
+#undef OPK_HD_ARGS
+}
+
+// Pair (A, B) on one histogram.
+template <bool SUB>
+__device__ __forceinline__ void blk_h(const Upd64 &A, const Upd64 &B) {
+  if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u)) return;
+#define OPK_H_BODY(OPB)                                                                        \
+  "{\n\t.reg .u32 a0, a1, b0, b1;\n\t" OPK_LD64("a", "%0") OPK_LD64("b", "%3")                 \
+      OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5") OPK_ST64("a", "%0") OPK_ST64("b", "%3") "}"
+  if constexpr (SUB)
+    asm volatile(OPK_H_BODY(OPK_SUB64)::"r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo),
+                 "r"(B.hi));
+  else
+    asm volatile(OPK_H_BODY(OPK_ADD64)::"r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo),
+                 "r"(B.hi));
+#undef OPK_H_BODY
+}
+
+// Pair (E, F) on a D_i (E adds, F subtracts) with its count words (G, H).
+__device__ __forceinline__ void blk_d(const Upd64 &E, const Upd64 &F, const Upd32 &G,
+                                      const Upd32 &H) {
+  if (!OPK_SMEM_OK(E.a, 8u) || !OPK_SMEM_OK(F.a, 8u) || !OPK_SMEM_OK(G.a, 4u) ||
+      !OPK_SMEM_OK(H.a, 4u))
+    return;
+  asm volatile("{\n\t.reg .u32 e0, e1, f0, f1, g, h;\n\t" OPK_LD64("e", "%0") OPK_LD64("f", "%3")
+               "ld.shared.u32 g, [%6];\n\t"
+               "ld.shared.u32 h, [%8];\n\t" OPK_ADD64("e", "%1", "%2") OPK_SUB64("f", "%4", "%5")
+               "add.u32 g, g, %7;\n\tsub.u32 h, h, %9;\n\t" OPK_ST64("e", "%0") OPK_ST64("f", "%3")
+               "st.shared.u32 [%6], g;\n\t"
+               "st.shared.u32 [%8], h;\n\t}" ::"r"(E.a),
+               "r"(E.lo), "r"(E.hi), "r"(F.a), "r"(F.lo), "r"(F.hi), "r"(G.a), "r"(G.v), "r"(H.a),
+               "r"(H.v));
+}
+#undef OPK_LD64
+#undef OPK_ST64
+#undef OPK_ADD64
+#undef OPK_SUB64
+
+// One thread's K = 8 histograms and count words, and the updates of one
+// packed word (word format 1; the level field at bits 1..5, so w & 0x3E is
+// twice the level).
 template <int NT>
 struct Delta8 {
-  static constexpr uint32_t kHS = NT * 8u;    // between histograms
-  static constexpr uint32_t kLS = 8u * kHS;   // between levels (bins)
-  static constexpr uint32_t kDLS = NT * 8u;   // between levels (DC words: two per thread)
-  static constexpr uint32_t kDW = NT * 4u;    // between a level's two DC words
-  uint32_t h0;   // H's level-0 bin of this thread
+  static constexpr uint32_t kHS = NT * 8u;                   // between histograms
+  static constexpr uint32_t kLS = kD8Hists * kHS;            // between levels (bins)
+  static constexpr uint32_t kDLS = NT * 8u;                  // between levels (DC words)
+  static constexpr uint32_t kDW = NT * 4u;                   // between a level's two DC words
+  uint32_t h0;   // He's level-0 bin of this thread
   uint32_t dc0;  // this thread's first DC word of level 0
 
-  // bin of word w's level in histogram i (level field at bits 1..5: w & 0x3E
-  // is twice the level)
-  __device__ __forceinline__ uint32_t bin(int i, uint32_t w) const {
-    return h0 + static_cast<uint32_t>(i) * kHS + (w & 0x3Eu) * (kLS / 2u);
+  // +w in histogram k (0 He, 1 Ho, 1 + i D_i)
+  __device__ __forceinline__ Upd64 add(int k, uint32_t w) const {
+    uint32_t lo, hi;
+    dh_delta(w, lo, hi);
+    return Upd64{h0 + static_cast<uint32_t>(k) * kHS + (w & 0x3Eu) * (kLS / 2u), lo, hi};
   }
-  // DC word holding D_i's count at word w's level
-  __device__ __forceinline__ uint32_t dc(int i, uint32_t w) const {
-    return dc0 + static_cast<uint32_t>((i - 1) >> 2) * kDW + (w & 0x3Eu) * (kDLS / 2u);
-  }
-  // D_i's count delta of word w in its DC word: the valid bit (bit 0: 1 for
-  // an image pixel, 0 for the zero words outside the image) moved to D_i's byte
-  static __device__ __forceinline__ uint32_t cnt_of(int i, uint32_t w) {
-    return (w & 1u) << (8 * ((i - 1) & 3));
-  }
-  // H: +e -l (or, filling, +e +l); D_i: +a -b
+  // the second update of a pair whose first is `first`, of word w in
+  // histogram k, to be subtracted (SUB) or added; when both land on one bin
+  // it also carries the first's delta
   template <bool SUB>
-  __device__ __forceinline__ void hd(uint32_t e, uint32_t l, int i, uint32_t a, uint32_t b) const {
-    uint32_t elo, ehi, llo, lhi, alo, ahi, blo, bhi;
-    dh_delta(e, elo, ehi);
-    dh_delta(l, llo, lhi);
-    dh_delta(a, alo, ahi);
-    dh_delta(b, blo, bhi);
-    bin_pair_dpair<SUB>(bin(0, e), elo, ehi, bin(0, l), llo, lhi, bin(i, a), alo, ahi, bin(i, b),
-                        blo, bhi, dc(i, a), dc(i, b), cnt_of(i, a), cnt_of(i, b));
+  __device__ __forceinline__ Upd64 second(const Upd64 &first, int k, uint32_t w) const {
+    const Upd64 u = add(k, w);
+    const uint64_t d1 = static_cast<uint64_t>(first.hi) << 32 | first.lo;
+    const uint64_t d = static_cast<uint64_t>(u.hi) << 32 | u.lo;
+    const uint64_t x = u.a == first.a ? d1 : 0ull;
+    const uint64_t e = SUB ? d - x : d + x;
+    return Upd64{u.a, static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32)};
   }
-  // H: +e -l
-  __device__ __forceinline__ void h(uint32_t e, uint32_t l) const {
-    uint32_t elo, ehi, llo, lhi;
-    dh_delta(e, elo, ehi);
-    dh_delta(l, llo, lhi);
-    bin_addsub64_chain(bin(0, e), elo, ehi, bin(0, l), llo, lhi);
+  // D_i's count word at word w's level and the word's valid bit moved to
+  // D_i's byte
+  __device__ __forceinline__ Upd32 cnt(int i, uint32_t w) const {
+    return Upd32{dc0 + static_cast<uint32_t>((i - 1) >> 2) * kDW + (w & 0x3Eu) * (kDLS / 2u),
+                 (w & 1u) << (8 * ((i - 1) & 3))};
   }
-  // H: +a +b
-  __device__ __forceinline__ void h_add2(uint32_t a, uint32_t b) const {
-    uint32_t alo, ahi, blo, bhi;
-    dh_delta(a, alo, ahi);
-    dh_delta(b, blo, bhi);
-    bin_add64x2_chain(bin(0, a), alo, ahi, bin(0, b), blo, bhi);
-  }
-  // H: +a
-  __device__ __forceinline__ void h_add(uint32_t a) const {
-    uint32_t alo, ahi;
-    dh_delta(a, alo, ahi);
-    bin_add64(bin(0, a), alo, ahi);
-  }
-  // D_i: +a -b
-  __device__ __forceinline__ void d(int i, uint32_t a, uint32_t b) const {
-    uint32_t alo, ahi, blo, bhi;
-    dh_delta(a, alo, ahi);
-    dh_delta(b, blo, bhi);
-    bin_dpair(bin(i, a), alo, ahi, bin(i, b), blo, bhi, dc(i, a), dc(i, b), cnt_of(i, a),
-              cnt_of(i, b));
+  // D_i: +a -b (sums and count)
+  __device__ __forceinline__ void dpair(int i, uint32_t a, uint32_t b, Upd64 &E, Upd64 &F,
+                                        Upd32 &G, Upd32 &H) const {
+    E = add(1 + i, a);
+    F = second<true>(E, 1 + i, b);
+    G = cnt(i, a);
+    H = cnt(i, b);
+    if (H.a == G.a) H.v -= G.v;
   }
 };
 
-// One step of run_tile_delta8 from the ring words 0 .. 2r+7 of the entering
-// row pe and (RM) the leaving row pl.  Word j feeds H when j <= 2r, D_{j+1}
-// negatively (its left column leaves the window) when j <= 6, and D_{j-2r}
-// positively (its right column enters) when j >= 2r+1; with r >= 4 the left
-// words 0..7 all lie in H.  The words are read as 16-byte groups: groups 0
-// and 1 (the left words), the groups from M = (2r+1)/4 on (the right words:
-// with r even 2r+1 = 4M+1, so D_1..D_3 are words 1..3 of group M and
-// D_4..D_7 group M+1; with r odd 2r+1 = 4M+3, D_1 is word 3 of group M,
-// D_2..D_5 group M+1, D_6 and D_7 words 0 and 1 of group M+2), and the
-// middle groups 2 .. M-1, all H.
-template <int NT, bool ODD, bool RM>
+// One step of run_tile_delta8 from the ring words 0 .. 2R+7 (read as
+// 16-byte groups) of the entering row pe and (RM) the leaving row pl.
+// Word j feeds the window histogram when j <= 2R (He for even j, Ho for
+// odd j), D_{j+1} negatively (its left column leaves the window) when
+// j <= 6, and D_{j-2R} positively (its right column enters) when j >= 2R+1;
+// with R >= 4 the words 0..7 all lie in the window.  While the window fills
+// (RM false) rows only enter.
+template <int NT, int R, bool RM>
 __device__ __forceinline__ void delta8_step(const Delta8<NT> &o, const uint32_t *pe,
-                                            const uint32_t *pl, int r) {
-  auto ld = [](const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); };
-  const int M = (2 * r + 1) >> 2;
-  const uint4 e0 = ld(pe), e1 = ld(pe + 4);
-  const uint4 t0 = ld(pe + 4 * M), t1 = ld(pe + 4 * M + 4);
-  uint4 t2 = make_uint4(0u, 0u, 0u, 0u);
-  if (ODD) t2 = ld(pe + 4 * M + 8);
-  // the right words of D_1 .. D_7 (entering row)
-  uint32_t re[8];
-  if (ODD) {
-    re[1] = t0.w; re[2] = t1.x; re[3] = t1.y; re[4] = t1.z; re[5] = t1.w; re[6] = t2.x;
-    re[7] = t2.y;
-  } else {
-    re[1] = t0.y; re[2] = t0.z; re[3] = t0.w; re[4] = t1.x; re[5] = t1.y; re[6] = t1.z;
-    re[7] = t1.w;
+                                            const uint32_t *pl) {
+  constexpr int NG = (2 * R + 11) / 4;  // 16-byte groups covering words 0 .. 2R+7
+  uint32_t e[4 * NG], l[4 * NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(pe + 4 * g);
+    e[4 * g] = v.x;
+    e[4 * g + 1] = v.y;
+    e[4 * g + 2] = v.z;
+    e[4 * g + 3] = v.w;
+    if (RM) {
+      const uint4 u = *reinterpret_cast<const uint4 *>(pl + 4 * g);
+      l[4 * g] = u.x;
+      l[4 * g + 1] = u.y;
+      l[4 * g + 2] = u.z;
+      l[4 * g + 3] = u.w;
+    } else {
+      l[4 * g] = l[4 * g + 1] = l[4 * g + 2] = l[4 * g + 3] = 0u;
+    }
   }
-  re[0] = 0u;
+  Upd64 A, B, C, D, E, F;
+  Upd32 G, H;
   if constexpr (RM) {
-    const uint4 l0 = ld(pl), l1 = ld(pl + 4);
-    const uint4 u0 = ld(pl + 4 * M), u1 = ld(pl + 4 * M + 4);
-    uint4 u2 = make_uint4(0u, 0u, 0u, 0u);
-    if (ODD) u2 = ld(pl + 4 * M + 8);
-    // left words 0..6: H +e -l, D_{j+1} +l -e
-    o.template hd<true>(e0.x, l0.x, 1, l0.x, e0.x);
-    o.template hd<true>(e0.y, l0.y, 2, l0.y, e0.y);
-    o.template hd<true>(e0.z, l0.z, 3, l0.z, e0.z);
-    o.template hd<true>(e0.w, l0.w, 4, l0.w, e0.w);
-    o.template hd<true>(e1.x, l1.x, 5, l1.x, e1.x);
-    o.template hd<true>(e1.y, l1.y, 6, l1.y, e1.y);
-    o.template hd<true>(e1.z, l1.z, 7, l1.z, e1.z);
-    o.h(e1.w, l1.w);
-    // middle groups: H only
-#pragma unroll 2
-    for (int g = 2; g < M; ++g) {
-      const uint4 a = ld(pe + 4 * g), b = ld(pl + 4 * g);
-      o.h(a.x, b.x);
-      o.h(a.y, b.y);
-      o.h(a.z, b.z);
-      o.h(a.w, b.w);
+    // D pair k: the left words (k < 7: D_{k+1} +l_k -e_k), then the right
+    // words (k >= 7: D_{k-6} +e -l at word 2R + k - 6)
+    auto dp = [&](int k) {
+      if (k < 7)
+        o.dpair(k + 1, l[k], e[k], E, F, G, H);
+      else
+        o.dpair(k - 6, e[2 * R + k - 6], l[2 * R + k - 6], E, F, G, H);
+    };
+    // block b: He pair at word 2b, Ho pair at word 2b+1 (b < R), D pair b
+#pragma unroll
+    for (int b = 0; b <= R; ++b) {
+      A = o.add(0, e[2 * b]);
+      B = o.template second<true>(A, 0, l[2 * b]);
+      if (b < R) {
+        C = o.add(1, e[2 * b + 1]);
+        D = o.template second<true>(C, 1, l[2 * b + 1]);
+        if (b < 14) {
+          dp(b);
+          blk_hhd<true>(A, B, C, D, E, F, G, H);
+        } else {
+          blk_hh<true>(A, B, C, D);
+        }
+      } else if (b < 14) {
+        dp(b);
+        blk_hd<true>(A, B, E, F, G, H);
+      } else {
+        blk_h<true>(A, B);
+      }
     }
-    // the last window words of H, each with a right D pair, then the other
-    // right D pairs
-    if (ODD) {
-      o.template hd<true>(t0.x, u0.x, 1, t0.w, u0.w);
-      o.template hd<true>(t0.y, u0.y, 2, t1.x, u1.x);
-      o.template hd<true>(t0.z, u0.z, 3, t1.y, u1.y);
-      o.d(4, t1.z, u1.z);
-      o.d(5, t1.w, u1.w);
-      o.d(6, t2.x, u2.x);
-      o.d(7, t2.y, u2.y);
-    } else {
-      o.template hd<true>(t0.x, u0.x, 1, t0.y, u0.y);
-      o.d(2, t0.z, u0.z);
-      o.d(3, t0.w, u0.w);
-      o.d(4, t1.x, u1.x);
-      o.d(5, t1.y, u1.y);
-      o.d(6, t1.z, u1.z);
-      o.d(7, t1.w, u1.w);
+#pragma unroll
+    for (int k = R + 1; k < 14; ++k) {
+      dp(k);
+      blk_d(E, F, G, H);
     }
   } else {
-    // filling: H +e for every window word, D_i +(right word) -(left word)
-    o.template hd<false>(e0.x, e0.y, 1, re[1], e0.x);
-    o.template hd<false>(e0.z, e0.w, 2, re[2], e0.y);
-    o.template hd<false>(e1.x, e1.y, 3, re[3], e0.z);
-    o.template hd<false>(e1.z, e1.w, 4, re[4], e0.w);
-    o.d(5, re[5], e1.x);
-    o.d(6, re[6], e1.y);
-    o.d(7, re[7], e1.z);
-#pragma unroll 2
-    for (int g = 2; g < M; ++g) {
-      const uint4 a = ld(pe + 4 * g);
-      o.h_add2(a.x, a.y);
-      o.h_add2(a.z, a.w);
+    // He pairs of even words (4q, 4q + 2), Ho pairs of odd words (4q + 1,
+    // 4q + 3), D pair q: D_{q+1} +(word 2R + q + 1) -(word q)
+    constexpr int NPE = (R + 1) / 2, NPO = R / 2;
+    constexpr int NQ = NPE > NPO ? NPE : NPO;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const bool he = q < NPE, ho = q < NPO, hd = q < 7;
+      if (he) {
+        A = o.add(0, e[4 * q]);
+        B = o.template second<false>(A, 0, e[4 * q + 2]);
+      }
+      if (ho) {
+        C = o.add(1, e[4 * q + 1]);
+        D = o.template second<false>(C, 1, e[4 * q + 3]);
+      }
+      if (hd) o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
+      if (he && ho && hd)
+        blk_hhd<false>(A, B, C, D, E, F, G, H);
+      else if (he && ho)
+        blk_hh<false>(A, B, C, D);
+      else if (he && hd)
+        blk_hd<false>(A, B, E, F, G, H);
+      else if (ho && hd)
+        blk_hd<false>(C, D, E, F, G, H);
+      else if (he)
+        blk_h<false>(A, B);
+      else if (ho)
+        blk_h<false>(C, D);
     }
-    if (ODD) {
-      o.h_add2(t0.x, t0.y);
-      o.h_add(t0.z);
-    } else {
-      o.h_add(t0.x);
+    // the even and odd words left over, and the D pairs left over
+    if ((R + 1) % 2) {
+      A = o.add(0, e[2 * R]);
+      bin_add64(A.a, A.lo, A.hi);
+    }
+    if (R % 2) {
+      C = o.add(1, e[2 * R - 1]);
+      bin_add64(C.a, C.lo, C.hi);
+    }
+#pragma unroll
+    for (int q = NQ; q < 7; ++q) {
+      o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
+      blk_d(E, F, G, H);
     }
   }
 }
 
 // K = 8 output columns per thread (see above); the tile [x0, x0 + 8 NT) x
-// [y0, y1), x0 - r a multiple of 4 (tiles start at d.xshift), so every
+// [y0, y1), x0 - R a multiple of 4 (tiles start at d.xshift), so every
 // thread's window starts on a 16-byte boundary of the ring.  Pixels outside
 // the image are zero words (TMA fill, and the zeroed row padding), whose
 // delta is zero.
-template <int NT>
+template <int NT, int R>
 __device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
                                 const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
                                 uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
                                 bool tmap_global = false) {
   using O = Delta8<NT>;
   const int t = threadIdx.x;
-  const int r = d.r;
   const uint32_t L = d.L;
   const int xa = x0 + 8 * t;
-  const int xs = x0 - r;  // a multiple of 4 by the choice of d.xshift
+  const int xs = x0 - R;  // a multiple of 4 by the choice of d.xshift
   const int jl = 8 * t;
-  const int E0 = y0 - r;
-  const int nsteps = (y1 - y0) + 2 * r;
+  const int E0 = y0 - R;
+  const int nsteps = (y1 - y0) + 2 * R;
   O o;
   o.h0 = sm.sums + static_cast<uint32_t>(t) * 8u;
   o.dc0 = sm.sums + L * O::kLS + static_cast<uint32_t>(t) * 4u;
   for (uint32_t lv = 0; lv < L; ++lv) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) sts_zero64(o.h0 + lv * O::kLS + static_cast<uint32_t>(i) * O::kHS);
+    for (int i = 0; i < kD8Hists; ++i)
+      sts_zero64(o.h0 + lv * O::kLS + static_cast<uint32_t>(i) * O::kHS);
     sts_zero32(o.dc0 + lv * O::kDLS);
     sts_zero32(o.dc0 + lv * O::kDLS + O::kDW);
   }
-  const bool odd = (r & 1) != 0;
 
   return ring_pass(
       d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
       y1, [&](int s, const uint32_t *rowe, const uint32_t *rowl) {
-        const bool rm = s >= 2 * r + 1;  // the leaving row was added by this tile
-        const bool out_now = s >= 2 * r;
-        const int y = E0 + s - r;
+        const bool rm = s >= 2 * R + 1;  // the leaving row was added by this tile
+        const bool out_now = s >= 2 * R;
+        const int y = E0 + s - R;
         const uint32_t *pe = rowe + jl;
         const uint32_t *pl = rowl + jl;
         uint32_t alpha[8];
@@ -1957,24 +2009,20 @@ __device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x
           const int x = xa + i;
           alpha[i] = (out_now && d.bpp == 4 && x >= d.ox0 && x < d.ox1) ? load_alpha(d, x, y) : 0u;
         }
-        if (odd) {
-          if (rm)
-            delta8_step<NT, true, true>(o, pe, pl, r);
-          else
-            delta8_step<NT, true, false>(o, pe, pl, r);
-        } else {
-          if (rm)
-            delta8_step<NT, false, true>(o, pe, pl, r);
-          else
-            delta8_step<NT, false, false>(o, pe, pl, r);
-        }
+        if (rm)
+          delta8_step<NT, R, true>(o, pe, pl);
+        else
+          delta8_step<NT, R, false>(o, pe, pl);
         if (!out_now) return;
         // keys (count << 22) | (31 - level): the lowest level wins ties under max
         uint32_t best[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) best[i] = 0u;
+#pragma unroll 4
         for (uint32_t lv = 0; lv < L; ++lv) {
-          const uint32_t c = lds_u32(o.h0 + lv * O::kLS);  // count in bits 0..9
+          // He's and Ho's low words: the counts sit in bits 0..9, so the low
+          // 10 bits of the sum are the window's count
+          const uint32_t c = lds_u32(o.h0 + lv * O::kLS) + lds_u32(o.h0 + lv * O::kLS + O::kHS);
           const uint32_t da = lds_u32(o.dc0 + lv * O::kDLS);
           const uint32_t db = lds_u32(o.dc0 + lv * O::kDLS + O::kDW);
           const uint32_t k0 = (c << 22) | (31u - lv);
@@ -1986,11 +2034,13 @@ __device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x
           const uint32_t kb = k0 - (128u << 22);
           const uint32_t k4 = kb + ((pa >> 24) << 22);
 #pragma unroll
-          for (int i = 1; i <= 3; ++i) best[i] = max(best[i], kb + (((pa >> (8 * (i - 1))) & 0xFFu) << 22));
+          for (int i = 1; i <= 3; ++i)
+            best[i] = max(best[i], kb + (((pa >> (8 * (i - 1))) & 0xFFu) << 22));
           best[4] = max(best[4], k4);
           const uint32_t kb4 = k4 - (128u << 22);
 #pragma unroll
-          for (int i = 5; i <= 7; ++i) best[i] = max(best[i], kb4 + (((pb >> (8 * (i - 5))) & 0xFFu) << 22));
+          for (int i = 5; i <= 7; ++i)
+            best[i] = max(best[i], kb4 + (((pb >> (8 * (i - 5))) & 0xFFu) << 22));
         }
         // the reciprocals first, so that their latency overlaps the loads
         // of the winning bins
@@ -2005,19 +2055,19 @@ __device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x
           if ((best[i] >> 22) == 0u) continue;  // no level below L (literal mode only)
           uint64_t v = 0;
 #pragma unroll
-          for (int j = 0; j <= i; ++j) {
+          for (int j = 0; j < 2 + i; ++j) {  // He, Ho, D_1 .. D_i
             uint32_t lo, hi;
             lds_v2(o.h0 + m * O::kLS + static_cast<uint32_t>(j) * O::kHS, lo, hi);
             v += static_cast<uint64_t>(hi) << 32 | lo;
           }
           const uint32_t lo = static_cast<uint32_t>(v);
           const uint32_t hi = static_cast<uint32_t>(v >> 32);
-          const uint32_t R = (lo >> 10) & 0x3FFFFu;
-          const uint32_t G = (lo >> 28) | ((hi & 0x3FFFu) << 4);
-          const uint32_t B = hi >> 14;
+          const uint32_t Rs = (lo >> 10) & 0x3FFFFu;
+          const uint32_t Gs = (lo >> 28) | ((hi & 0x3FFFu) << 4);
+          const uint32_t Bs = hi >> 14;
           const uint32_t mul = mulv[i];
-          store_pixel(d, x, y, __umulhi(R << 1, mul), __umulhi(G << 1, mul), __umulhi(B << 1, mul),
-                      alpha[i]);
+          store_pixel(d, x, y, __umulhi(Rs << 1, mul), __umulhi(Gs << 1, mul),
+                      __umulhi(Bs << 1, mul), alpha[i]);
         }
       });
 }

@@ -133,11 +133,11 @@ inline int pack_grid_for(uint32_t rows, int sms) {
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
 // per thread, bins of the variant's size; 2 or 4: kcols histograms, one
 // more where the window histogram is split, of L levels per thread, bins of
-// 8 bytes (variant A) or 8 + 2 bytes (variant B); 8: eight histograms of
+// 8 bytes (variant A) or 8 + 2 bytes (variant B); 8: nine histograms of
 // 8-byte bins and two count words per level and thread).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
   // (column path: cols_hist_bytes)
-  if (kcols == 8) return static_cast<size_t>(8u * 8u + 8u) * L * nt;
+  if (kcols == 8) return static_cast<size_t>(kD8Hists * 8u + 8u) * L * nt;
   if (kcols > 1) {
     const size_t nh = static_cast<size_t>(kcols) + static_cast<size_t>(hsplit(kcols, variant)) - 1u;
     // variant B: 8-byte sums and a 16-bit count per bin
@@ -214,6 +214,14 @@ cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
 cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStream_t s);
+// Eight columns per thread (oilpaint_delta8.cu): nt = 32 or 64 threads,
+// d.r in kDelta8MinRadius .. kDelta8MaxRadius (one kernel per radius),
+// variant A, d.L <= 32; cudaErrorInvalidValue otherwise.
+cudaError_t launch_delta8(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
+                          const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
+                          uint64_t timeout_ns, cudaStream_t s);
+cudaError_t set_delta8_smem_limit(size_t bytes);
+int delta8_occupancy(uint32_t nt, size_t smem);
 // Checked builds: the bounds-check violation bits since the last call
 // (1 shared memory, 2 image pixels, 4 TMA copy), cleared; 0 otherwise.
 cudaError_t take_check_error(uint32_t *bits);

@@ -9,7 +9,8 @@
 //   tile_delta_kernel<NT, K, VAR>           one CTA per output tile, K output
 //                                           columns per thread through
 //                                           difference histograms (K = 8:
-//                                           run_tile_delta8, variant A)
+//                                           tile_delta8_kernel, in
+//                                           oilpaint_delta8.cu)
 //   tile_cols_kernel<NW, TWK, VAR>          one CTA per output tile, column
 //                                           histograms swept by NW warps
 //   persistent_kernel<NT, K>                grid-sized CTAs pulling
@@ -85,10 +86,7 @@ __global__ void __launch_bounds__(NT, 1)
   const int x0 = d.xshift + static_cast<int>(blockIdx.x) * NT * K;
   const int y0 = d.oy0 + static_cast<int>(blockIdx.y * d.tile_h);
   const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
-  if constexpr (K == 8)
-    run_tile_delta8<NT>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
-  else
-    run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+  run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
 template <int NW, int TWK, int VAR>
@@ -210,10 +208,7 @@ template <int NT>
 static void delta_n(int k, const ImgDesc &d, const CUtensorMap &map, const RingCfg &rc,
                     dim3 grid, size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
   const bool a = d.variant == static_cast<uint32_t>(kVarA);
-  if (k == 8) {  // variant A, 32 or 64 threads (checked by the host)
-    if constexpr (NT <= 64)
-      if (a) tile_delta_kernel<NT, 8, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
-  } else if (k == 4) {
+  if (k == 4) {
     if (a)
       tile_delta_kernel<NT, 4, kVarA><<<grid, NT, smem, s>>>(map, d, rc, err, timeout_ns);
     else
@@ -257,8 +252,8 @@ cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
     }
     return cudaGetLastError();
   }
-  if (kcols != 1 && kcols != 2 && kcols != 4 && kcols != 8) return cudaErrorInvalidValue;
-  if (kcols == 8 && (nt > 64 || variant != kVarA)) return cudaErrorInvalidValue;
+  if (kcols == 8) return launch_delta8(nt, d, map, rc, grid, smem, err, timeout_ns, s);
+  if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
   switch (nt) {
     case 32:
       kcols == 1 ? plain_n<32>(variant, d, map, rc, grid, smem, err, timeout_ns, s)
@@ -355,8 +350,6 @@ static cudaError_t set_limit_n(int b) {
   if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kVarA>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 2, kVarB>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 4, kVarB>, a, b)) != cudaSuccess) return e;
-  if constexpr (NT <= 64)
-    if ((e = cudaFuncSetAttribute(tile_delta_kernel<NT, 8, kVarA>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 1>, a, b)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(persistent_kernel<NT, 2>, a, b)) != cudaSuccess) return e;
   return cudaFuncSetAttribute(persistent_kernel<NT, 4>, a, b);
@@ -375,6 +368,7 @@ static cudaError_t set_limit_cols(int b) {
 cudaError_t set_tile_smem_limit(size_t bytes) {
   const int b = static_cast<int>(bytes);
   cudaError_t e;
+  if ((e = set_delta8_smem_limit(bytes)) != cudaSuccess) return e;
   if ((e = set_limit_cols<1>(b)) != cudaSuccess) return e;
   if ((e = set_limit_cols<2>(b)) != cudaSuccess) return e;
   if ((e = set_limit_cols<4>(b)) != cudaSuccess) return e;
@@ -397,11 +391,7 @@ static int occupancy_n(bool persistent, int kcols, int variant, size_t smem) {
     if (kcols == 2) return occ_of(persistent_kernel<NT, 2>, NT, smem);
     return occ_of(persistent_kernel<NT, 1>, NT, smem);
   }
-  if (kcols == 8) {
-    if constexpr (NT <= 64)
-      if (variant == kVarA) return occ_of(tile_delta_kernel<NT, 8, kVarA>, NT, smem);
-    return 0;
-  }
+  if (kcols == 8) return variant == kVarA ? delta8_occupancy(NT, smem) : 0;
   if (kcols == 4)
     return variant == kVarA ? occ_of(tile_delta_kernel<NT, 4, kVarA>, NT, smem)
                             : occ_of(tile_delta_kernel<NT, 4, kVarB>, NT, smem);
