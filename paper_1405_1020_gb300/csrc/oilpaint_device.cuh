@@ -277,56 +277,61 @@ __device__ __forceinline__ void sts_u16(uint32_t addr, uint32_t v) {
 }
 
 
-// 64-bit read-modify-write of one histogram bin.  All histogram accesses are
-// volatile asm, so they keep their program order among themselves; the ring
-// reads are ordinary loads and may be scheduled around them.
+// Raw shared-memory accesses of the histogram helpers (volatile asm: they
+// keep their program order among themselves, so a read after a write of the
+// same bin sees it; the arithmetic between them is plain C++, scheduled
+// freely).  Bins are 64-bit words updated by 64-bit integer adds.
+__device__ __forceinline__ uint64_t ld_bin(uint32_t addr) {
+  uint64_t v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void st_bin(uint32_t addr, uint64_t v) {
+  asm volatile("st.shared.u64 [%0], %1;" ::"r"(addr), "l"(v));
+}
+__device__ __forceinline__ uint32_t ld_w32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void st_w32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ uint32_t ld_w16(uint32_t addr) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void st_w16(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(static_cast<uint16_t>(v)));
+}
+__device__ __forceinline__ uint64_t u64_of(uint32_t lo, uint32_t hi) {
+  return static_cast<uint64_t>(hi) << 32 | lo;
+}
+
+// 64-bit read-modify-write of one histogram bin.
 __device__ __forceinline__ void bin_add64(uint32_t addr, uint32_t dlo, uint32_t dhi) {
   if (!OPK_SMEM_OK(addr, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a, b;\n\t"
-      "ld.shared.v2.u32 {a, b}, [%0];\n\t"
-      "add.cc.u32 a, a, %1;\n\t"
-      "addc.u32 b, b, %2;\n\t"
-      "st.shared.v2.u32 [%0], {a, b};\n\t}" ::"r"(addr),
-      "r"(dlo), "r"(dhi));
+  st_bin(addr, ld_bin(addr) + u64_of(dlo, dhi));
 }
 
 __device__ __forceinline__ void bin_sub64(uint32_t addr, uint32_t dlo, uint32_t dhi) {
   if (!OPK_SMEM_OK(addr, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a, b;\n\t"
-      "ld.shared.v2.u32 {a, b}, [%0];\n\t"
-      "sub.cc.u32 a, a, %1;\n\t"
-      "subc.u32 b, b, %2;\n\t"
-      "st.shared.v2.u32 [%0], {a, b};\n\t}" ::"r"(addr),
-      "r"(dlo), "r"(dhi));
+  st_bin(addr, ld_bin(addr) - u64_of(dlo, dhi));
 }
 
 __device__ __forceinline__ void cnt_add(uint32_t addr, uint32_t d) {
   if (!OPK_SMEM_OK(addr, 4u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a;\n\t"
-      "ld.shared.u32 a, [%0];\n\t"
-      "add.u32 a, a, %1;\n\t"
-      "st.shared.u32 [%0], a;\n\t}" ::"r"(addr),
-      "r"(d));
+  st_w32(addr, ld_w32(addr) + d);
 }
 
 // Two 64-bit additions issued together (addr_a != addr_b).
 __device__ __forceinline__ void bin_add64x2(uint32_t addr_a, uint32_t alo, uint32_t ahi,
                                             uint32_t addr_b, uint32_t blo, uint32_t bhi) {
   if (!OPK_SMEM_OK(addr_a, 8u) || !OPK_SMEM_OK(addr_b, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
-      "add.cc.u32 a0, a0, %1;\n\t"
-      "addc.u32 a1, a1, %2;\n\t"
-      "add.cc.u32 b0, b0, %4;\n\t"
-      "addc.u32 b1, b1, %5;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(addr_a),
-      "r"(alo), "r"(ahi), "r"(addr_b), "r"(blo), "r"(bhi));
+  const uint64_t a = ld_bin(addr_a), b = ld_bin(addr_b);
+  st_bin(addr_a, a + u64_of(alo, ahi));
+  st_bin(addr_b, b + u64_of(blo, bhi));
 }
 
 // +(alo, ahi) at A and -(blo, bhi) at B as one two-deep update that is
@@ -336,20 +341,11 @@ __device__ __forceinline__ void bin_add64x2(uint32_t addr_a, uint32_t alo, uint3
 __device__ __forceinline__ void bin_addsub64_chain(uint32_t A, uint32_t alo, uint32_t ahi,
                                                    uint32_t B, uint32_t blo, uint32_t bhi) {
   if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t.reg .pred p;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
-      "add.cc.u32 a0, a0, %1;\n\t"
-      "addc.u32 a1, a1, %2;\n\t"
-      "setp.eq.u32 p, %0, %3;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "sub.cc.u32 b0, b0, %4;\n\t"
-      "subc.u32 b1, b1, %5;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(A),
-      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi));
+  const uint64_t a0 = ld_bin(A), b0 = ld_bin(B);
+  const uint64_t a = a0 + u64_of(alo, ahi);
+  const uint64_t b = (A == B ? a : b0) - u64_of(blo, bhi);
+  st_bin(A, a);
+  st_bin(B, b);
 }
 
 // +(alo, ahi) at A, then +(blo, bhi) at B, where A and B may coincide (the
@@ -357,20 +353,11 @@ __device__ __forceinline__ void bin_addsub64_chain(uint32_t A, uint32_t alo, uin
 __device__ __forceinline__ void bin_add64x2_chain(uint32_t A, uint32_t alo, uint32_t ahi,
                                                   uint32_t B, uint32_t blo, uint32_t bhi) {
   if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1;\n\t.reg .pred p;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
-      "add.cc.u32 a0, a0, %1;\n\t"
-      "addc.u32 a1, a1, %2;\n\t"
-      "setp.eq.u32 p, %0, %3;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "add.cc.u32 b0, b0, %4;\n\t"
-      "addc.u32 b1, b1, %5;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.v2.u32 [%3], {b0, b1};\n\t}" ::"r"(A),
-      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi));
+  const uint64_t a0 = ld_bin(A), b0 = ld_bin(B);
+  const uint64_t a = a0 + u64_of(alo, ahi);
+  const uint64_t b = (A == B ? a : b0) + u64_of(blo, bhi);
+  st_bin(A, a);
+  st_bin(B, b);
 }
 
 // Two such chained pairs issued together (A, B in one histogram; C, D in
@@ -381,32 +368,14 @@ __device__ __forceinline__ void bin_add64x4_chain(uint32_t A, uint32_t alo, uint
                                                   uint32_t D, uint32_t dlo, uint32_t dhi) {
   if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u))
     return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t.reg .pred p, q;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
-      "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"
-      "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"
-      "add.cc.u32 a0, a0, %1;\n\t"
-      "addc.u32 a1, a1, %2;\n\t"
-      "add.cc.u32 c0, c0, %7;\n\t"
-      "addc.u32 c1, c1, %8;\n\t"
-      "setp.eq.u32 p, %0, %3;\n\t"
-      "setp.eq.u32 q, %6, %9;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "selp.b32 d0, c0, d0, q;\n\t"
-      "selp.b32 d1, c1, d1, q;\n\t"
-      "add.cc.u32 b0, b0, %4;\n\t"
-      "addc.u32 b1, b1, %5;\n\t"
-      "add.cc.u32 d0, d0, %10;\n\t"
-      "addc.u32 d1, d1, %11;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.v2.u32 [%3], {b0, b1};\n\t"
-      "st.shared.v2.u32 [%6], {c0, c1};\n\t"
-      "st.shared.v2.u32 [%9], {d0, d1};\n\t}" ::"r"(A),
-      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi), "r"(D),
-      "r"(dlo), "r"(dhi));
+  const uint64_t a0 = ld_bin(A), b0 = ld_bin(B), c0 = ld_bin(C), d0 = ld_bin(D);
+  const uint64_t a = a0 + u64_of(alo, ahi), c = c0 + u64_of(clo, chi);
+  const uint64_t b = (A == B ? a : b0) + u64_of(blo, bhi);
+  const uint64_t d = (C == D ? c : d0) + u64_of(dlo, dhi);
+  st_bin(A, a);
+  st_bin(B, b);
+  st_bin(C, c);
+  st_bin(D, d);
 }
 
 // Two such updates issued together (A, B in one histogram; C, D in
@@ -417,32 +386,14 @@ __device__ __forceinline__ void bin_addsub64x2_chain(uint32_t A, uint32_t alo, u
                                                      uint32_t D, uint32_t dlo, uint32_t dhi) {
   if (!OPK_SMEM_OK(A, 8u) || !OPK_SMEM_OK(B, 8u) || !OPK_SMEM_OK(C, 8u) || !OPK_SMEM_OK(D, 8u))
     return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t.reg .pred p, q;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%3];\n\t"
-      "ld.shared.v2.u32 {c0, c1}, [%6];\n\t"
-      "ld.shared.v2.u32 {d0, d1}, [%9];\n\t"
-      "add.cc.u32 a0, a0, %1;\n\t"
-      "addc.u32 a1, a1, %2;\n\t"
-      "add.cc.u32 c0, c0, %7;\n\t"
-      "addc.u32 c1, c1, %8;\n\t"
-      "setp.eq.u32 p, %0, %3;\n\t"
-      "setp.eq.u32 q, %6, %9;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "selp.b32 d0, c0, d0, q;\n\t"
-      "selp.b32 d1, c1, d1, q;\n\t"
-      "sub.cc.u32 b0, b0, %4;\n\t"
-      "subc.u32 b1, b1, %5;\n\t"
-      "sub.cc.u32 d0, d0, %10;\n\t"
-      "subc.u32 d1, d1, %11;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.v2.u32 [%3], {b0, b1};\n\t"
-      "st.shared.v2.u32 [%6], {c0, c1};\n\t"
-      "st.shared.v2.u32 [%9], {d0, d1};\n\t}" ::"r"(A),
-      "r"(alo), "r"(ahi), "r"(B), "r"(blo), "r"(bhi), "r"(C), "r"(clo), "r"(chi), "r"(D),
-      "r"(dlo), "r"(dhi));
+  const uint64_t a0 = ld_bin(A), b0 = ld_bin(B), c0 = ld_bin(C), d0 = ld_bin(D);
+  const uint64_t a = a0 + u64_of(alo, ahi), c = c0 + u64_of(clo, chi);
+  const uint64_t b = (A == B ? a : b0) - u64_of(blo, bhi);
+  const uint64_t d = (C == D ? c : d0) - u64_of(dlo, dhi);
+  st_bin(A, a);
+  st_bin(B, b);
+  st_bin(C, c);
+  st_bin(D, d);
 }
 
 // Variant B bins (64-bit sums at As / Bs, 32-bit counts at Ac / Bc): +(alo,
@@ -456,27 +407,19 @@ __device__ __forceinline__ void binb_addsub_chain(uint32_t As, uint32_t Ac, uint
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
       !OPK_SMEM_OK(Bc, 4u))
     return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t.reg .pred p;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u32 a2, [%1];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
-      "ld.shared.u32 b2, [%6];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "setp.eq.u32 p, %0, %5;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "selp.b32 b2, a2, b2, p;\n\t"
-      "sub.cc.u32 b0, b0, %7;\n\t"
-      "subc.u32 b1, b1, %8;\n\t"
-      "sub.u32 b2, b2, %9;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u32 [%1], a2;\n\t"
-      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
-      "st.shared.u32 [%6], b2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+  const uint64_t a0 = ld_bin(As);
+  const uint32_t ca0 = ld_w32(Ac);
+  const uint64_t b0 = ld_bin(Bs);
+  const uint32_t cb0 = ld_w32(Bc);
+  const bool same = As == Bs;
+  const uint64_t a = a0 + u64_of(alo, ahi);
+  const uint32_t ca = ca0 + ac;
+  const uint64_t b = (same ? a : b0) - u64_of(blo, bhi);
+  const uint32_t cb = (same ? ca : cb0) - bc;
+  st_bin(As, a);
+  st_w32(Ac, ca);
+  st_bin(Bs, b);
+  st_w32(Bc, cb);
 }
 
 // ------------------------------------------------------------ pack prepass
@@ -814,38 +757,23 @@ __device__ __forceinline__ void binb_add_x2(uint32_t As, uint32_t Ac, uint32_t a
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u) || !OPK_SMEM_OK(Bs, 8u) ||
       !OPK_SMEM_OK(Bc, 4u))
     return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u32 a2, [%1];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
-      "ld.shared.u32 b2, [%6];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "add.cc.u32 b0, b0, %7;\n\t"
-      "addc.u32 b1, b1, %8;\n\t"
-      "add.u32 b2, b2, %9;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u32 [%1], a2;\n\t"
-      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
-      "st.shared.u32 [%6], b2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+  const uint64_t a0 = ld_bin(As);
+  const uint32_t ca0 = ld_w32(Ac);
+  const uint64_t b0 = ld_bin(Bs);
+  const uint32_t cb0 = ld_w32(Bc);
+  st_bin(As, a0 + u64_of(alo, ahi));
+  st_w32(Ac, ca0 + ac);
+  st_bin(Bs, b0 + u64_of(blo, bhi));
+  st_w32(Bc, cb0 + bc);
 }
 
 __device__ __forceinline__ void binb_add(uint32_t As, uint32_t Ac, uint32_t lo, uint32_t hi,
                                          uint32_t c) {
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 4u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u32 a2, [%1];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u32 [%1], a2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(lo), "r"(hi), "r"(c));
+  const uint64_t a0 = ld_bin(As);
+  const uint32_t ca0 = ld_w32(Ac);
+  st_bin(As, a0 + u64_of(lo, hi));
+  st_w32(Ac, ca0 + c);
 }
 
 // Variant B bins with 16-bit counts (the K-column path: a window's count is
@@ -856,16 +784,10 @@ __device__ __forceinline__ void binb_add(uint32_t As, uint32_t Ac, uint32_t lo, 
 __device__ __forceinline__ void binb16_add(uint32_t As, uint32_t Ac, uint32_t lo, uint32_t hi,
                                            uint32_t c) {
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 2u)) return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u16 a2, [%1];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u16 [%1], a2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(lo), "r"(hi), "r"(c));
+  const uint64_t a0 = ld_bin(As);
+  const uint32_t ca0 = ld_w16(Ac);
+  st_bin(As, a0 + u64_of(lo, hi));
+  st_w16(Ac, ca0 + c);
 }
 
 __device__ __forceinline__ void binb16_add_x2(uint32_t As, uint32_t Ac, uint32_t alo,
@@ -875,23 +797,14 @@ __device__ __forceinline__ void binb16_add_x2(uint32_t As, uint32_t Ac, uint32_t
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 2u) || !OPK_SMEM_OK(Bs, 8u) ||
       !OPK_SMEM_OK(Bc, 2u))
     return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u16 a2, [%1];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
-      "ld.shared.u16 b2, [%6];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "add.cc.u32 b0, b0, %7;\n\t"
-      "addc.u32 b1, b1, %8;\n\t"
-      "add.u32 b2, b2, %9;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u16 [%1], a2;\n\t"
-      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
-      "st.shared.u16 [%6], b2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+  const uint64_t a0 = ld_bin(As);
+  const uint32_t ca0 = ld_w16(Ac);
+  const uint64_t b0 = ld_bin(Bs);
+  const uint32_t cb0 = ld_w16(Bc);
+  st_bin(As, a0 + u64_of(alo, ahi));
+  st_w16(Ac, ca0 + ac);
+  st_bin(Bs, b0 + u64_of(blo, bhi));
+  st_w16(Bc, cb0 + bc);
 }
 
 __device__ __forceinline__ void binb16_addsub_chain(uint32_t As, uint32_t Ac, uint32_t alo,
@@ -901,27 +814,19 @@ __device__ __forceinline__ void binb16_addsub_chain(uint32_t As, uint32_t Ac, ui
   if (!OPK_SMEM_OK(As, 8u) || !OPK_SMEM_OK(Ac, 2u) || !OPK_SMEM_OK(Bs, 8u) ||
       !OPK_SMEM_OK(Bc, 2u))
     return;
-  asm volatile(
-      "{\n\t.reg .u32 a0, a1, a2, b0, b1, b2;\n\t.reg .pred p;\n\t"
-      "ld.shared.v2.u32 {a0, a1}, [%0];\n\t"
-      "ld.shared.u16 a2, [%1];\n\t"
-      "ld.shared.v2.u32 {b0, b1}, [%5];\n\t"
-      "ld.shared.u16 b2, [%6];\n\t"
-      "add.cc.u32 a0, a0, %2;\n\t"
-      "addc.u32 a1, a1, %3;\n\t"
-      "add.u32 a2, a2, %4;\n\t"
-      "setp.eq.u32 p, %0, %5;\n\t"
-      "selp.b32 b0, a0, b0, p;\n\t"
-      "selp.b32 b1, a1, b1, p;\n\t"
-      "selp.b32 b2, a2, b2, p;\n\t"
-      "sub.cc.u32 b0, b0, %7;\n\t"
-      "subc.u32 b1, b1, %8;\n\t"
-      "sub.u32 b2, b2, %9;\n\t"
-      "st.shared.v2.u32 [%0], {a0, a1};\n\t"
-      "st.shared.u16 [%1], a2;\n\t"
-      "st.shared.v2.u32 [%5], {b0, b1};\n\t"
-      "st.shared.u16 [%6], b2;\n\t}" ::"r"(As),
-      "r"(Ac), "r"(alo), "r"(ahi), "r"(ac), "r"(Bs), "r"(Bc), "r"(blo), "r"(bhi), "r"(bc));
+  const uint64_t a0 = ld_bin(As);
+  const uint32_t ca0 = ld_w16(Ac);
+  const uint64_t b0 = ld_bin(Bs);
+  const uint32_t cb0 = ld_w16(Bc);
+  const bool same = As == Bs;
+  const uint64_t a = a0 + u64_of(alo, ahi);
+  const uint32_t ca = ca0 + ac;
+  const uint64_t b = (same ? a : b0) - u64_of(blo, bhi);
+  const uint32_t cb = (same ? ca : cb0) - bc;
+  st_bin(As, a);
+  st_w16(Ac, ca);
+  st_bin(Bs, b);
+  st_w16(Bc, cb);
 }
 
 // Word format 2 (L <= 32): R @0..7 | level @8..12 | B @13..20 | G @21..28 |
@@ -1676,21 +1581,16 @@ constexpr int kD8Hists = 9;
 
 // A 64-bit bin update (shared address, delta) and a 32-bit one.
 struct Upd64 {
-  uint32_t a, lo, hi;
+  uint32_t a;
+  uint64_t d;
 };
 struct Upd32 {
   uint32_t a, v;
 };
 
-#define OPK_LD64(r, a) "ld.shared.v2.u32 {" r "0, " r "1}, [" a "];\n\t"
-#define OPK_ST64(r, a) "st.shared.v2.u32 [" a "], {" r "0, " r "1};\n\t"
-#define OPK_ADD64(r, lo, hi) \
-  "add.cc.u32 " r "0, " r "0, " lo ";\n\taddc.u32 " r "1, " r "1, " hi ";\n\t"
-#define OPK_SUB64(r, lo, hi) \
-  "sub.cc.u32 " r "0, " r "0, " lo ";\n\tsubc.u32 " r "1, " r "1, " hi ";\n\t"
-
 // Pairs (A, B) on He, (C, D) on Ho and (E, F) on a D_i with its count words
 // (G, H): A, C, E, G add; B and D subtract (SUB) or add; F and H subtract.
+// All loads first, then the stores in slot order.
 template <bool SUB>
 __device__ __forceinline__ void blk_hhd(const Upd64 &A, const Upd64 &B, const Upd64 &C,
                                         const Upd64 &D, const Upd64 &E, const Upd64 &F,
@@ -1699,26 +1599,17 @@ __device__ __forceinline__ void blk_hhd(const Upd64 &A, const Upd64 &B, const Up
       !OPK_SMEM_OK(D.a, 8u) || !OPK_SMEM_OK(E.a, 8u) || !OPK_SMEM_OK(F.a, 8u) ||
       !OPK_SMEM_OK(G.a, 4u) || !OPK_SMEM_OK(H.a, 4u))
     return;
-#define OPK_HHD_BODY(OPB, OPD)                                                                 \
-  "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1, e0, e1, f0, f1, g, h;\n\t" OPK_LD64(         \
-      "a", "%0") OPK_LD64("b", "%3") OPK_LD64("c", "%6") OPK_LD64("d", "%9")                   \
-      OPK_LD64("e", "%12") OPK_LD64("f", "%15") "ld.shared.u32 g, [%18];\n\t"                  \
-      "ld.shared.u32 h, [%20];\n\t" OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5")            \
-      OPK_ADD64("c", "%7", "%8") OPD("d", "%10", "%11") OPK_ADD64("e", "%13", "%14")           \
-      OPK_SUB64("f", "%16", "%17") "add.u32 g, g, %19;\n\tsub.u32 h, h, %21;\n\t"              \
-      OPK_ST64("a", "%0") OPK_ST64("b", "%3") OPK_ST64("c", "%6") OPK_ST64("d", "%9")          \
-      OPK_ST64("e", "%12") OPK_ST64("f", "%15") "st.shared.u32 [%18], g;\n\t"                  \
-      "st.shared.u32 [%20], h;\n\t}"
-#define OPK_HHD_ARGS                                                                           \
-  "r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo), "r"(B.hi), "r"(C.a), "r"(C.lo),        \
-      "r"(C.hi), "r"(D.a), "r"(D.lo), "r"(D.hi), "r"(E.a), "r"(E.lo), "r"(E.hi), "r"(F.a),     \
-      "r"(F.lo), "r"(F.hi), "r"(G.a), "r"(G.v), "r"(H.a), "r"(H.v)
-  if constexpr (SUB)
-    asm volatile(OPK_HHD_BODY(OPK_SUB64, OPK_SUB64)::OPK_HHD_ARGS);
-  else
-    asm volatile(OPK_HHD_BODY(OPK_ADD64, OPK_ADD64)::OPK_HHD_ARGS);
-#undef OPK_HHD_BODY
-#undef OPK_HHD_ARGS
+  const uint64_t a = ld_bin(A.a), b = ld_bin(B.a), c = ld_bin(C.a), d = ld_bin(D.a);
+  const uint64_t e = ld_bin(E.a), f = ld_bin(F.a);
+  const uint32_t g = ld_w32(G.a), h = ld_w32(H.a);
+  st_bin(A.a, a + A.d);
+  st_bin(B.a, SUB ? b - B.d : b + B.d);
+  st_bin(C.a, c + C.d);
+  st_bin(D.a, SUB ? d - D.d : d + D.d);
+  st_bin(E.a, e + E.d);
+  st_bin(F.a, f - F.d);
+  st_w32(G.a, g + G.v);
+  st_w32(H.a, h - H.v);
 }
 
 // Pairs (A, B) and (C, D) on two histograms.
@@ -1728,20 +1619,11 @@ __device__ __forceinline__ void blk_hh(const Upd64 &A, const Upd64 &B, const Upd
   if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u) || !OPK_SMEM_OK(C.a, 8u) ||
       !OPK_SMEM_OK(D.a, 8u))
     return;
-#define OPK_HH_BODY(OPB)                                                                       \
-  "{\n\t.reg .u32 a0, a1, b0, b1, c0, c1, d0, d1;\n\t" OPK_LD64("a", "%0") OPK_LD64("b", "%3") \
-      OPK_LD64("c", "%6") OPK_LD64("d", "%9") OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5")  \
-      OPK_ADD64("c", "%7", "%8") OPB("d", "%10", "%11") OPK_ST64("a", "%0")                    \
-      OPK_ST64("b", "%3") OPK_ST64("c", "%6") OPK_ST64("d", "%9") "}"
-#define OPK_HH_ARGS                                                                            \
-  "r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo), "r"(B.hi), "r"(C.a), "r"(C.lo),        \
-      "r"(C.hi), "r"(D.a), "r"(D.lo), "r"(D.hi)
-  if constexpr (SUB)
-    asm volatile(OPK_HH_BODY(OPK_SUB64)::OPK_HH_ARGS);
-  else
-    asm volatile(OPK_HH_BODY(OPK_ADD64)::OPK_HH_ARGS);
-#undef OPK_HH_BODY
-#undef OPK_HH_ARGS
+  const uint64_t a = ld_bin(A.a), b = ld_bin(B.a), c = ld_bin(C.a), d = ld_bin(D.a);
+  st_bin(A.a, a + A.d);
+  st_bin(B.a, SUB ? b - B.d : b + B.d);
+  st_bin(C.a, c + C.d);
+  st_bin(D.a, SUB ? d - D.d : d + D.d);
 }
 
 // Pair (A, B) on He or Ho, pair (E, F) on a D_i with its count words (G, H).
@@ -1751,39 +1633,23 @@ __device__ __forceinline__ void blk_hd(const Upd64 &A, const Upd64 &B, const Upd
   if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u) || !OPK_SMEM_OK(E.a, 8u) ||
       !OPK_SMEM_OK(F.a, 8u) || !OPK_SMEM_OK(G.a, 4u) || !OPK_SMEM_OK(H.a, 4u))
     return;
-#define OPK_HD_BODY(OPB)                                                                       \
-  "{\n\t.reg .u32 a0, a1, b0, b1, e0, e1, f0, f1, g, h;\n\t" OPK_LD64("a", "%0")               \
-      OPK_LD64("b", "%3") OPK_LD64("e", "%6") OPK_LD64("f", "%9") "ld.shared.u32 g, [%12];\n\t" \
-      "ld.shared.u32 h, [%14];\n\t" OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5")            \
-      OPK_ADD64("e", "%7", "%8") OPK_SUB64("f", "%10", "%11")                                  \
-      "add.u32 g, g, %13;\n\tsub.u32 h, h, %15;\n\t" OPK_ST64("a", "%0") OPK_ST64("b", "%3")   \
-      OPK_ST64("e", "%6") OPK_ST64("f", "%9") "st.shared.u32 [%12], g;\n\t"                    \
-      "st.shared.u32 [%14], h;\n\t}"
-#define OPK_HD_ARGS                                                                            \
-  "r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo), "r"(B.hi), "r"(E.a), "r"(E.lo),        \
-      "r"(E.hi), "r"(F.a), "r"(F.lo), "r"(F.hi), "r"(G.a), "r"(G.v), "r"(H.a), "r"(H.v)
-  if constexpr (SUB)
-    asm volatile(OPK_HD_BODY(OPK_SUB64)::OPK_HD_ARGS);
-  else
-    asm volatile(OPK_HD_BODY(OPK_ADD64)::OPK_HD_ARGS);
-#undef OPK_HD_BODY
-#undef OPK_HD_ARGS
+  const uint64_t a = ld_bin(A.a), b = ld_bin(B.a), e = ld_bin(E.a), f = ld_bin(F.a);
+  const uint32_t g = ld_w32(G.a), h = ld_w32(H.a);
+  st_bin(A.a, a + A.d);
+  st_bin(B.a, SUB ? b - B.d : b + B.d);
+  st_bin(E.a, e + E.d);
+  st_bin(F.a, f - F.d);
+  st_w32(G.a, g + G.v);
+  st_w32(H.a, h - H.v);
 }
 
 // Pair (A, B) on one histogram.
 template <bool SUB>
 __device__ __forceinline__ void blk_h(const Upd64 &A, const Upd64 &B) {
   if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u)) return;
-#define OPK_H_BODY(OPB)                                                                        \
-  "{\n\t.reg .u32 a0, a1, b0, b1;\n\t" OPK_LD64("a", "%0") OPK_LD64("b", "%3")                 \
-      OPK_ADD64("a", "%1", "%2") OPB("b", "%4", "%5") OPK_ST64("a", "%0") OPK_ST64("b", "%3") "}"
-  if constexpr (SUB)
-    asm volatile(OPK_H_BODY(OPK_SUB64)::"r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo),
-                 "r"(B.hi));
-  else
-    asm volatile(OPK_H_BODY(OPK_ADD64)::"r"(A.a), "r"(A.lo), "r"(A.hi), "r"(B.a), "r"(B.lo),
-                 "r"(B.hi));
-#undef OPK_H_BODY
+  const uint64_t a = ld_bin(A.a), b = ld_bin(B.a);
+  st_bin(A.a, a + A.d);
+  st_bin(B.a, SUB ? b - B.d : b + B.d);
 }
 
 // Pair (E, F) on a D_i (E adds, F subtracts) with its count words (G, H).
@@ -1792,19 +1658,13 @@ __device__ __forceinline__ void blk_d(const Upd64 &E, const Upd64 &F, const Upd3
   if (!OPK_SMEM_OK(E.a, 8u) || !OPK_SMEM_OK(F.a, 8u) || !OPK_SMEM_OK(G.a, 4u) ||
       !OPK_SMEM_OK(H.a, 4u))
     return;
-  asm volatile("{\n\t.reg .u32 e0, e1, f0, f1, g, h;\n\t" OPK_LD64("e", "%0") OPK_LD64("f", "%3")
-               "ld.shared.u32 g, [%6];\n\t"
-               "ld.shared.u32 h, [%8];\n\t" OPK_ADD64("e", "%1", "%2") OPK_SUB64("f", "%4", "%5")
-               "add.u32 g, g, %7;\n\tsub.u32 h, h, %9;\n\t" OPK_ST64("e", "%0") OPK_ST64("f", "%3")
-               "st.shared.u32 [%6], g;\n\t"
-               "st.shared.u32 [%8], h;\n\t}" ::"r"(E.a),
-               "r"(E.lo), "r"(E.hi), "r"(F.a), "r"(F.lo), "r"(F.hi), "r"(G.a), "r"(G.v), "r"(H.a),
-               "r"(H.v));
+  const uint64_t e = ld_bin(E.a), f = ld_bin(F.a);
+  const uint32_t g = ld_w32(G.a), h = ld_w32(H.a);
+  st_bin(E.a, e + E.d);
+  st_bin(F.a, f - F.d);
+  st_w32(G.a, g + G.v);
+  st_w32(H.a, h - H.v);
 }
-#undef OPK_LD64
-#undef OPK_ST64
-#undef OPK_ADD64
-#undef OPK_SUB64
 
 // One thread's K = 8 histograms and count words, and the updates of one
 // packed word (word format 1; the level field at bits 1..5, so w & 0x3E is
@@ -1822,7 +1682,7 @@ struct Delta8 {
   __device__ __forceinline__ Upd64 add(int k, uint32_t w) const {
     uint32_t lo, hi;
     dh_delta(w, lo, hi);
-    return Upd64{h0 + static_cast<uint32_t>(k) * kHS + (w & 0x3Eu) * (kLS / 2u), lo, hi};
+    return Upd64{h0 + static_cast<uint32_t>(k) * kHS + (w & 0x3Eu) * (kLS / 2u), u64_of(lo, hi)};
   }
   // the second update of a pair whose first is `first`, of word w in
   // histogram k, to be subtracted (SUB) or added; when both land on one bin
@@ -1830,11 +1690,8 @@ struct Delta8 {
   template <bool SUB>
   __device__ __forceinline__ Upd64 second(const Upd64 &first, int k, uint32_t w) const {
     const Upd64 u = add(k, w);
-    const uint64_t d1 = static_cast<uint64_t>(first.hi) << 32 | first.lo;
-    const uint64_t d = static_cast<uint64_t>(u.hi) << 32 | u.lo;
-    const uint64_t x = u.a == first.a ? d1 : 0ull;
-    const uint64_t e = SUB ? d - x : d + x;
-    return Upd64{u.a, static_cast<uint32_t>(e), static_cast<uint32_t>(e >> 32)};
+    const uint64_t x = u.a == first.a ? first.d : 0ull;
+    return Upd64{u.a, SUB ? u.d - x : u.d + x};
   }
   // D_i's count word at word w's level and the word's valid bit moved to
   // D_i's byte
@@ -1952,11 +1809,11 @@ __device__ __forceinline__ void delta8_step(const Delta8<NT> &o, const uint32_t 
     // the even and odd words left over, and the D pairs left over
     if ((R + 1) % 2) {
       A = o.add(0, e[2 * R]);
-      bin_add64(A.a, A.lo, A.hi);
+      bin_add64(A.a, static_cast<uint32_t>(A.d), static_cast<uint32_t>(A.d >> 32));
     }
     if (R % 2) {
       C = o.add(1, e[2 * R - 1]);
-      bin_add64(C.a, C.lo, C.hi);
+      bin_add64(C.a, static_cast<uint32_t>(C.d), static_cast<uint32_t>(C.d >> 32));
     }
 #pragma unroll
     for (int q = NQ; q < 7; ++q) {
