@@ -299,8 +299,8 @@ def run_ours(args):
     launch = op.config()
     if launch.get("path", 0) == 1:
         kernel = "tile_cols_kernel"
-    elif launch["cols_per_thread"] == 8:
-        kernel = "tile_delta8_kernel"
+    elif launch.get("path", 0) >= 2 or launch["cols_per_thread"] == 8:
+        kernel = "tile_deltak_kernel"
     elif launch["cols_per_thread"] > 1 and LEVELS <= 32:
         kernel = "tile_delta_kernel"
     else:
@@ -384,7 +384,7 @@ def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1405_1020_gb300", "csrc")
-    for name in ("oilpaint_device.cuh", "oilpaint_kernels.cu", "oilpaint_delta8.cu"):
+    for name in ("oilpaint_device.cuh", "oilpaint_kernels.cu", "oilpaint_deltak.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

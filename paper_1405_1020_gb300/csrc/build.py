@@ -1,8 +1,9 @@
 """Builds the CUDA library paper_1405_1020_gb300/liboilpaint.so for sm_103a.
 
-Four translation units (the kernels, the eight-columns-per-thread kernels,
-the C ABI, and the allocation-free entry point with its device scratch array)
-are compiled in parallel with nvcc and linked into one shared library with the CUDA runtime linked statically, so
+Five translation units (the kernels, the straight-line difference-histogram
+kernels with four and with eight columns per thread, the C ABI, and the
+allocation-free entry point with its device scratch array) are compiled in
+parallel with nvcc and linked into one shared library with the CUDA runtime linked statically, so
 the library needs nothing but the NVIDIA driver at run time.  The library is
 built in-tree (the package directory) and git-ignored.
 """
@@ -18,8 +19,11 @@ PKG = os.path.dirname(CSRC)
 ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liboilpaint.so")
-SOURCES = ["oilpaint_kernels.cu", "oilpaint_delta8.cu", "oilpaint_api.cu", "oilpaint_noalloc.cu"]
-HEADERS = ["oilpaint_device.cuh", "oilpaint_internal.h"]
+SOURCES = [
+    "oilpaint_kernels.cu", "oilpaint_delta4.cu", "oilpaint_delta8.cu", "oilpaint_api.cu",
+    "oilpaint_noalloc.cu",
+]
+HEADERS = ["oilpaint_device.cuh", "oilpaint_internal.h", "oilpaint_deltak.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", INCLUDE, "-I", CSRC]

@@ -152,7 +152,7 @@ uint32_t threads_of(const op_config_t &c) {
 
 // Range checks that need no device.
 bool config_in_range(const op_config_t &c) {
-  if (c.path > 1u) return false;
+  if (c.path > 3u) return false;
   if (c.cols_per_thread != 0 && c.cols_per_thread != 1 && c.cols_per_thread != 2 &&
       c.cols_per_thread != 4 && c.cols_per_thread != 8)
     return false;
@@ -160,7 +160,10 @@ bool config_in_range(const op_config_t &c) {
   if (c.tile_w % cpt) return false;
   const uint32_t nt = c.tile_w / cpt;
   if (nt != 32 && nt != 64 && nt != 96 && nt != 128) return false;
-  if (cpt == 8u && (nt > 64 || c.path != 0u)) return false;  // 32 or 64 threads x 8
+  // the straight-line paths (2, 3): 4 or 8 columns of 32 or 64 threads; eight
+  // columns exist only there (path 0 with 8 columns means path 3)
+  if ((c.path >= 2u || cpt == 8u) && (nt > 64 || (cpt != 4u && cpt != 8u))) return false;
+  if (cpt == 8u && c.path == 1u) return false;
   if (c.path == 1u && (cpt == 4u || nt == 96u)) return false;  // 1, 2 or 4 warps x 32 or 64
   if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4) return false;
   return c.tile_h <= OP_MAX_DIM;
@@ -215,8 +218,9 @@ int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
   if (!config_in_range(c)) return OP_E_INVALID;
   const opk::Geometry g = geometry_of(c, r, L, 1u);
   // the path and columns asked for must apply (K columns and the column
-  // histograms need L <= 32)
-  if (g.path != static_cast<int>(c.path) || g.kcols != cols_per_thread(c)) return OP_E_UNSUPPORTED;
+  // histograms need L <= 32, the straight-line path its radius range)
+  const int want_path = (c.path == 0u && cols_per_thread(c) == 8) ? 3 : static_cast<int>(c.path);
+  if (g.path != want_path || g.kcols != cols_per_thread(c)) return OP_E_UNSUPPORTED;
   if (g.boxw > opk::kMaxBoxWords) return OP_E_UNSUPPORTED;
   if (smem_of(g, c, r, L) > di.smem_optin - 1024u) return OP_E_UNSUPPORTED;
   return OP_OK;

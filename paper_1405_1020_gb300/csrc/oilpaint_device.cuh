@@ -98,9 +98,10 @@ constexpr uint32_t kModeLiteral = 2u;
 // (5-bit level field next to the valid bit).
 constexpr int kDeltaMaxRadius = 44;
 constexpr uint32_t kDeltaMaxLevels = 32;
-// Eight columns per thread (run_tile_delta8): variant-A bins, 4 <= r <= 15.
-constexpr int kDelta8MinRadius = 4;
-constexpr int kDelta8MaxRadius = 15;
+// The straight-line difference-histogram path (run_tile_deltak): variant-A
+// bins, K/2 <= r <= 15 for K = 4 or 8 columns per thread (r >= 4 for K = 8).
+constexpr int kDeltaKMaxRadius = 15;
+__host__ __device__ constexpr int deltak_min_radius(int k) { return k == 8 ? 4 : 2; }
 
 // Halo boxes up to kMaxBox2dWords words wide are 2-D TMA copies; wider ones
 // (up to kMaxBoxWords) use the 3-D view of the packed image (tma_load_3d),
@@ -1577,8 +1578,6 @@ __device__ bool run_tile_delta(const ImgDesc &d, const CUtensorMap *tmap, int x0
 // histograms He, Ho, D_1..D_7 numbered 0..8, then the DC words
 // [level][word][thread].
 
-constexpr int kD8Hists = 9;
-
 // A 64-bit bin update (shared address, delta) and a 32-bit one.
 struct Upd64 {
   uint32_t a;
@@ -1666,19 +1665,25 @@ __device__ __forceinline__ void blk_d(const Upd64 &E, const Upd64 &F, const Upd3
   st_w32(H.a, h - H.v);
 }
 
-// One thread's K = 8 histograms and count words, and the updates of one
-// packed word (word format 1; the level field at bits 1..5, so w & 0x3E is
-// twice the level).
-template <int NT>
-struct Delta8 {
+// One thread's histograms and count words for K output columns per thread
+// (K = 4 or 8), the window histogram split into NB = 1 or 2 parts (by the
+// parity of the window column), and the updates of one packed word (word
+// format 1; the level field at bits 1..5, so w & 0x3E is twice the level).
+// Histograms 0 .. NB-1 are the window histogram's parts, NB - 1 + i is D_i;
+// the DC words hold the counts of D_1 .. D_4 (word 0) and D_5 .. D_7 (word 1).
+template <int NT, int K, int NB>
+struct DeltaK {
+  static_assert((K == 4 || K == 8) && (NB == 1 || NB == 2), "K columns, NB window parts");
+  static constexpr int kHists = NB + K - 1;
+  static constexpr int kDCWords = (K - 1 + 3) / 4;
   static constexpr uint32_t kHS = NT * 8u;                   // between histograms
-  static constexpr uint32_t kLS = kD8Hists * kHS;            // between levels (bins)
-  static constexpr uint32_t kDLS = NT * 8u;                  // between levels (DC words)
-  static constexpr uint32_t kDW = NT * 4u;                   // between a level's two DC words
-  uint32_t h0;   // He's level-0 bin of this thread
+  static constexpr uint32_t kLS = kHists * kHS;              // between levels (bins)
+  static constexpr uint32_t kDW = NT * 4u;                   // between a level's DC words
+  static constexpr uint32_t kDLS = kDCWords * kDW;           // between levels (DC words)
+  uint32_t h0;   // the first window part's level-0 bin of this thread
   uint32_t dc0;  // this thread's first DC word of level 0
 
-  // +w in histogram k (0 He, 1 Ho, 1 + i D_i)
+  // +w in histogram k
   __device__ __forceinline__ Upd64 add(int k, uint32_t w) const {
     uint32_t lo, hi;
     dh_delta(w, lo, hi);
@@ -1702,25 +1707,26 @@ struct Delta8 {
   // D_i: +a -b (sums and count)
   __device__ __forceinline__ void dpair(int i, uint32_t a, uint32_t b, Upd64 &E, Upd64 &F,
                                         Upd32 &G, Upd32 &H) const {
-    E = add(1 + i, a);
-    F = second<true>(E, 1 + i, b);
+    E = add(NB - 1 + i, a);
+    F = second<true>(E, NB - 1 + i, b);
     G = cnt(i, a);
     H = cnt(i, b);
     if (H.a == G.a) H.v -= G.v;
   }
 };
 
-// One step of run_tile_delta8 from the ring words 0 .. 2R+7 (read as
-// 16-byte groups) of the entering row pe and (RM) the leaving row pl.
-// Word j feeds the window histogram when j <= 2R (He for even j, Ho for
-// odd j), D_{j+1} negatively (its left column leaves the window) when
-// j <= 6, and D_{j-2R} positively (its right column enters) when j >= 2R+1;
-// with R >= 4 the words 0..7 all lie in the window.  While the window fills
-// (RM false) rows only enter.
-template <int NT, int R, bool RM>
-__device__ __forceinline__ void delta8_step(const Delta8<NT> &o, const uint32_t *pe,
+// One step of run_tile_deltak from the ring words 0 .. 2R+K-1 (read as
+// 16-byte groups) of the entering row pe and (RM) the leaving row pl.  Word j
+// feeds the window histogram when j <= 2R (with NB = 2: part 0 for even j,
+// part 1 for odd j), D_{j+1} negatively (its left column leaves the window)
+// when j <= K-2, and D_{j-2R} positively (its right column enters) when
+// j >= 2R+1; R >= K/2 keeps the words 0 .. K-2 inside the window and apart
+// from the right words.  While the window fills (RM false) rows only enter.
+template <int NT, int K, int NB, int R, bool RM>
+__device__ __forceinline__ void deltak_step(const DeltaK<NT, K, NB> &o, const uint32_t *pe,
                                             const uint32_t *pl) {
-  constexpr int NG = (2 * R + 11) / 4;  // 16-byte groups covering words 0 .. 2R+7
+  constexpr int NG = (2 * R + K + 3) / 4;  // 16-byte groups covering words 0 .. 2R+K-1
+  constexpr int ND = 2 * (K - 1);          // D pairs of a step
   uint32_t e[4 * NG], l[4 * NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
@@ -1742,103 +1748,145 @@ __device__ __forceinline__ void delta8_step(const Delta8<NT> &o, const uint32_t 
   Upd64 A, B, C, D, E, F;
   Upd32 G, H;
   if constexpr (RM) {
-    // D pair k: the left words (k < 7: D_{k+1} +l_k -e_k), then the right
-    // words (k >= 7: D_{k-6} +e -l at word 2R + k - 6)
+    // D pair k: the left words (k < K-1: D_{k+1} +l_k -e_k), then the right
+    // words (k >= K-1: D_{k-K+2} +e -l at word 2R + k - K + 2)
     auto dp = [&](int k) {
-      if (k < 7)
+      if (k < K - 1)
         o.dpair(k + 1, l[k], e[k], E, F, G, H);
       else
-        o.dpair(k - 6, e[2 * R + k - 6], l[2 * R + k - 6], E, F, G, H);
+        o.dpair(k - K + 2, e[2 * R + k - K + 2], l[2 * R + k - K + 2], E, F, G, H);
     };
-    // block b: He pair at word 2b, Ho pair at word 2b+1 (b < R), D pair b
+    if constexpr (NB == 2) {
+      // block b: part-0 pair at word 2b, part-1 pair at word 2b+1 (b < R), D pair b
 #pragma unroll
-    for (int b = 0; b <= R; ++b) {
-      A = o.add(0, e[2 * b]);
-      B = o.template second<true>(A, 0, l[2 * b]);
-      if (b < R) {
-        C = o.add(1, e[2 * b + 1]);
-        D = o.template second<true>(C, 1, l[2 * b + 1]);
-        if (b < 14) {
+      for (int b = 0; b <= R; ++b) {
+        A = o.add(0, e[2 * b]);
+        B = o.template second<true>(A, 0, l[2 * b]);
+        if (b < R) {
+          C = o.add(1, e[2 * b + 1]);
+          D = o.template second<true>(C, 1, l[2 * b + 1]);
+          if (b < ND) {
+            dp(b);
+            blk_hhd<true>(A, B, C, D, E, F, G, H);
+          } else {
+            blk_hh<true>(A, B, C, D);
+          }
+        } else if (b < ND) {
           dp(b);
-          blk_hhd<true>(A, B, C, D, E, F, G, H);
+          blk_hd<true>(A, B, E, F, G, H);
         } else {
-          blk_hh<true>(A, B, C, D);
+          blk_h<true>(A, B);
         }
-      } else if (b < 14) {
-        dp(b);
-        blk_hd<true>(A, B, E, F, G, H);
-      } else {
-        blk_h<true>(A, B);
       }
-    }
 #pragma unroll
-    for (int k = R + 1; k < 14; ++k) {
-      dp(k);
-      blk_d(E, F, G, H);
+      for (int k = R + 1; k < ND; ++k) {
+        dp(k);
+        blk_d(E, F, G, H);
+      }
+    } else {
+      // block j: the window pair at word j, D pair j
+#pragma unroll
+      for (int j = 0; j <= 2 * R; ++j) {
+        A = o.add(0, e[j]);
+        B = o.template second<true>(A, 0, l[j]);
+        if (j < ND) {
+          dp(j);
+          blk_hd<true>(A, B, E, F, G, H);
+        } else {
+          blk_h<true>(A, B);
+        }
+      }
+#pragma unroll
+      for (int k = 2 * R + 1; k < ND; ++k) {
+        dp(k);
+        blk_d(E, F, G, H);
+      }
     }
   } else {
-    // He pairs of even words (4q, 4q + 2), Ho pairs of odd words (4q + 1,
-    // 4q + 3), D pair q: D_{q+1} +(word 2R + q + 1) -(word q)
-    constexpr int NPE = (R + 1) / 2, NPO = R / 2;
-    constexpr int NQ = NPE > NPO ? NPE : NPO;
+    // D pair q: D_{q+1} +(word 2R + q + 1) -(word q)
+    if constexpr (NB == 2) {
+      // part-0 pairs of even words (4q, 4q + 2), part-1 pairs of odd words
+      // (4q + 1, 4q + 3)
+      constexpr int NPE = (R + 1) / 2, NPO = R / 2;
+      constexpr int NQ = NPE > NPO ? NPE : NPO;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const bool he = q < NPE, ho = q < NPO, hd = q < 7;
-      if (he) {
-        A = o.add(0, e[4 * q]);
-        B = o.template second<false>(A, 0, e[4 * q + 2]);
+      for (int q = 0; q < NQ; ++q) {
+        const bool he = q < NPE, ho = q < NPO, hd = q < K - 1;
+        if (he) {
+          A = o.add(0, e[4 * q]);
+          B = o.template second<false>(A, 0, e[4 * q + 2]);
+        }
+        if (ho) {
+          C = o.add(1, e[4 * q + 1]);
+          D = o.template second<false>(C, 1, e[4 * q + 3]);
+        }
+        if (hd) o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
+        if (he && ho && hd)
+          blk_hhd<false>(A, B, C, D, E, F, G, H);
+        else if (he && ho)
+          blk_hh<false>(A, B, C, D);
+        else if (he && hd)
+          blk_hd<false>(A, B, E, F, G, H);
+        else if (ho && hd)
+          blk_hd<false>(C, D, E, F, G, H);
+        else if (he)
+          blk_h<false>(A, B);
+        else if (ho)
+          blk_h<false>(C, D);
       }
-      if (ho) {
-        C = o.add(1, e[4 * q + 1]);
-        D = o.template second<false>(C, 1, e[4 * q + 3]);
+      if ((R + 1) % 2) {
+        A = o.add(0, e[2 * R]);
+        bin_add64(A.a, static_cast<uint32_t>(A.d), static_cast<uint32_t>(A.d >> 32));
       }
-      if (hd) o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
-      if (he && ho && hd)
-        blk_hhd<false>(A, B, C, D, E, F, G, H);
-      else if (he && ho)
-        blk_hh<false>(A, B, C, D);
-      else if (he && hd)
-        blk_hd<false>(A, B, E, F, G, H);
-      else if (ho && hd)
-        blk_hd<false>(C, D, E, F, G, H);
-      else if (he)
-        blk_h<false>(A, B);
-      else if (ho)
-        blk_h<false>(C, D);
-    }
-    // the even and odd words left over, and the D pairs left over
-    if ((R + 1) % 2) {
+      if (R % 2) {
+        C = o.add(1, e[2 * R - 1]);
+        bin_add64(C.a, static_cast<uint32_t>(C.d), static_cast<uint32_t>(C.d >> 32));
+      }
+#pragma unroll
+      for (int q = NQ; q < K - 1; ++q) {
+        o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
+        blk_d(E, F, G, H);
+      }
+    } else {
+      // window pairs (2q, 2q + 1), then the last window word 2R
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        A = o.add(0, e[2 * q]);
+        B = o.template second<false>(A, 0, e[2 * q + 1]);
+        if (q < K - 1) {
+          o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
+          blk_hd<false>(A, B, E, F, G, H);
+        } else {
+          blk_h<false>(A, B);
+        }
+      }
       A = o.add(0, e[2 * R]);
       bin_add64(A.a, static_cast<uint32_t>(A.d), static_cast<uint32_t>(A.d >> 32));
-    }
-    if (R % 2) {
-      C = o.add(1, e[2 * R - 1]);
-      bin_add64(C.a, static_cast<uint32_t>(C.d), static_cast<uint32_t>(C.d >> 32));
-    }
 #pragma unroll
-    for (int q = NQ; q < 7; ++q) {
-      o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
-      blk_d(E, F, G, H);
+      for (int q = R; q < K - 1; ++q) {
+        o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
+        blk_d(E, F, G, H);
+      }
     }
   }
 }
 
-// K = 8 output columns per thread (see above); the tile [x0, x0 + 8 NT) x
+// K output columns per thread (see above); the tile [x0, x0 + K NT) x
 // [y0, y1), x0 - R a multiple of 4 (tiles start at d.xshift), so every
 // thread's window starts on a 16-byte boundary of the ring.  Pixels outside
 // the image are zero words (TMA fill, and the zeroed row padding), whose
 // delta is zero.
-template <int NT, int R>
-__device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
+template <int NT, int K, int NB, int R>
+__device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0, int y1,
                                 const RingCfg &rc, const SmemMap &sm, uint32_t &chunk_ctr,
                                 uint32_t *err, uint64_t timeout_ns, uint32_t *diag = nullptr,
                                 bool tmap_global = false) {
-  using O = Delta8<NT>;
+  using O = DeltaK<NT, K, NB>;
   const int t = threadIdx.x;
   const uint32_t L = d.L;
-  const int xa = x0 + 8 * t;
+  const int xa = x0 + K * t;
   const int xs = x0 - R;  // a multiple of 4 by the choice of d.xshift
-  const int jl = 8 * t;
+  const int jl = K * t;
   const int E0 = y0 - R;
   const int nsteps = (y1 - y0) + 2 * R;
   O o;
@@ -1846,10 +1894,11 @@ __device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x
   o.dc0 = sm.sums + L * O::kLS + static_cast<uint32_t>(t) * 4u;
   for (uint32_t lv = 0; lv < L; ++lv) {
 #pragma unroll
-    for (int i = 0; i < kD8Hists; ++i)
+    for (int i = 0; i < O::kHists; ++i)
       sts_zero64(o.h0 + lv * O::kLS + static_cast<uint32_t>(i) * O::kHS);
-    sts_zero32(o.dc0 + lv * O::kDLS);
-    sts_zero32(o.dc0 + lv * O::kDLS + O::kDW);
+#pragma unroll
+    for (int w = 0; w < O::kDCWords; ++w)
+      sts_zero32(o.dc0 + lv * O::kDLS + static_cast<uint32_t>(w) * O::kDW);
   }
 
   return ring_pass(
@@ -1860,59 +1909,64 @@ __device__ bool run_tile_delta8(const ImgDesc &d, const CUtensorMap *tmap, int x
         const int y = E0 + s - R;
         const uint32_t *pe = rowe + jl;
         const uint32_t *pl = rowl + jl;
-        uint32_t alpha[8];
+        uint32_t alpha[K];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < K; ++i) {
           const int x = xa + i;
           alpha[i] = (out_now && d.bpp == 4 && x >= d.ox0 && x < d.ox1) ? load_alpha(d, x, y) : 0u;
         }
         if (rm)
-          delta8_step<NT, R, true>(o, pe, pl);
+          deltak_step<NT, K, NB, R, true>(o, pe, pl);
         else
-          delta8_step<NT, R, false>(o, pe, pl);
+          deltak_step<NT, K, NB, R, false>(o, pe, pl);
         if (!out_now) return;
         // keys (count << 22) | (31 - level): the lowest level wins ties under max
-        uint32_t best[8];
+        uint32_t best[K];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) best[i] = 0u;
+        for (int i = 0; i < K; ++i) best[i] = 0u;
 #pragma unroll 4
         for (uint32_t lv = 0; lv < L; ++lv) {
-          // He's and Ho's low words: the counts sit in bits 0..9, so the low
-          // 10 bits of the sum are the window's count
-          const uint32_t c = lds_u32(o.h0 + lv * O::kLS) + lds_u32(o.h0 + lv * O::kLS + O::kHS);
-          const uint32_t da = lds_u32(o.dc0 + lv * O::kDLS);
-          const uint32_t db = lds_u32(o.dc0 + lv * O::kDLS + O::kDW);
+          // the window parts' low words: the counts sit in bits 0..9, so the
+          // low 10 bits of the sum are the window's count
+          uint32_t c = lds_u32(o.h0 + lv * O::kLS);
+          if (NB == 2) c += lds_u32(o.h0 + lv * O::kLS + O::kHS);
           const uint32_t k0 = (c << 22) | (31u - lv);
           best[0] = max(best[0], k0);
-          // byte k of pa: 128 + the count of D_1 + .. + D_{k+1}; of pb:
-          // 128 + the count of D_5 + .. + D_{k+5}
-          const uint32_t pa = da * 0x01010101u + 0x80808080u;
-          const uint32_t pb = db * 0x01010101u + 0x80808080u;
-          const uint32_t kb = k0 - (128u << 22);
-          const uint32_t k4 = kb + ((pa >> 24) << 22);
+          // byte k of p: 128 + the count of D_{4w+1} + .. + D_{4w+k+1} for DC
+          // word w; the key of window 4w + k + 1 adds that prefix to the key
+          // of window 4w
+          uint32_t kw = k0;
 #pragma unroll
-          for (int i = 1; i <= 3; ++i)
-            best[i] = max(best[i], kb + (((pa >> (8 * (i - 1))) & 0xFFu) << 22));
-          best[4] = max(best[4], k4);
-          const uint32_t kb4 = k4 - (128u << 22);
+          for (int w = 0; w < O::kDCWords; ++w) {
+            const uint32_t p =
+                lds_u32(o.dc0 + lv * O::kDLS + static_cast<uint32_t>(w) * O::kDW) * 0x01010101u +
+                0x80808080u;
+            const uint32_t kb = kw - (128u << 22);
 #pragma unroll
-          for (int i = 5; i <= 7; ++i)
-            best[i] = max(best[i], kb4 + (((pb >> (8 * (i - 5))) & 0xFFu) << 22));
+            for (int k = 0; k < 4; ++k) {
+              const int i = 4 * w + k + 1;
+              if (i < K) {
+                const uint32_t ki = kb + (((p >> (8 * k)) & 0xFFu) << 22);
+                best[i] = max(best[i], ki);
+                if (k == 3) kw = ki;
+              }
+            }
+          }
         }
         // the reciprocals first, so that their latency overlaps the loads
         // of the winning bins
-        uint32_t mulv[8];
+        uint32_t mulv[K];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) mulv[i] = rcp_of(best[i] >> 22);
+        for (int i = 0; i < K; ++i) mulv[i] = rcp_of(best[i] >> 22);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < K; ++i) {
           const int x = xa + i;
           if (x < d.ox0 || x >= d.ox1) continue;
           const uint32_t m = 31u - (best[i] & 31u);
           if ((best[i] >> 22) == 0u) continue;  // no level below L (literal mode only)
           uint64_t v = 0;
 #pragma unroll
-          for (int j = 0; j < 2 + i; ++j) {  // He, Ho, D_1 .. D_i
+          for (int j = 0; j < NB + i; ++j) {  // the window parts, D_1 .. D_i
             uint32_t lo, hi;
             lds_v2(o.h0 + m * O::kLS + static_cast<uint32_t>(j) * O::kHS, lo, hi);
             v += static_cast<uint64_t>(hi) << 32 | lo;

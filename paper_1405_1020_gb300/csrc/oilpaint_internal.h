@@ -46,10 +46,13 @@ inline bool delta_eligible(int r, uint32_t L) {
   return r >= 0 && r <= kDeltaMaxRadius && L >= 1 && L <= kDeltaMaxLevels;
 }
 
-// Eight columns per thread: variant-A bins, and r >= 4 so that the left
-// difference words 0..6 all lie inside the window.
-inline bool delta8_eligible(int r, uint32_t L) {
-  return r >= kDelta8MinRadius && r <= kDelta8MaxRadius && L >= 1 && L <= kDeltaMaxLevels;
+// The straight-line difference-histogram path (paths 2 and 3; K = 4 or 8
+// columns per thread, one kernel per radius): variant-A bins, L <= 32, and
+// r >= K/2 so that the left difference words 0 .. K-2 lie inside the window
+// and apart from the right ones.
+inline bool deltak_eligible(int k, int r, uint32_t L) {
+  return (k == 4 || k == 8) && r >= deltak_min_radius(k) && r <= kDeltaKMaxRadius && L >= 1 &&
+         L <= kDeltaMaxLevels;
 }
 
 // Box width (words) of a difference-histogram tile: thread t reads K-word
@@ -62,10 +65,12 @@ inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
 }
 
 // Launch geometry of one image: path (0 histograms per thread, 1 column
-// histograms), threads per CTA, columns per thread (path 0: 2 or 4 only where
-// the difference-histogram path applies; path 1: outputs per warp / 32), tile
-// width, the x of the first tile, tiles per row, the halo box width, the
-// histogram variant and the packed word format.
+// histograms, 2 and 3 the straight-line difference histograms with the
+// window histogram in one or two parts), threads per CTA, columns per thread
+// (path 0: 2 or 4 only where the difference-histogram path applies; path 1:
+// outputs per warp / 32; paths 2 and 3: 4 or 8), tile width, the x of the
+// first tile, tiles per row, the halo box width, the histogram variant and
+// the packed word format.
 struct Geometry {
   int path;
   uint32_t nt;
@@ -83,6 +88,23 @@ inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, u
   Geometry g;
   g.nt = nt;
   g.variant = variant_for_radius(r);
+  // eight columns per thread exist only on the straight-line path (in two parts)
+  if (path == 0 && kcols_wanted == 8) path = 3;
+  if (path == 2 || path == 3) {
+    g.path = deltak_eligible(kcols_wanted, r, L) ? path : 0;
+    if (g.path) {
+      g.kcols = kcols_wanted;
+      g.tile_w = nt * static_cast<uint32_t>(g.kcols);
+      g.xshift = (r & 3) ? (r & 3) - 4 : 0;
+      g.boxw = delta_box_width(nt, g.kcols, r);
+      g.fmt = 1u;
+      g.tiles_x = static_cast<uint32_t>((static_cast<int64_t>(w) - g.xshift + g.tile_w - 1) /
+                                        g.tile_w);
+      return g;
+    }
+    path = 0;
+    if (kcols_wanted == 8) kcols_wanted = 1;
+  }
   g.path = (path == 1 && delta_eligible(r, L)) ? 1 : 0;
   if (g.path == 1) {
     g.kcols = kcols_wanted == 2 ? 2 : 1;
@@ -90,10 +112,7 @@ inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, u
     g.xshift = (r & 3) ? (r & 3) - 4 : 0;
     g.boxw = (g.tile_w + 2u * static_cast<uint32_t>(r) + 3u) & ~3u;
   } else {
-    g.kcols = (kcols_wanted == 8 ? delta8_eligible(r, L)
-                                 : (kcols_wanted > 1 && delta_eligible(r, L)))
-                  ? kcols_wanted
-                  : 1;
+    g.kcols = (kcols_wanted > 1 && kcols_wanted <= 4 && delta_eligible(r, L)) ? kcols_wanted : 1;
     g.tile_w = nt * static_cast<uint32_t>(g.kcols);
     if (g.kcols > 1) {
       // first tile at x0 = xshift with x0 - r a multiple of 4
@@ -130,14 +149,18 @@ inline int pack_grid_for(uint32_t rows, int sms) {
   return static_cast<int>(per_block ? (rows + per_block - 1u) / per_block : 1u);
 }
 
+// Histogram bytes of a CTA on the straight-line path: per level and thread
+// nb + k - 1 histograms of 8-byte bins and (k - 1)/4 rounded up count words.
+inline size_t deltak_hist_bytes(uint32_t nt, int k, int nb, uint32_t L) {
+  return static_cast<size_t>((nb + k - 1) * 8 + (k - 1 + 3) / 4 * 4) * L * nt;
+}
+
 // Histogram bytes of a CTA on path kcols (1: one histogram of L + 1 levels
 // per thread, bins of the variant's size; 2 or 4: kcols histograms, one
 // more where the window histogram is split, of L levels per thread, bins of
-// 8 bytes (variant A) or 8 + 2 bytes (variant B); 8: nine histograms of
-// 8-byte bins and two count words per level and thread).
+// 8 bytes (variant A) or 8 + 2 bytes (variant B)).
 inline size_t hist_bytes(uint32_t nt, int kcols, uint32_t L, int variant) {
-  // (column path: cols_hist_bytes)
-  if (kcols == 8) return static_cast<size_t>(kD8Hists * 8u + 8u) * L * nt;
+  // (column path: cols_hist_bytes; straight-line path: deltak_hist_bytes)
   if (kcols > 1) {
     const size_t nh = static_cast<size_t>(kcols) + static_cast<size_t>(hsplit(kcols, variant)) - 1u;
     // variant B: 8-byte sums and a 16-bit count per bin
@@ -214,14 +237,19 @@ cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
 cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStream_t s);
-// Eight columns per thread (oilpaint_delta8.cu): nt = 32 or 64 threads,
-// d.r in kDelta8MinRadius .. kDelta8MaxRadius (one kernel per radius),
-// variant A, d.L <= 32; cudaErrorInvalidValue otherwise.
-cudaError_t launch_delta8(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
+// The straight-line difference-histogram path (paths 2 and 3, d.kcols = 4
+// or 8, nt = 32 or 64 threads, one kernel per radius in K's range, variant
+// A, d.L <= 32); cudaErrorInvalidValue otherwise.
+cudaError_t launch_deltak(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
                           const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
                           uint64_t timeout_ns, cudaStream_t s);
-cudaError_t set_delta8_smem_limit(size_t bytes);
-int delta8_occupancy(uint32_t nt, size_t smem);
+cudaError_t set_deltak_smem_limit(size_t bytes);
+int deltak_occupancy(uint32_t nt, int k, int nb, size_t smem);
+// One straight-line kernel (nullptr outside the tables): nt threads, nb
+// window parts, radius r; defined in oilpaint_delta4.cu / oilpaint_delta8.cu.
+using DeltaKFn = void (*)(const CUtensorMap, const ImgDesc, const RingCfg, uint32_t *, uint64_t);
+DeltaKFn deltak_kernel_k4(uint32_t nt, int nb, int r);
+DeltaKFn deltak_kernel_k8(uint32_t nt, int nb, int r);
 // Checked builds: the bounds-check violation bits since the last call
 // (1 shared memory, 2 image pixels, 4 TMA copy), cleared; 0 otherwise.
 cudaError_t take_check_error(uint32_t *bits);
@@ -237,9 +265,11 @@ int tile_occupancy_cols(uint32_t nt, int twk, int variant, size_t smem);
 
 // Histogram bytes and resident CTAs of an image's single-image kernel.
 inline size_t geometry_hist_bytes(const Geometry &g, int r, uint32_t L) {
+  if (g.path == 2 || g.path == 3) return deltak_hist_bytes(g.nt, g.kcols, g.path - 1, L);
   return g.path == 1 ? cols_hist_bytes(g, r, L) : hist_bytes(g.nt, g.kcols, L, g.variant);
 }
 inline int geometry_occupancy(const Geometry &g, size_t smem) {
+  if (g.path == 2 || g.path == 3) return deltak_occupancy(g.nt, g.kcols, g.path - 1, smem);
   return g.path == 1 ? tile_occupancy_cols(g.nt, g.kcols, g.variant, smem)
                      : tile_occupancy(g.nt, false, g.kcols, g.variant, smem);
 }

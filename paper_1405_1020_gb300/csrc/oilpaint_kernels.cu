@@ -8,8 +8,8 @@
 //                                           column per thread (NT threads)
 //   tile_delta_kernel<NT, K, VAR>           one CTA per output tile, K output
 //                                           columns per thread through
-//                                           difference histograms (K = 8:
-//                                           tile_delta8_kernel, in
+//                                           difference histograms (one kernel
+//                                           per radius instead: oilpaint_delta4.cu,
 //                                           oilpaint_delta8.cu)
 //   tile_cols_kernel<NW, TWK, VAR>          one CTA per output tile, column
 //                                           histograms swept by NW warps
@@ -252,7 +252,8 @@ cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
     }
     return cudaGetLastError();
   }
-  if (kcols == 8) return launch_delta8(nt, d, map, rc, grid, smem, err, timeout_ns, s);
+  if (d.path == 2u || d.path == 3u)
+    return launch_deltak(nt, d, map, rc, grid, smem, err, timeout_ns, s);
   if (kcols != 1 && kcols != 2 && kcols != 4) return cudaErrorInvalidValue;
   switch (nt) {
     case 32:
@@ -368,7 +369,7 @@ static cudaError_t set_limit_cols(int b) {
 cudaError_t set_tile_smem_limit(size_t bytes) {
   const int b = static_cast<int>(bytes);
   cudaError_t e;
-  if ((e = set_delta8_smem_limit(bytes)) != cudaSuccess) return e;
+  if ((e = set_deltak_smem_limit(bytes)) != cudaSuccess) return e;
   if ((e = set_limit_cols<1>(b)) != cudaSuccess) return e;
   if ((e = set_limit_cols<2>(b)) != cudaSuccess) return e;
   if ((e = set_limit_cols<4>(b)) != cudaSuccess) return e;
@@ -391,7 +392,6 @@ static int occupancy_n(bool persistent, int kcols, int variant, size_t smem) {
     if (kcols == 2) return occ_of(persistent_kernel<NT, 2>, NT, smem);
     return occ_of(persistent_kernel<NT, 1>, NT, smem);
   }
-  if (kcols == 8) return variant == kVarA ? delta8_occupancy(NT, smem) : 0;
   if (kcols == 4)
     return variant == kVarA ? occ_of(tile_delta_kernel<NT, 4, kVarA>, NT, smem)
                             : occ_of(tile_delta_kernel<NT, 4, kVarB>, NT, smem);
@@ -419,6 +419,46 @@ int tile_occupancy_cols(uint32_t nt, int twk, int variant, size_t smem) {
     case 128: return occupancy_cols<4>(twk, variant, smem);
     default: return 0;
   }
+}
+
+static DeltaKFn deltak_fn(uint32_t nt, int k, int nb, int r) {
+  return k == 4 ? deltak_kernel_k4(nt, nb, r) : k == 8 ? deltak_kernel_k8(nt, nb, r) : nullptr;
+}
+
+cudaError_t launch_deltak(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
+                          const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
+                          uint64_t timeout_ns, cudaStream_t s) {
+  const DeltaKFn f = deltak_fn(nt, static_cast<int>(d.kcols), static_cast<int>(d.path) - 1,
+                                   d.r);
+  if (!f || d.variant != static_cast<uint32_t>(kVarA) || d.L > kDeltaMaxLevels)
+    return cudaErrorInvalidValue;
+  f<<<grid, nt, smem, s>>>(map, d, rc, err, timeout_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t set_deltak_smem_limit(size_t bytes) {
+  for (int k : {4, 8})
+    for (uint32_t nt : {32u, 64u})
+      for (int nb : {1, 2})
+        for (int r = deltak_min_radius(k); r <= kDeltaKMaxRadius; ++r) {
+          const cudaError_t e =
+              cudaFuncSetAttribute(deltak_fn(nt, k, nb, r),
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(bytes));
+          if (e != cudaSuccess) return e;
+        }
+  return cudaSuccess;
+}
+
+int deltak_occupancy(uint32_t nt, int k, int nb, size_t smem) {
+  // the same resources at every radius of one (nt, k, nb)
+  const DeltaKFn f = deltak_fn(nt, k, nb, kDeltaKMaxRadius);
+  if (!f) return 0;
+  int n = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, static_cast<int>(nt), smem) ==
+                 cudaSuccess
+             ? n
+             : 0;
 }
 
 int tile_occupancy(uint32_t nt, bool persistent, int kcols, int variant, size_t smem) {

@@ -176,66 +176,82 @@ def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
         assert smem > 226 * 1024, (cfg, r, L, smem)
 
 
-def _delta8_cases(n=64, seed=17):
-    """Eight columns per thread (4 <= r <= 15, L <= 32): both r parities (the
-    right difference words start at word 1 or 3 of a 16-byte group), widths
-    around the 256- and 512-column tiles, one-row and short images, both
-    level modes and literal mode, tile heights, halo chunk heights and
-    prefetch depths."""
+def _straight_cases(n=96, seed=17):
+    """The straight-line difference-histogram path (one kernel per radius):
+    4 or 8 columns per thread, the window histogram in one part (path 2) or
+    two (path 3; eight columns on path 0 mean path 3), every radius of each
+    width's range and both parities (where in a 16-byte group the right
+    difference words start), widths around the tile widths, one-row and short
+    images, both level modes and literal mode, tile heights, halo chunk
+    heights and prefetch depths."""
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(n):
-        w = int(rng.choice([1, 3, 8, 9, 31, 200, 255, 256, 257, 263, 500, 511, 512, 513, 700, 1030]))
+        K = 8 if k % 2 else 4
+        path = int(rng.choice([0, 2, 3])) if K == 8 else int(rng.choice([2, 3]))
+        w = int(rng.choice([1, 3, 8, 9, 31, 127, 129, 200, 255, 256, 257, 263, 500, 511, 512,
+                            513, 700, 1030]))
         h = int(rng.choice([1, 2, 5, 16, 33, 90, 161]))
-        r = int(rng.integers(4, 16))
+        r = int(rng.integers(4 if K == 8 else 2, 16))
         L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32]))
         bpp = int(rng.choice([3, 4]))
         pad = int(rng.choice([0, 1, 4, 13]))
         mode = int(rng.choice([0, 1, B.OP_LITERAL, B.OP_LITERAL | 1]))
         nt = int(rng.choice([32, 64]))
-        cfg = {"tile_w": nt * 8, "tile_h": int(rng.choice([0, 1, 3, 16, 64])),
+        cfg = {"tile_w": nt * K, "tile_h": int(rng.choice([0, 1, 3, 16, 64])),
                "chunk_rows": int(rng.choice([1, 2, 3, 8])), "prefetch": int(rng.integers(1, 3)),
-               "cols_per_thread": 8}
+               "cols_per_thread": K, "path": path}
         cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
     return cases
 
 
-@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _delta8_cases())
-def test_fuzz_eight_columns(k, w, h, r, L, bpp, pad, mode, cfg):
-    img = synth.camera_like(h, w, seed=1700 + k, npoly=12, rad_range=(1, 60)) if k % 2 else \
+@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _straight_cases())
+def test_fuzz_straight_line_path(k, w, h, r, L, bpp, pad, mode, cfg):
+    img = synth.camera_like(h, w, seed=1700 + k, npoly=12, rad_range=(1, 60)) if k % 4 < 2 else \
         synth.uniform_rgb(h, w, seed=1700 + k)
     if k % 3 == 0:  # runs of white pixels (level L - 1, or level L in literal mode)
         img[np.random.default_rng(k).random((h, w)) < 0.2] = 255
     try:
         check_case(img, r, L, bpp, pad, mode, cfg)
     except B.OilPaintError as e:
-        # refused only when the halo ring plus the histograms (nine of 8-byte
-        # bins and two count words per level and thread) exceed a CTA's
-        # shared memory
+        # refused only when the halo ring plus the histograms (nb + K - 1 of
+        # 8-byte bins and (K - 1) / 4 count words per level and thread)
+        # exceed a CTA's shared memory
         assert e.status == B.OP_E_UNSUPPORTED, e
-        nt = cfg["tile_w"] // 8
-        boxw = 8 * (nt - 1 + (2 * r + 7) // 8 + 1)
+        K = cfg["cols_per_thread"]
+        nb = 1 if cfg["path"] == 2 else 2
+        nt = cfg["tile_w"] // K
+        boxw = -(-K * (nt - 1 + (2 * r + K - 1) // K + 1) // 4) * 4
         half = -(-boxw * cfg["chunk_rows"] * 4 // 128) * 128
         slots = cfg["prefetch"] + 1
-        smem = 128 + -(-slots * 8 // 128) * 128 + 2 * half * slots + 80 * L * nt
+        hist = ((nb + K - 1) * 8 + -(-(K - 1) // 4) * 4) * L * nt
+        smem = 128 + -(-slots * 8 // 128) * 128 + 2 * half * slots + hist
         assert smem > 226 * 1024, (cfg, r, L, smem)
 
 
-@pytest.mark.parametrize("r", list(range(4, 16)))
-def test_eight_columns_every_radius(r):
-    """Every radius the eight-column path takes, 32 and 64 threads, RGB and
-    RGBA, on an image whose width is not a tile multiple."""
+@pytest.mark.parametrize("r", list(range(2, 16)))
+def test_straight_line_every_radius(r):
+    """Every radius of the straight-line path, four and eight columns per
+    thread, the window histogram in one and two parts, 32 and 64 threads,
+    RGB and RGBA, on an image whose width is not a tile multiple."""
     img = synth.camera_like(97, 601, seed=40 + r, npoly=30, rad_range=(3, 150))
-    for nt, bpp, pad, ch in ((32, 4, 0, 2), (64, 3, 5, 1)):
-        check_case(img, r, 20, bpp=bpp, pad=pad,
-                   config={"tile_w": 8 * nt, "cols_per_thread": 8, "chunk_rows": ch})
+    for K in (4, 8):
+        if K == 8 and r < 4:
+            continue
+        for path, nt, bpp, pad, ch in ((2, 32, 4, 0, 2), (3, 64, 3, 5, 1), (2, 64, 3, 1, 1),
+                                       (3, 32, 4, 8, 3)):
+            check_case(img, r, 20, bpp=bpp, pad=pad,
+                       config={"tile_w": K * nt, "cols_per_thread": K, "chunk_rows": ch,
+                               "path": path})
 
 
-@pytest.mark.parametrize("r,L", [(3, 20), (16, 20), (15, 33), (0, 1)])
-def test_eight_columns_refused_outside_its_range(r, L):
+@pytest.mark.parametrize("K,path,r,L", [(8, 0, 3, 20), (8, 2, 16, 20), (8, 3, 15, 33),
+                                        (4, 2, 1, 20), (4, 3, 16, 20), (4, 2, 15, 64),
+                                        (8, 0, 0, 1)])
+def test_straight_line_refused_outside_its_range(K, path, r, L):
     op = OilPaint(300, 40, r, L)
     with pytest.raises(B.OilPaintError) as e:
-        op.set_config({"tile_w": 256, "cols_per_thread": 8})
+        op.set_config({"tile_w": 32 * K, "cols_per_thread": K, "path": path})
     assert e.value.status == B.OP_E_UNSUPPORTED
     op.close()
 
