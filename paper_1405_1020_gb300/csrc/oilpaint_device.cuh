@@ -1651,6 +1651,38 @@ __device__ __forceinline__ void blk_h(const Upd64 &A, const Upd64 &B) {
   st_bin(B.a, SUB ? b - B.d : b + B.d);
 }
 
+// As blk_hd and blk_h, with the window pair (A, B) chained instead of
+// alias-safe: B's delta is its own, and when A == B the second update
+// applies to the first's sum (one select after the loads, two instructions
+// fewer than computing the alias-safe delta).
+template <bool SUB>
+__device__ __forceinline__ void blk_hd_chain(const Upd64 &A, const Upd64 &B, const Upd64 &E,
+                                             const Upd64 &F, const Upd32 &G, const Upd32 &H) {
+  if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u) || !OPK_SMEM_OK(E.a, 8u) ||
+      !OPK_SMEM_OK(F.a, 8u) || !OPK_SMEM_OK(G.a, 4u) || !OPK_SMEM_OK(H.a, 4u))
+    return;
+  const uint64_t a0 = ld_bin(A.a), b0 = ld_bin(B.a), e = ld_bin(E.a), f = ld_bin(F.a);
+  const uint32_t g = ld_w32(G.a), h = ld_w32(H.a);
+  const uint64_t a = a0 + A.d;
+  const uint64_t b = A.a == B.a ? a : b0;
+  st_bin(A.a, a);
+  st_bin(B.a, SUB ? b - B.d : b + B.d);
+  st_bin(E.a, e + E.d);
+  st_bin(F.a, f - F.d);
+  st_w32(G.a, g + G.v);
+  st_w32(H.a, h - H.v);
+}
+
+template <bool SUB>
+__device__ __forceinline__ void blk_h_chain(const Upd64 &A, const Upd64 &B) {
+  if (!OPK_SMEM_OK(A.a, 8u) || !OPK_SMEM_OK(B.a, 8u)) return;
+  const uint64_t a0 = ld_bin(A.a), b0 = ld_bin(B.a);
+  const uint64_t a = a0 + A.d;
+  const uint64_t b = A.a == B.a ? a : b0;
+  st_bin(A.a, a);
+  st_bin(B.a, SUB ? b - B.d : b + B.d);
+}
+
 // Pair (E, F) on a D_i (E adds, F subtracts) with its count words (G, H).
 __device__ __forceinline__ void blk_d(const Upd64 &E, const Upd64 &F, const Upd32 &G,
                                       const Upd32 &H) {
@@ -1784,16 +1816,16 @@ __device__ __forceinline__ void deltak_step(const DeltaK<NT, K, NB> &o, const ui
         blk_d(E, F, G, H);
       }
     } else {
-      // block j: the window pair at word j, D pair j
+      // block j: the window pair at word j (chained), D pair j
 #pragma unroll
       for (int j = 0; j <= 2 * R; ++j) {
         A = o.add(0, e[j]);
-        B = o.template second<true>(A, 0, l[j]);
+        B = o.add(0, l[j]);
         if (j < ND) {
           dp(j);
-          blk_hd<true>(A, B, E, F, G, H);
+          blk_hd_chain<true>(A, B, E, F, G, H);
         } else {
-          blk_h<true>(A, B);
+          blk_h_chain<true>(A, B);
         }
       }
 #pragma unroll
@@ -1848,16 +1880,16 @@ __device__ __forceinline__ void deltak_step(const DeltaK<NT, K, NB> &o, const ui
         blk_d(E, F, G, H);
       }
     } else {
-      // window pairs (2q, 2q + 1), then the last window word 2R
+      // window pairs (2q, 2q + 1) (chained), then the last window word 2R
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         A = o.add(0, e[2 * q]);
-        B = o.template second<false>(A, 0, e[2 * q + 1]);
+        B = o.add(0, e[2 * q + 1]);
         if (q < K - 1) {
           o.dpair(q + 1, e[2 * R + q + 1], e[q], E, F, G, H);
-          blk_hd<false>(A, B, E, F, G, H);
+          blk_hd_chain<false>(A, B, E, F, G, H);
         } else {
-          blk_h<false>(A, B);
+          blk_h_chain<false>(A, B);
         }
       }
       A = o.add(0, e[2 * R]);
@@ -1924,6 +1956,34 @@ __device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x
         uint32_t best[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) best[i] = 0u;
+        if constexpr (K == 4) {
+          // two windows per word: 16-bit keys (count << 5) | (31 - level)
+          // (count <= 961, so a key is below 2^15), max per halfword
+          uint32_t b01 = 0u, b23 = 0u;
+#pragma unroll 4
+          for (uint32_t lv = 0; lv < L; ++lv) {
+            uint32_t c = lds_u32(o.h0 + lv * O::kLS);
+            if (NB == 2) c += lds_u32(o.h0 + lv * O::kLS + O::kHS);
+            // byte k of p: 128 + the count of D_1 + .. + D_{k+1}
+            const uint32_t p = lds_u32(o.dc0 + lv * O::kDLS) * 0x01010101u + 0x80808080u;
+            const uint32_t k0 = ((c << 5) & 0x7FE0u) | (31u - lv);
+            // window 1 (high half of b01) adds byte 0, windows 2 and 3 (b23)
+            // bytes 1 and 2, each still carrying its bias of 128, i.e. 4096
+            // in the key: the same for every level of a window, so it leaves
+            // the argmax alone, keeps every halfword within 16 bits (at most
+            // 30783 + 4096) and is taken off once after the loop
+            const uint32_t x01 = __byte_perm(p, 0u, 0x4044u) << 5;  // byte 0 -> high half
+            const uint32_t x23 = __byte_perm(p, 0u, 0x4241u) << 5;  // bytes 1, 2 -> low, high
+            b01 = __viaddmax_u16x2(k0 * 0x00010001u, x01, b01);
+            b23 = __viaddmax_u16x2(k0 * 0x00010001u, x23, b23);
+          }
+          // back to the 32-bit keys (count << 22) | tag of the general code
+          auto key32 = [](uint32_t h) { return (h & 0xFFE0u) << 17 | (h & 31u); };
+          best[0] = key32(b01 & 0xFFFFu);
+          best[1] = key32((b01 >> 16) - 4096u);
+          best[2] = key32((b23 & 0xFFFFu) - 4096u);
+          best[3] = key32((b23 >> 16) - 4096u);
+        } else {
 #pragma unroll 4
         for (uint32_t lv = 0; lv < L; ++lv) {
           // the window parts' low words: the counts sit in bits 0..9, so the
@@ -1952,6 +2012,7 @@ __device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x
               }
             }
           }
+        }
         }
         // the reciprocals first, so that their latency overlaps the loads
         // of the winning bins
