@@ -28,8 +28,9 @@ TABLE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb
 
 def candidates(radius: int, levels: int, tile_hs=(0,)) -> list[dict]:
     """Threads per CTA x output columns per thread x halo chunk height x
-    prefetch depth x tile height; configurations the library refuses (halo
-    wider than 256 columns, shared memory) are skipped when timed."""
+    prefetch depth x tile height, on every path that applies; configurations
+    the library refuses (shared memory, a path outside its radius range) are
+    skipped when timed."""
     out = []
     for nt, cpt, ch, pf, th in itertools.product((32, 64, 96, 128), (1, 2, 4), (1, 2, 4, 8, 16), (1, 2),
                                                   tile_hs):
@@ -40,6 +41,13 @@ def candidates(radius: int, levels: int, tile_hs=(0,)) -> list[dict]:
                                                       tile_hs):
             out.append({"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
                         "cols_per_thread": cpt, "path": 1})
+    if levels <= 32 and 2 <= radius <= 15:  # straight-line difference histograms
+        for path, cpt, nt, ch, pf, th in itertools.product((2, 3), (4, 8), (32, 64), (1, 2, 4),
+                                                            (1, 2), tile_hs):
+            if cpt == 8 and radius < 4:
+                continue
+            out.append({"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
+                        "cols_per_thread": cpt, "path": path})
     return out
 
 

@@ -227,17 +227,21 @@ int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
 }
 
 // Built-in default: the first of a preference list that runs and whose shared
-// memory leaves room for >= 2 CTAs per SM, 8-row halo chunks, one chunk in
-// flight; difference histograms over 4 or 2 columns per thread first where
-// they apply (r <= 15, L <= 32).
+// memory leaves room for >= 2 CTAs per SM, one halo chunk in flight: the
+// straight-line difference histograms (64 threads x 4 columns, the window
+// histogram in one part, 2-row chunks) where they apply (2 <= r <= 15,
+// L <= 32), then difference histograms over 4 or 2 columns per thread
+// (r <= 44, L <= 32), then one column per thread (8-row chunks).
 op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
-  static const uint32_t prefs[][2] = {{32, 4}, {64, 2}, {128, 1}, {96, 1}, {64, 1}, {32, 1}};
+  // threads, columns per thread, path, halo chunk rows
+  static const uint32_t prefs[][4] = {{64, 4, 2, 2}, {32, 4, 0, 8}, {64, 2, 0, 8}, {128, 1, 0, 8},
+                                      {96, 1, 0, 8},  {64, 1, 0, 8}, {32, 1, 0, 8}};
   for (const auto &p : prefs) {
-    op_config_t c = {p[0] * p[1], 0, 8, 1, p[1]};
+    op_config_t c = {p[0] * p[1], 0, p[3], 1, p[1], p[2]};
     if (check_config(c, r, L, di) != OP_OK) continue;
     if (smem_for(c, r, L) * 2 <= di.smem_optin) return c;
   }
-  return op_config_t{32, 0, 4, 1, 1};
+  return op_config_t{32, 0, 4, 1, 1, 0};
 }
 
 int pick_config(int r, uint32_t L, const DevInfo &di, op_config_t *out) {
