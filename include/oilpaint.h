@@ -87,16 +87,17 @@ typedef struct op_s op_t;
  *   chunk_rows      input rows per TMA halo copy, 1..32;
  *   prefetch        halo copies in flight ahead of the one being consumed, 1..4;
  *   cols_per_thread output columns per thread: 1 (one running histogram of
- *                   the window per output column), 2 or 4 (difference
+ *                   the window per output column), 2, 4 or 8 (difference
  *                   histograms: each thread keeps the window histogram H of
  *                   its first column and, for each next column i, the
  *                   histogram D_i of the column entering minus the column
  *                   leaving the window, so the window of column i is
  *                   H + D_1 + ... + D_i; 2(2r+1) + 4(K-1) bin updates per K
- *                   outputs instead of 2(2r+1) per output); 0 = 1.  2 and 4
- *                   need levels <= 32, else the configuration is refused
+ *                   outputs instead of 2(2r+1) per output); 0 = 1.  2, 4 and
+ *                   8 need levels <= 32, else the configuration is refused
  *                   (OP_E_UNSUPPORTED) by op_set_config; a batch runs its
- *                   other images on the one-column path.
+ *                   other images on the one-column path.  8 exists only on
+ *                   path 3 (path 0 with 8 columns means path 3).
  *   path            0: histograms kept per thread (the fields above);
  *                   1: column histograms with the levels across a warp's
  *                   lanes (Perreault and Hebert's constant-time column
@@ -105,9 +106,19 @@ typedef struct op_s op_t;
  *                   halo, each warp sweeps
  *                   32 * cols_per_thread output columns of every row
  *                   (cols_per_thread 1 or 2), tile_w / cols_per_thread =
- *                   32, 64 or 128 threads; needs levels <= 32.
- * The halo copy of a tile is at most 256 columns wide: tile_w + 2r + up to
- * 3 columns for one column per thread and for path 1, K * (threads - 1 +
+ *                   32, 64 or 128 threads; needs levels <= 32;
+ *                   2 and 3: the difference histograms of 4 or 8 columns
+ *                   per thread compiled once per radius (straight-line
+ *                   steps), with the counts of D_1 .. D_{K-1} also kept as
+ *                   bytes packed into one word per level and per four
+ *                   columns, so that the argmax reads two words per level;
+ *                   the window histogram in one part (path 2) or split by
+ *                   column parity into two (path 3); 32 or 64 threads;
+ *                   needs levels <= 32 and K/2 <= radius <= 15 (radius >= 4
+ *                   for 8 columns), else OP_E_UNSUPPORTED.  Not for batches.
+ * The halo copy of a tile is at most 1024 columns wide (copies wider than
+ * 256 columns read the packed image as groups of 4 words): tile_w + 2r + up
+ * to 3 columns for one column per thread and for path 1, K * (threads - 1 +
  * ceil((2r+K-1)/K) + 1) rounded up to 4 for K columns per thread.
  */
 typedef struct {
