@@ -41,6 +41,10 @@ def candidates(radius: int, levels: int, tile_hs=(0,)) -> list[dict]:
                                                       tile_hs):
             out.append({"tile_w": nt * cpt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
                         "cols_per_thread": cpt, "path": 1})
+    if levels <= 64 and 1 <= radius <= 15:  # straight-line, two columns per thread
+        for nt, ch, pf, th in itertools.product((32, 64), (1, 2, 4), (1, 2), tile_hs):
+            out.append({"tile_w": nt * 2, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
+                        "cols_per_thread": 2, "path": 2})
     if levels <= 32 and 2 <= radius <= 15:  # straight-line difference histograms
         for path, cpt, nt, ch, pf, th in itertools.product((2, 3), (4, 8), (32, 64), (1, 2, 4),
                                                             (1, 2), tile_hs):

@@ -1,7 +1,7 @@
 """Builds the CUDA library paper_1405_1020_gb300/liboilpaint.so for sm_103a.
 
-Five translation units (the kernels, the straight-line difference-histogram
-kernels with four and with eight columns per thread, the C ABI, and the
+Six translation units (the kernels, the straight-line difference-histogram
+kernels with two, four and eight columns per thread, the C ABI, and the
 allocation-free entry point with its device scratch array) are compiled in
 parallel with nvcc and linked into one shared library with the CUDA runtime linked statically, so
 the library needs nothing but the NVIDIA driver at run time.  The library is
@@ -20,7 +20,8 @@ ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liboilpaint.so")
 SOURCES = [
-    "oilpaint_kernels.cu", "oilpaint_delta4.cu", "oilpaint_delta8.cu", "oilpaint_api.cu",
+    "oilpaint_kernels.cu", "oilpaint_delta2.cu", "oilpaint_delta4.cu", "oilpaint_delta8.cu",
+    "oilpaint_api.cu",
     "oilpaint_noalloc.cu",
 ]
 HEADERS = ["oilpaint_device.cuh", "oilpaint_internal.h", "oilpaint_deltak.cuh"]

@@ -160,9 +160,13 @@ bool config_in_range(const op_config_t &c) {
   if (c.tile_w % cpt) return false;
   const uint32_t nt = c.tile_w / cpt;
   if (nt != 32 && nt != 64 && nt != 96 && nt != 128) return false;
-  // the straight-line paths (2, 3): 4 or 8 columns of 32 or 64 threads; eight
-  // columns exist only there (path 0 with 8 columns means path 3)
-  if ((c.path >= 2u || cpt == 8u) && (nt > 64 || (cpt != 4u && cpt != 8u))) return false;
+  // the straight-line paths (2, 3): 4 or 8 columns of 32 or 64 threads, or 2
+  // columns on path 2; eight columns exist only there (path 0 with 8 columns
+  // means path 3)
+  if ((c.path >= 2u || cpt == 8u) && (nt > 64 || (cpt != 4u && cpt != 8u))) {
+    // two columns: path 2 only (the window histogram in one part)
+    if (!(c.path == 2u && cpt == 2u && nt <= 64)) return false;
+  }
   if (cpt == 8u && c.path == 1u) return false;
   if (c.path == 1u && (cpt == 4u || nt == 96u)) return false;  // 1, 2 or 4 warps x 32 or 64
   if (c.chunk_rows < 1 || c.chunk_rows > 32 || c.prefetch < 1 || c.prefetch > 4) return false;

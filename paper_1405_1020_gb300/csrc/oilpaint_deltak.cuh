@@ -1,9 +1,9 @@
 // oilpaint_deltak.cuh -- kernels and launch tables of the straight-line
 // difference-histogram path (run_tile_deltak in oilpaint_device.cuh): one
 // kernel per radius, per CTA of 32 or 64 threads, per window split (NB = 1
-// or 2 parts), for K = 4 or 8 output columns per thread.  Each K is compiled
-// in a translation unit of its own (oilpaint_delta4.cu, oilpaint_delta8.cu)
-// so that the two compile in parallel.
+// or 2 parts; 1 for K = 2), for K = 2, 4 or 8 output columns per thread.
+// Each K is compiled in a translation unit of its own (oilpaint_delta2.cu,
+// oilpaint_delta4.cu, oilpaint_delta8.cu) so that they compile in parallel.
 #pragma once
 
 #include <utility>
@@ -38,10 +38,16 @@ template <int K>
 DeltaKFn deltak_kernel(uint32_t nt, int nb, int r) {
   constexpr int R0 = deltak_min_radius(K);
   using Seq = std::make_integer_sequence<int, kDeltaKMaxRadius - R0 + 1>;
-  if (nt == 32) return nb == 1 ? deltak_kernel_for<32, K, 1, R0>(r, Seq{})
-                               : deltak_kernel_for<32, K, 2, R0>(r, Seq{});
-  if (nt == 64) return nb == 1 ? deltak_kernel_for<64, K, 1, R0>(r, Seq{})
-                               : deltak_kernel_for<64, K, 2, R0>(r, Seq{});
+  if constexpr (K == 2) {  // the window histogram in one part only
+    if (nb != 1) return nullptr;
+    if (nt == 32) return deltak_kernel_for<32, K, 1, R0>(r, Seq{});
+    if (nt == 64) return deltak_kernel_for<64, K, 1, R0>(r, Seq{});
+  } else {
+    if (nt == 32) return nb == 1 ? deltak_kernel_for<32, K, 1, R0>(r, Seq{})
+                                 : deltak_kernel_for<32, K, 2, R0>(r, Seq{});
+    if (nt == 64) return nb == 1 ? deltak_kernel_for<64, K, 1, R0>(r, Seq{})
+                                 : deltak_kernel_for<64, K, 2, R0>(r, Seq{});
+  }
   return nullptr;
 }
 

@@ -99,9 +99,13 @@ constexpr uint32_t kModeLiteral = 2u;
 constexpr int kDeltaMaxRadius = 44;
 constexpr uint32_t kDeltaMaxLevels = 32;
 // The straight-line difference-histogram path (run_tile_deltak): variant-A
-// bins, K/2 <= r <= 15 for K = 4 or 8 columns per thread (r >= 4 for K = 8).
+// bins, K/2 <= r <= 15 for K = 2, 4 or 8 columns per thread (r >= 4 for
+// K = 8), L <= 32 (L <= 64 for K = 2).
 constexpr int kDeltaKMaxRadius = 15;
-__host__ __device__ constexpr int deltak_min_radius(int k) { return k == 8 ? 4 : 2; }
+constexpr uint32_t kDeltaK2MaxLevels = 64;
+__host__ __device__ constexpr int deltak_min_radius(int k) {
+  return k == 8 ? 4 : (k == 4 ? 2 : 1);
+}
 
 // Halo boxes up to kMaxBox2dWords words wide are 2-D TMA copies; wider ones
 // (up to kMaxBoxWords) use the 3-D view of the packed image (tma_load_3d),
@@ -443,16 +447,20 @@ __device__ __forceinline__ uint32_t pack_word(uint32_t R, uint32_t G, uint32_t B
   return (level_of(R, G, B, L, mode) << 24) | (R << 16) | (G << 8) | B;
 }
 
-// Word format 1 (L <= 32), laid out so that one mask gives the low word and
-// one shift and mask the high word of the pixel's bin delta (see DHist):
+// Word format 1 (L <= 64), laid out so that one mask gives the low word and
+// one shift and mask the high word of the pixel's bin delta (see dh_delta):
 //   bit 0 valid (1 for every image pixel; the zero words TMA supplies outside
-//   the image therefore add nothing), bits 1..5 level, 6..9 G >> 4,
-//   10..17 R, 20..27 B, 28..31 G & 15.
+//   the image therefore add nothing), bits 1..5 level & 31, 6..9 G >> 4,
+//   10..17 R, 18 level >> 5, 20..27 B, 28..31 G & 15.
+// Bit 18 lies outside both masks of the delta; it is set only when L > 32,
+// which only the two-column straight-line path accepts (the other paths read
+// the level as w & 0x3E).
 __device__ __forceinline__ uint32_t pack_word_delta(uint32_t R, uint32_t G, uint32_t B,
                                                     uint32_t L, uint32_t mode) {
   const uint32_t l = level_of(R, G, B, L, mode);
   if (l >= L) return 0u;  // literal mode: level L is never read, so it adds nothing
-  return 1u | (l << 1) | ((G >> 4) << 6) | (R << 10) | (B << 20) | ((G & 0xFu) << 28);
+  return 1u | ((l & 31u) << 1) | ((G >> 4) << 6) | (R << 10) | ((l >> 5) << 18) | (B << 20) |
+         ((G & 0xFu) << 28);
 }
 
 // Word format 2 (L <= 32, 16 <= r <= 44): R @0..7 | level @8..12 |
@@ -1698,28 +1706,39 @@ __device__ __forceinline__ void blk_d(const Upd64 &E, const Upd64 &F, const Upd3
 }
 
 // One thread's histograms and count words for K output columns per thread
-// (K = 4 or 8), the window histogram split into NB = 1 or 2 parts (by the
-// parity of the window column), and the updates of one packed word (word
-// format 1; the level field at bits 1..5, so w & 0x3E is twice the level).
-// Histograms 0 .. NB-1 are the window histogram's parts, NB - 1 + i is D_i;
-// the DC words hold the counts of D_1 .. D_4 (word 0) and D_5 .. D_7 (word 1).
+// (K = 2, 4 or 8), the window histogram split into NB = 1 or 2 parts (by the
+// parity of the window column; NB = 1 for K = 2), and the updates of one
+// packed word (word format 1).  Histograms 0 .. NB-1 are the window
+// histogram's parts, NB - 1 + i is D_i.  The count words hold, for K = 4 and
+// 8, the counts of D_1 .. D_4 (word 0) and D_5 .. D_7 (word 1) of one level;
+// for K = 2 (L <= 64) the counts of D_1 at four consecutive levels (byte
+// lv & 3 of word lv / 4).  The level is read as the 5-bit field at bits 1..5
+// (L <= 32) or, for K = 2, with bit 18 as its sixth bit.
 template <int NT, int K, int NB>
 struct DeltaK {
-  static_assert((K == 4 || K == 8) && (NB == 1 || NB == 2), "K columns, NB window parts");
+  static_assert((K == 2 && NB == 1) || ((K == 4 || K == 8) && (NB == 1 || NB == 2)),
+                "K columns, NB window parts");
   static constexpr int kHists = NB + K - 1;
-  static constexpr int kDCWords = (K - 1 + 3) / 4;
+  static constexpr int kDCWords = (K - 1 + 3) / 4;  // per level (K = 4, 8)
   static constexpr uint32_t kHS = NT * 8u;                   // between histograms
   static constexpr uint32_t kLS = kHists * kHS;              // between levels (bins)
-  static constexpr uint32_t kDW = NT * 4u;                   // between a level's DC words
-  static constexpr uint32_t kDLS = kDCWords * kDW;           // between levels (DC words)
+  static constexpr uint32_t kDW = NT * 4u;                   // between DC words
+  static constexpr uint32_t kDLS = kDCWords * kDW;           // between levels (DC, K = 4, 8)
   uint32_t h0;   // the first window part's level-0 bin of this thread
-  uint32_t dc0;  // this thread's first DC word of level 0
+  uint32_t dc0;  // this thread's first DC word
 
+  // twice word w's level
+  static __device__ __forceinline__ uint32_t lv2(uint32_t w) {
+    if constexpr (K == 2)
+      return (w & 0x3Eu) | ((w >> 12) & 0x40u);
+    else
+      return w & 0x3Eu;
+  }
   // +w in histogram k
   __device__ __forceinline__ Upd64 add(int k, uint32_t w) const {
     uint32_t lo, hi;
     dh_delta(w, lo, hi);
-    return Upd64{h0 + static_cast<uint32_t>(k) * kHS + (w & 0x3Eu) * (kLS / 2u), u64_of(lo, hi)};
+    return Upd64{h0 + static_cast<uint32_t>(k) * kHS + lv2(w) * (kLS / 2u), u64_of(lo, hi)};
   }
   // the second update of a pair whose first is `first`, of word w in
   // histogram k, to be subtracted (SUB) or added; when both land on one bin
@@ -1731,10 +1750,15 @@ struct DeltaK {
     return Upd64{u.a, SUB ? u.d - x : u.d + x};
   }
   // D_i's count word at word w's level and the word's valid bit moved to
-  // D_i's byte
+  // D_i's byte (K = 4, 8) or to the level's byte (K = 2)
   __device__ __forceinline__ Upd32 cnt(int i, uint32_t w) const {
-    return Upd32{dc0 + static_cast<uint32_t>((i - 1) >> 2) * kDW + (w & 0x3Eu) * (kDLS / 2u),
-                 (w & 1u) << (8 * ((i - 1) & 3))};
+    if constexpr (K == 2) {
+      const uint32_t l2 = lv2(w);  // 2 * level
+      return Upd32{dc0 + (l2 >> 3) * kDW, (w & 1u) << ((l2 & 6u) << 2)};
+    } else {
+      return Upd32{dc0 + static_cast<uint32_t>((i - 1) >> 2) * kDW + lv2(w) * (kDLS / 2u),
+                   (w & 1u) << (8 * ((i - 1) & 3))};
+    }
   }
   // D_i: +a -b (sums and count)
   __device__ __forceinline__ void dpair(int i, uint32_t a, uint32_t b, Upd64 &E, Upd64 &F,
@@ -1748,7 +1772,8 @@ struct DeltaK {
 };
 
 // One step of run_tile_deltak from the ring words 0 .. 2R+K-1 (read as
-// 16-byte groups) of the entering row pe and (RM) the leaving row pl.  Word j
+// 16-byte groups, 8-byte for K = 2) of the entering row pe and (RM) the
+// leaving row pl.  Word j
 // feeds the window histogram when j <= 2R (with NB = 2: part 0 for even j,
 // part 1 for odd j), D_{j+1} negatively (its left column leaves the window)
 // when j <= K-2, and D_{j-2R} positively (its right column enters) when
@@ -1757,24 +1782,40 @@ struct DeltaK {
 template <int NT, int K, int NB, int R, bool RM>
 __device__ __forceinline__ void deltak_step(const DeltaK<NT, K, NB> &o, const uint32_t *pe,
                                             const uint32_t *pl) {
-  constexpr int NG = (2 * R + K + 3) / 4;  // 16-byte groups covering words 0 .. 2R+K-1
-  constexpr int ND = 2 * (K - 1);          // D pairs of a step
-  uint32_t e[4 * NG], l[4 * NG];
+  // groups of GW words covering words 0 .. 2R+K-1: 16 bytes, or 8 for K = 2
+  // (a two-column thread's window starts on an 8-byte boundary only)
+  constexpr int GW = K == 2 ? 2 : 4;
+  constexpr int NG = (2 * R + K + GW - 1) / GW;
+  constexpr int ND = 2 * (K - 1);  // D pairs of a step
+  uint32_t e[GW * NG], l[GW * NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(pe + 4 * g);
-    e[4 * g] = v.x;
-    e[4 * g + 1] = v.y;
-    e[4 * g + 2] = v.z;
-    e[4 * g + 3] = v.w;
-    if (RM) {
-      const uint4 u = *reinterpret_cast<const uint4 *>(pl + 4 * g);
-      l[4 * g] = u.x;
-      l[4 * g + 1] = u.y;
-      l[4 * g + 2] = u.z;
-      l[4 * g + 3] = u.w;
+    if constexpr (GW == 4) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(pe + 4 * g);
+      e[4 * g] = v.x;
+      e[4 * g + 1] = v.y;
+      e[4 * g + 2] = v.z;
+      e[4 * g + 3] = v.w;
+      if (RM) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(pl + 4 * g);
+        l[4 * g] = u.x;
+        l[4 * g + 1] = u.y;
+        l[4 * g + 2] = u.z;
+        l[4 * g + 3] = u.w;
+      } else {
+        l[4 * g] = l[4 * g + 1] = l[4 * g + 2] = l[4 * g + 3] = 0u;
+      }
     } else {
-      l[4 * g] = l[4 * g + 1] = l[4 * g + 2] = l[4 * g + 3] = 0u;
+      const uint2 v = *reinterpret_cast<const uint2 *>(pe + 2 * g);
+      e[2 * g] = v.x;
+      e[2 * g + 1] = v.y;
+      if (RM) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(pl + 2 * g);
+        l[2 * g] = u.x;
+        l[2 * g + 1] = u.y;
+      } else {
+        l[2 * g] = l[2 * g + 1] = 0u;
+      }
     }
   }
   Upd64 A, B, C, D, E, F;
@@ -1928,10 +1969,14 @@ __device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x
 #pragma unroll
     for (int i = 0; i < O::kHists; ++i)
       sts_zero64(o.h0 + lv * O::kLS + static_cast<uint32_t>(i) * O::kHS);
+    if constexpr (K != 2) {
 #pragma unroll
-    for (int w = 0; w < O::kDCWords; ++w)
-      sts_zero32(o.dc0 + lv * O::kDLS + static_cast<uint32_t>(w) * O::kDW);
+      for (int w = 0; w < O::kDCWords; ++w)
+        sts_zero32(o.dc0 + lv * O::kDLS + static_cast<uint32_t>(w) * O::kDW);
+    }
   }
+  if constexpr (K == 2)  // one count word per four levels
+    for (uint32_t q = 0; q < (L + 3u) / 4u; ++q) sts_zero32(o.dc0 + q * O::kDW);
 
   return ring_pass(
       d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, diag, tmap_global, x0, y0,
@@ -1956,7 +2001,30 @@ __device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x
         uint32_t best[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) best[i] = 0u;
-        if constexpr (K == 4) {
+        // the level tag: 6 bits (L <= 64) for two columns, else 5
+        constexpr uint32_t kTag = K == 2 ? 63u : 31u;
+        if constexpr (K == 2) {
+          // windows 0 and 1 as the halves of one word: 16-bit keys
+          // (count << 6) | (63 - level), below 2^16 for count <= 961; window
+          // 1 adds D_1's signed count (byte lv & 3 of the level group's word)
+          // times 64 to the high half, whose sum stays in [0, 2^16)
+          uint32_t b01 = 0u;
+          for (uint32_t lq = 0; lq < L; lq += 4u) {
+            const uint32_t dw = lds_u32(o.dc0 + (lq >> 2) * O::kDW);
+#pragma unroll
+            for (uint32_t k = 0; k < 4u; ++k) {
+              const uint32_t lv = lq + k;
+              if (lv >= L) break;
+              const uint32_t c = lds_u32(o.h0 + lv * O::kLS);
+              const int32_t d1 = static_cast<int32_t>(dw << (24u - 8u * k)) >> 24;
+              const uint32_t k0 = ((c << 6) & 0xFFC0u) | (63u - lv);
+              b01 = __viaddmax_u16x2(k0 * 0x00010001u, static_cast<uint32_t>(d1) << 22, b01);
+            }
+          }
+          auto key32 = [](uint32_t h) { return (h & 0xFFC0u) << 16 | (h & 63u); };
+          best[0] = key32(b01 & 0xFFFFu);
+          best[1] = key32(b01 >> 16);
+        } else if constexpr (K == 4) {
           // two windows per word: 16-bit keys (count << 5) | (31 - level)
           // (count <= 961, so a key is below 2^15), max per halfword
           uint32_t b01 = 0u, b23 = 0u;
@@ -2023,7 +2091,7 @@ __device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x
         for (int i = 0; i < K; ++i) {
           const int x = xa + i;
           if (x < d.ox0 || x >= d.ox1) continue;
-          const uint32_t m = 31u - (best[i] & 31u);
+          const uint32_t m = kTag - (best[i] & kTag);
           if ((best[i] >> 22) == 0u) continue;  // no level below L (literal mode only)
           uint64_t v = 0;
 #pragma unroll

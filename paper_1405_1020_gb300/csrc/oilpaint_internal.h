@@ -46,13 +46,14 @@ inline bool delta_eligible(int r, uint32_t L) {
   return r >= 0 && r <= kDeltaMaxRadius && L >= 1 && L <= kDeltaMaxLevels;
 }
 
-// The straight-line difference-histogram path (paths 2 and 3; K = 4 or 8
-// columns per thread, one kernel per radius): variant-A bins, L <= 32, and
-// r >= K/2 so that the left difference words 0 .. K-2 lie inside the window
-// and apart from the right ones.
+// The straight-line difference-histogram path (paths 2 and 3; K = 2, 4 or
+// 8 columns per thread, one kernel per radius): variant-A bins, L <= 32 (64
+// for K = 2, window histogram in one part only), and r >= K/2 so that the
+// left difference words 0 .. K-2 lie inside the window and apart from the
+// right ones.
 inline bool deltak_eligible(int k, int r, uint32_t L) {
-  return (k == 4 || k == 8) && r >= deltak_min_radius(k) && r <= kDeltaKMaxRadius && L >= 1 &&
-         L <= kDeltaMaxLevels;
+  return (k == 2 || k == 4 || k == 8) && r >= deltak_min_radius(k) && r <= kDeltaKMaxRadius &&
+         L >= 1 && L <= (k == 2 ? kDeltaK2MaxLevels : kDeltaMaxLevels);
 }
 
 // Box width (words) of a difference-histogram tile: thread t reads K-word
@@ -150,8 +151,11 @@ inline int pack_grid_for(uint32_t rows, int sms) {
 }
 
 // Histogram bytes of a CTA on the straight-line path: per level and thread
-// nb + k - 1 histograms of 8-byte bins and (k - 1)/4 rounded up count words.
+// nb + k - 1 histograms of 8-byte bins and (k - 1)/4 rounded up count words
+// (k = 2: one count word per four levels).
 inline size_t deltak_hist_bytes(uint32_t nt, int k, int nb, uint32_t L) {
+  if (k == 2)  // two histograms, one count word per four levels
+    return (static_cast<size_t>(16) * L + (L + 3u) / 4u * 4u) * nt;
   return static_cast<size_t>((nb + k - 1) * 8 + (k - 1 + 3) / 4 * 4) * L * nt;
 }
 
@@ -237,9 +241,9 @@ cudaError_t launch_persistent(uint32_t nt, int kcols, const ImgDesc *d_descs,
                               uint32_t *d_queue, const RingCfg &rc, uint32_t lmax, int grid,
                               size_t smem, uint32_t *err, uint64_t timeout_ns, cudaStream_t s);
 cudaError_t launch_selftest_wait(uint32_t *d_err, uint64_t timeout_ns, cudaStream_t s);
-// The straight-line difference-histogram path (paths 2 and 3, d.kcols = 4
-// or 8, nt = 32 or 64 threads, one kernel per radius in K's range, variant
-// A, d.L <= 32); cudaErrorInvalidValue otherwise.
+// The straight-line difference-histogram path (paths 2 and 3, d.kcols = 2,
+// 4 or 8, nt = 32 or 64 threads, one kernel per radius in K's range, variant
+// A, d.L within K's limit); cudaErrorInvalidValue otherwise.
 cudaError_t launch_deltak(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
                           const RingCfg &rc, dim3 grid, size_t smem, uint32_t *err,
                           uint64_t timeout_ns, cudaStream_t s);
@@ -248,6 +252,7 @@ int deltak_occupancy(uint32_t nt, int k, int nb, size_t smem);
 // One straight-line kernel (nullptr outside the tables): nt threads, nb
 // window parts, radius r; defined in oilpaint_delta4.cu / oilpaint_delta8.cu.
 using DeltaKFn = void (*)(const CUtensorMap, const ImgDesc, const RingCfg, uint32_t *, uint64_t);
+DeltaKFn deltak_kernel_k2(uint32_t nt, int nb, int r);
 DeltaKFn deltak_kernel_k4(uint32_t nt, int nb, int r);
 DeltaKFn deltak_kernel_k8(uint32_t nt, int nb, int r);
 // Checked builds: the bounds-check violation bits since the last call

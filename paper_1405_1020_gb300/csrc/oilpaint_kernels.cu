@@ -422,7 +422,10 @@ int tile_occupancy_cols(uint32_t nt, int twk, int variant, size_t smem) {
 }
 
 static DeltaKFn deltak_fn(uint32_t nt, int k, int nb, int r) {
-  return k == 4 ? deltak_kernel_k4(nt, nb, r) : k == 8 ? deltak_kernel_k8(nt, nb, r) : nullptr;
+  return k == 2   ? deltak_kernel_k2(nt, nb, r)
+         : k == 4 ? deltak_kernel_k4(nt, nb, r)
+         : k == 8 ? deltak_kernel_k8(nt, nb, r)
+                  : nullptr;
 }
 
 cudaError_t launch_deltak(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
@@ -430,17 +433,19 @@ cudaError_t launch_deltak(uint32_t nt, const ImgDesc &d, const CUtensorMap &map,
                           uint64_t timeout_ns, cudaStream_t s) {
   const DeltaKFn f = deltak_fn(nt, static_cast<int>(d.kcols), static_cast<int>(d.path) - 1,
                                    d.r);
-  if (!f || d.variant != static_cast<uint32_t>(kVarA) || d.L > kDeltaMaxLevels)
+  if (!f || d.variant != static_cast<uint32_t>(kVarA) ||
+      d.L > (d.kcols == 2u ? kDeltaK2MaxLevels : kDeltaMaxLevels))
     return cudaErrorInvalidValue;
   f<<<grid, nt, smem, s>>>(map, d, rc, err, timeout_ns);
   return cudaGetLastError();
 }
 
 cudaError_t set_deltak_smem_limit(size_t bytes) {
-  for (int k : {4, 8})
+  for (int k : {2, 4, 8})
     for (uint32_t nt : {32u, 64u})
       for (int nb : {1, 2})
         for (int r = deltak_min_radius(k); r <= kDeltaKMaxRadius; ++r) {
+          if (k == 2 && nb == 2) continue;
           const cudaError_t e =
               cudaFuncSetAttribute(deltak_fn(nt, k, nb, r),
                                    cudaFuncAttributeMaxDynamicSharedMemorySize,

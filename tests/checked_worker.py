@@ -42,6 +42,8 @@ def main() -> int:
         (15, 20, 0, {"tile_w": 128, "cols_per_thread": 4, "chunk_rows": 2, "path": 2}),
         (2, 32, B.OP_LITERAL, {"tile_w": 256, "cols_per_thread": 4, "chunk_rows": 1, "path": 3}),
         (9, 16, 1, {"tile_w": 256, "cols_per_thread": 8, "chunk_rows": 2, "path": 2}),
+        (15, 64, 0, {"tile_w": 64, "cols_per_thread": 2, "chunk_rows": 2, "path": 2}),
+        (1, 47, B.OP_LITERAL, {"tile_w": 128, "cols_per_thread": 2, "chunk_rows": 1, "path": 2}),
         (2, 20, 0, {"tile_w": 64, "cols_per_thread": 1}),
         (20, 64, 1, {"tile_w": 32, "cols_per_thread": 1}),
         (15, 20, 0, {"tile_w": 128, "cols_per_thread": 4, "chunk_rows": 2}),

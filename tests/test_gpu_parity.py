@@ -176,10 +176,11 @@ def test_fuzz_difference_histograms(k, w, h, r, L, bpp, pad, mode, cfg):
         assert smem > 226 * 1024, (cfg, r, L, smem)
 
 
-def _straight_cases(n=96, seed=17):
+def _straight_cases(n=120, seed=17):
     """The straight-line difference-histogram path (one kernel per radius):
-    4 or 8 columns per thread, the window histogram in one part (path 2) or
-    two (path 3; eight columns on path 0 mean path 3), every radius of each
+    2, 4 or 8 columns per thread, the window histogram in one part (path 2)
+    or two (path 3; eight columns on path 0 mean path 3; two columns: path 2
+    only, with up to 64 levels, the sixth level bit), every radius of each
     width's range and both parities (where in a 16-byte group the right
     difference words start), widths around the tile widths, one-row and short
     images, both level modes and literal mode, tile heights, halo chunk
@@ -187,13 +188,13 @@ def _straight_cases(n=96, seed=17):
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(n):
-        K = 8 if k % 2 else 4
-        path = int(rng.choice([0, 2, 3])) if K == 8 else int(rng.choice([2, 3]))
+        K = (4, 8, 2)[k % 3]
+        path = {8: int(rng.choice([0, 2, 3])), 4: int(rng.choice([2, 3])), 2: 2}[K]
         w = int(rng.choice([1, 3, 8, 9, 31, 127, 129, 200, 255, 256, 257, 263, 500, 511, 512,
                             513, 700, 1030]))
         h = int(rng.choice([1, 2, 5, 16, 33, 90, 161]))
-        r = int(rng.integers(4 if K == 8 else 2, 16))
-        L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32]))
+        r = int(rng.integers({8: 4, 4: 2, 2: 1}[K], 16))
+        L = int(rng.choice([1, 2, 3, 7, 16, 20, 31, 32] + ([33, 47, 63, 64] if K == 2 else [])))
         bpp = int(rng.choice([3, 4]))
         pad = int(rng.choice([0, 1, 4, 13]))
         mode = int(rng.choice([0, 1, B.OP_LITERAL, B.OP_LITERAL | 1]))
@@ -224,19 +225,24 @@ def test_fuzz_straight_line_path(k, w, h, r, L, bpp, pad, mode, cfg):
         boxw = -(-K * (nt - 1 + (2 * r + K - 1) // K + 1) // 4) * 4
         half = -(-boxw * cfg["chunk_rows"] * 4 // 128) * 128
         slots = cfg["prefetch"] + 1
-        hist = ((nb + K - 1) * 8 + -(-(K - 1) // 4) * 4) * L * nt
+        hist = (((nb + K - 1) * 8 + -(-(K - 1) // 4) * 4) * L if K > 2 else
+                16 * L + -(-L // 4) * 4) * nt
         smem = 128 + -(-slots * 8 // 128) * 128 + 2 * half * slots + hist
         assert smem > 226 * 1024, (cfg, r, L, smem)
 
 
-@pytest.mark.parametrize("r", list(range(2, 16)))
+@pytest.mark.parametrize("r", list(range(1, 16)))
 def test_straight_line_every_radius(r):
-    """Every radius of the straight-line path, four and eight columns per
-    thread, the window histogram in one and two parts, 32 and 64 threads,
-    RGB and RGBA, on an image whose width is not a tile multiple."""
+    """Every radius of the straight-line path, two, four and eight columns
+    per thread, the window histogram in one and two parts, 32 and 64 threads,
+    RGB and RGBA, on an image whose width is not a tile multiple; two columns
+    also at 64 levels."""
     img = synth.camera_like(97, 601, seed=40 + r, npoly=30, rad_range=(3, 150))
+    for nt, L in ((32, 20), (64, 64)):
+        check_case(img, r, L, bpp=4 if L == 20 else 3, pad=0 if L == 20 else 7,
+                   config={"tile_w": 2 * nt, "cols_per_thread": 2, "chunk_rows": 2, "path": 2})
     for K in (4, 8):
-        if K == 8 and r < 4:
+        if r < {4: 2, 8: 4}[K]:
             continue
         for path, nt, bpp, pad, ch in ((2, 32, 4, 0, 2), (3, 64, 3, 5, 1), (2, 64, 3, 1, 1),
                                        (3, 32, 4, 8, 3)):
@@ -245,14 +251,18 @@ def test_straight_line_every_radius(r):
                                "path": path})
 
 
-@pytest.mark.parametrize("K,path,r,L", [(8, 0, 3, 20), (8, 2, 16, 20), (8, 3, 15, 33),
-                                        (4, 2, 1, 20), (4, 3, 16, 20), (4, 2, 15, 64),
-                                        (8, 0, 0, 1)])
-def test_straight_line_refused_outside_its_range(K, path, r, L):
+@pytest.mark.parametrize("K,path,r,L,status", [
+    (8, 0, 3, 20, B.OP_E_UNSUPPORTED), (8, 2, 16, 20, B.OP_E_UNSUPPORTED),
+    (8, 3, 15, 33, B.OP_E_UNSUPPORTED), (4, 2, 1, 20, B.OP_E_UNSUPPORTED),
+    (4, 3, 16, 20, B.OP_E_UNSUPPORTED), (4, 2, 15, 64, B.OP_E_UNSUPPORTED),
+    (8, 0, 0, 1, B.OP_E_UNSUPPORTED), (2, 2, 0, 20, B.OP_E_UNSUPPORTED),
+    (2, 2, 16, 20, B.OP_E_UNSUPPORTED), (2, 2, 15, 65, B.OP_E_UNSUPPORTED),
+    (2, 3, 5, 20, B.OP_E_INVALID)])
+def test_straight_line_refused_outside_its_range(K, path, r, L, status):
     op = OilPaint(300, 40, r, L)
     with pytest.raises(B.OilPaintError) as e:
         op.set_config({"tile_w": 32 * K, "cols_per_thread": K, "path": path})
-    assert e.value.status == B.OP_E_UNSUPPORTED
+    assert e.value.status == status
     op.close()
 
 
