@@ -2006,19 +2006,23 @@ __device__ bool run_tile_deltak(const ImgDesc &d, const CUtensorMap *tmap, int x
         if constexpr (K == 2) {
           // windows 0 and 1 as the halves of one word: 16-bit keys
           // (count << 6) | (63 - level), below 2^16 for count <= 961; window
-          // 1 adds D_1's signed count (byte lv & 3 of the level group's word)
-          // times 64 to the high half, whose sum stays in [0, 2^16)
+          // 1 adds D_1's signed count times 64 to the high half, whose sum
+          // stays in [0, 2^16).  The four levels' counts share a word as
+          // signed bytes, linear mod 2^32 (a negative byte borrows from the
+          // next), so the word plus 0x80808080 holds each count plus 128 as
+          // an unsigned byte, no carry between them.
           uint32_t b01 = 0u;
           for (uint32_t lq = 0; lq < L; lq += 4u) {
-            const uint32_t dw = lds_u32(o.dc0 + (lq >> 2) * O::kDW);
+            const uint32_t dw = lds_u32(o.dc0 + (lq >> 2) * O::kDW) + 0x80808080u;
 #pragma unroll
             for (uint32_t k = 0; k < 4u; ++k) {
               const uint32_t lv = lq + k;
               if (lv >= L) break;
               const uint32_t c = lds_u32(o.h0 + lv * O::kLS);
-              const int32_t d1 = static_cast<int32_t>(dw << (24u - 8u * k)) >> 24;
+              // (count + 128) << 22, less 128 << 22: the count times 64 in the high half
+              const uint32_t x = (((dw >> (8u * k)) & 0xFFu) << 22) - (128u << 22);
               const uint32_t k0 = ((c << 6) & 0xFFC0u) | (63u - lv);
-              b01 = __viaddmax_u16x2(k0 * 0x00010001u, static_cast<uint32_t>(d1) << 22, b01);
+              b01 = __viaddmax_u16x2(k0 * 0x00010001u, x, b01);
             }
           }
           auto key32 = [](uint32_t h) { return (h & 0xFFC0u) << 16 | (h & 63u); };
