@@ -366,6 +366,9 @@ def run_ours(args):
     if not args.skip_batch:
         from paper_1405_1020_gb300 import batchbench
         line["batched"] = batchbench.run(steps=max(3, args.steps // 2), warmup=2)
+    if not args.skip_jpeg and rank == 0:
+        from paper_1405_1020_gb300 import jpegbench
+        line["jpeg_pipeline"] = jpegbench.run()
     if args.serve_seconds > 0:
         from paper_1405_1020_gb300 import serve
         line["served"] = serve.bench_loads(seconds=args.serve_seconds,
@@ -399,6 +402,8 @@ def main(argv=None):
     p.add_argument("--config", default=None, help="launch config JSON, e.g. '{\"tile_w\": 64}'")
     p.add_argument("--autotune", action="store_true", help="search the launch config first")
     p.add_argument("--skip-batch", action="store_true")
+    p.add_argument("--skip-jpeg", action="store_true",
+                   help="skip the decode -> filter -> encode timing")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="seconds of served traffic per configured offered load (0 skips "
                         "serving)")

@@ -6,6 +6,12 @@ allocation-free entry point with its device scratch array) are compiled in
 parallel with nvcc and linked into one shared library with the CUDA runtime linked statically, so
 the library needs nothing but the NVIDIA driver at run time.  The library is
 built in-tree (the package directory) and git-ignored.
+
+build_jpeg() then builds liboilpaint_jpeg.so, the decode -> filter -> encode
+pipeline (include/oilpaint_jpeg.h): one host translation unit linked against
+liboilpaint.so (found beside it at run time) and the toolkit's nvJPEG.  It is
+skipped, with a note, when the toolkit has no nvJPEG; the filter library does
+not depend on it.
 """
 from __future__ import annotations
 
@@ -83,12 +89,66 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: b
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "-soname=" + os.path.basename(lib), "-o", tmp,
+           *objs]
     subprocess.run(cmd, check=True)
     os.replace(tmp, lib)
     return lib
 
 
+JPEG_LIB = os.path.join(PKG, "liboilpaint_jpeg.so")
+JPEG_SOURCE = "oilpaint_jpeg.cu"
+
+
+def nvjpeg_dirs():
+    """(include dir, library dir) of the toolkit's nvJPEG, or None."""
+    home = os.path.dirname(os.path.dirname(os.path.realpath(_nvcc())))
+    inc = os.path.join(home, "include")
+    if not os.path.exists(os.path.join(inc, "nvjpeg.h")):
+        return None
+    cands = [os.path.join(home, "lib64"), os.path.join(home, "lib")]
+    tdir = os.path.join(home, "targets")
+    if os.path.isdir(tdir):
+        cands += [os.path.join(tdir, t, "lib") for t in sorted(os.listdir(tdir))]
+    for d in cands:
+        if os.path.exists(os.path.join(d, "libnvjpeg.so")):
+            return inc, d
+    return None
+
+
+def build_jpeg(force: bool = False, verbose: bool = False):
+    """Build liboilpaint_jpeg.so if missing or stale; None when nvJPEG is absent."""
+    dirs = nvjpeg_dirs()
+    if dirs is None:
+        print("oilpaint: nvJPEG not found in the CUDA toolkit; liboilpaint_jpeg.so not built")
+        return None
+    inc, libdir = dirs
+    deps = [os.path.join(CSRC, JPEG_SOURCE), os.path.join(INCLUDE, "oilpaint_jpeg.h"),
+            os.path.join(INCLUDE, "oilpaint.h"), os.path.abspath(__file__), LIB]
+    if (not force and os.path.exists(JPEG_LIB)
+            and all(os.path.getmtime(d) <= os.path.getmtime(JPEG_LIB) for d in deps)):
+        return JPEG_LIB
+    nvcc = _nvcc()
+    bdir = os.path.join(PKG, "_build")
+    os.makedirs(bdir, exist_ok=True)
+    obj = os.path.join(bdir, JPEG_SOURCE.replace(".cu", ".o"))
+    cmd = [nvcc, *ARCH, *FLAGS, "-I", inc, "-c", os.path.join(CSRC, JPEG_SOURCE), "-o", obj]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    tmp = JPEG_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "-soname=liboilpaint_jpeg.so", "-o", tmp, obj,
+           "-L", PKG, "-loilpaint", "-L", libdir, "-lnvjpeg",
+           "-Xlinker", "-rpath=$ORIGIN", "-Xlinker", "-rpath=" + libdir]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, JPEG_LIB)
+    return JPEG_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 checked="--checked" in sys.argv))
+    if "--checked" not in sys.argv:
+        print(build_jpeg(force="--force" in sys.argv, verbose="-v" in sys.argv))

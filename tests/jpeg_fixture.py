@@ -1,0 +1,103 @@
+"""Test helpers for the JPEG pipeline: a writer of baseline grayscale JPEGs
+whose 8x8 blocks are flat, and a reader of JPEG frame headers.
+
+The writer follows ITU-T T.81 (baseline sequential DCT, Huffman coded) for
+the one case whose decoded pixels are known exactly without a decoder: every
+block constant.  A block of value v has only a DC coefficient, 8 (v - 128)
+(the forward DCT of a constant block), all quantisers are 1, and the inverse
+DCT of a DC-only block is DC / 8 everywhere, so a conforming decoder
+reproduces v exactly.  The stream carries its own Huffman tables (T.81
+allows any): DC categories 0..11 get the 4-bit codes 0000..1011 and the AC
+table holds only end-of-block, code 0.  No filter arithmetic here.
+"""
+from __future__ import annotations
+
+import struct
+
+import numpy as np
+
+
+def _segment(marker: int, payload: bytes) -> bytes:
+    return struct.pack(">HH", marker, len(payload) + 2) + payload
+
+
+class _Bits:
+    def __init__(self):
+        self.out = bytearray()
+        self.acc = 0
+        self.n = 0
+
+    def put(self, value: int, nbits: int):
+        for i in range(nbits - 1, -1, -1):
+            self.acc = (self.acc << 1) | ((value >> i) & 1)
+            self.n += 1
+            if self.n == 8:
+                self.out.append(self.acc)
+                if self.acc == 0xFF:        # byte stuffing (T.81 F.1.2.3)
+                    self.out.append(0x00)
+                self.acc, self.n = 0, 0
+
+    def flush(self) -> bytes:
+        if self.n:                          # pad with 1-bits
+            self.put((1 << (8 - self.n)) - 1, 8 - self.n)
+        return bytes(self.out)
+
+
+def flat_gray_jpeg(blocks: np.ndarray) -> bytes:
+    """Baseline grayscale JPEG of a (by, bx) array of block values (uint8):
+    the image is (8 by) x (8 bx) pixels, block (i, j) filled with blocks[i, j]."""
+    blocks = np.asarray(blocks, dtype=np.int64)
+    by, bx = blocks.shape
+    h, w = 8 * by, 8 * bx
+    out = bytearray(b"\xff\xd8")                                            # SOI
+    out += _segment(0xFFDB, bytes([0x00]) + bytes([1] * 64))                # DQT: table 0, all 1
+    out += _segment(0xFFC0, struct.pack(">BHHB", 8, h, w, 1) + bytes([1, 0x11, 0]))  # SOF0
+    dc_bits = [0, 0, 0, 12] + [0] * 12                                       # 12 codes of length 4
+    out += _segment(0xFFC4, bytes([0x00] + dc_bits + list(range(12))))      # DHT: DC table 0
+    ac_bits = [1] + [0] * 15                                                 # 1 code of length 1
+    out += _segment(0xFFC4, bytes([0x10] + ac_bits + [0x00]))               # DHT: AC table 0 (EOB)
+    out += _segment(0xFFDA, bytes([1, 1, 0x00, 0, 63, 0]))                  # SOS
+    bits = _Bits()
+    pred = 0
+    for v in blocks.reshape(-1):                                            # raster order of blocks
+        dc = 8 * (int(v) - 128)
+        diff = dc - pred
+        pred = dc
+        size = 0 if diff == 0 else abs(diff).bit_length()                   # category (T.81 F.1.2.1)
+        bits.put(size, 4)                                                   # its code
+        if size:
+            bits.put(diff if diff > 0 else diff + (1 << size) - 1, size)    # additional bits
+        bits.put(0, 1)                                                      # EOB
+    out += bits.flush()
+    out += b"\xff\xd9"                                                      # EOI
+    return bytes(out)
+
+
+def flat_gray_image(blocks: np.ndarray) -> np.ndarray:
+    """The (8 by) x (8 bx) grayscale image flat_gray_jpeg(blocks) encodes."""
+    return np.kron(np.asarray(blocks, dtype=np.uint8), np.ones((8, 8), dtype=np.uint8))
+
+
+def frame_header(data: bytes) -> dict:
+    """Width, height, components and their sampling factors from the first
+    SOF marker; checks that the stream starts with SOI and ends with EOI."""
+    assert data[:2] == b"\xff\xd8", "no SOI"
+    assert data[-2:] == b"\xff\xd9", "no EOI"
+    i = 2
+    while i + 4 <= len(data):
+        assert data[i] == 0xFF, f"marker expected at {i}"
+        marker = data[i + 1]
+        if marker == 0xFF:          # fill byte
+            i += 1
+            continue
+        length = struct.unpack(">H", data[i + 2:i + 4])[0]
+        if marker in (0xC0, 0xC1, 0xC2):
+            p, h, w, nf = struct.unpack(">BHHB", data[i + 4:i + 10])
+            comps = [(data[i + 10 + 3 * k], data[i + 11 + 3 * k] >> 4, data[i + 11 + 3 * k] & 15)
+                     for k in range(nf)]
+            return {"precision": p, "width": w, "height": h, "components": nf,
+                    "sampling": [(hs, vs) for _, hs, vs in comps], "sof": marker}
+        if marker == 0xDA:
+            break
+        i += 2 + length
+    raise AssertionError("no SOF marker before the scan")

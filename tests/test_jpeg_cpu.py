@@ -1,0 +1,84 @@
+"""The JPEG pipeline library (include/oilpaint_jpeg.h) builds, loads and
+exports every declared entry point, its argument checks that come before any
+CUDA call behave, and the test JPEG writer produces well-formed streams.  No
+GPU needed."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1405_1020_gb300 import jpeg as J
+from paper_1405_1020_gb300.binding import OP_E_INVALID, OP_OK
+from paper_1405_1020_gb300.csrc import build as cbuild
+from tests.jpeg_fixture import flat_gray_image, flat_gray_jpeg, frame_header
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "oilpaint_jpeg.h")
+
+
+def declared():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(op_jpeg_[a-z_]+)\s*\(", text)))
+
+
+def header_constants():
+    text = open(HEADER).read()
+    return {m.group(1): int(m.group(2))
+            for m in re.finditer(r"#define\s+(OP_\w+)\s+\(?(-?\d+)\)?", text)}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cbuild.build()
+    if cbuild.build_jpeg() is None:
+        pytest.skip("nvJPEG is not in this CUDA toolkit")
+    return J.load()
+
+
+def test_header_and_binding_agree():
+    assert sorted(J.EXPORTS) == declared()
+    consts = header_constants()
+    for name in ("OP_E_CODEC", "OP_E_NOSPACE", "OP_JPEG_CSS_444", "OP_JPEG_CSS_422",
+                 "OP_JPEG_CSS_420"):
+        assert consts[name] == getattr(J, name), name
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def test_null_handles(lib):
+    import ctypes
+    n = ctypes.c_size_t()
+    w = ctypes.c_uint32()
+    assert J.op_jpeg_info(None, b"\xff\xd8", w, None, None) == OP_E_INVALID
+    assert J.op_jpeg_decode(None, b"\xff\xd8", 1 << 20, 30) == OP_E_INVALID
+    assert J.op_jpeg_encode_bound(None, 10, 10, 90, 0, n) == OP_E_INVALID
+    assert J.op_jpeg_encode(None, 1 << 20, 10, 10, 30, 90, 0, None, 0, n) == OP_E_INVALID
+    assert J.op_jpeg_filter(None, b"\xff\xd8", 2, 20, 0, 90, 0, None, 0, n) == OP_E_INVALID
+    assert J.op_jpeg_filter_file(None, "a.jpg", "b.jpg", 2, 20, 0, 90, 0) == OP_E_INVALID
+    assert J.op_jpeg_last_timing(None, J.op_jpeg_timing_t()) == OP_E_INVALID
+    assert J.op_jpeg_destroy(None) == OP_OK
+
+
+def test_status_strings():
+    assert "nvJPEG" in J.status_string(J.OP_E_CODEC)
+    assert "small" in J.status_string(J.OP_E_NOSPACE)
+
+
+def test_flat_gray_writer():
+    rng = np.random.default_rng(0)
+    blocks = rng.integers(0, 256, size=(5, 7)).astype(np.uint8)
+    blocks[0, 0], blocks[0, 1] = 0, 255
+    data = flat_gray_jpeg(blocks)
+    hdr = frame_header(data)
+    assert hdr == {"precision": 8, "width": 56, "height": 40, "components": 1,
+                   "sampling": [(1, 1)], "sof": 0xC0}
+    # entropy-coded data: every 0xFF is stuffed, so the only markers left are SOS's and EOI
+    scan = data[data.index(b"\xff\xda") + 2 + 8:-2]
+    for i in np.flatnonzero(np.frombuffer(scan, dtype=np.uint8) == 0xFF):
+        assert scan[i + 1] == 0x00
+    img = flat_gray_image(blocks)
+    assert img.shape == (40, 56) and img[8 * 4 + 3, 8 * 6 + 5] == blocks[4, 6]
