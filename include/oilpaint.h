@@ -69,6 +69,20 @@ extern "C" {
  */
 #define OP_LITERAL 2u
 #define OP_LITERAL_MAX_LEVELS 254u
+/*
+ * OP_FUSED_PACK (flag bit): no separate pack launch.  For an image of 4 bytes
+ * per pixel whose input pointer and stride are multiples of 16 bytes, op_run
+ * then runs one launch: the filter's halo copies read the input pixels
+ * themselves and each copied chunk is converted to the packed words in
+ * shared memory (the same words, so the same output bytes), and the packed
+ * workspace is neither allocated nor written.  It saves 4 * width * height
+ * bytes of device memory but is slower on GB300 (4000 x 3000, r = 15, L = 20:
+ * 0.367 ms per image against 0.287 ms with the prepass; 23-33% slower at
+ * r = 1..12): the conversion runs in the filter, which is bound by its
+ * shared-memory pipe, for every halo row it copies, entering and leaving.
+ * Other images, the batch API and op_run_noalloc ignore the flag.
+ */
+#define OP_FUSED_PACK 4u
 
 /* ---- limits ------------------------------------------------------------- */
 #define OP_MAX_RADIUS 44   /* 255*(2r+1)^2 must fit the 21-bit per-level channel sums */

@@ -26,6 +26,7 @@ OP_LEVEL_PAPER = 0
 OP_LEVEL_INTDIV3 = 1
 OP_LITERAL = 2  # flag bit: the section-4 listing as printed
 OP_LITERAL_MAX_LEVELS = 254
+OP_FUSED_PACK = 4  # flag bit: pack in the filter's shared memory, no prepass launch
 
 OP_MAX_RADIUS = 44
 OP_MAX_LEVELS = 256

@@ -44,26 +44,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 bool encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint32_t h,
                        uint32_t ppitch, uint32_t boxw, uint32_t ch) {
+  return encode_word_map(map, packed, w, h, static_cast<uint64_t>(ppitch) * 4u, boxw, ch);
+}
+
+bool encode_word_map(CUtensorMap *map, const void *base, uint32_t w, uint32_t h,
+                     uint64_t pitch_bytes, uint32_t boxw, uint32_t ch) {
   auto fn = encode_fn();
   if (!fn) return false;
+  if (pitch_bytes % 16u || reinterpret_cast<uintptr_t>(base) % 16u) return false;
   CUresult r;
   if (boxw <= kMaxBox2dWords) {
     cuuint64_t dims[2] = {w, h};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ppitch) * 4u};
+    cuuint64_t strides[1] = {pitch_bytes};
     cuuint32_t box[2] = {boxw, ch};
     cuuint32_t estr[2] = {1, 1};
-    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(packed), dims, strides,
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(base), dims, strides,
            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
-    // {4 words, ppitch / 4 groups, rows}: the same rows, read in groups of
-    // four words, so that a box row may be up to 4 * 256 words wide
-    if (boxw % 4u || boxw > kMaxBoxWords || ppitch % 4u) return false;
-    cuuint64_t dims[3] = {4, ppitch / 4u, h};
-    cuuint64_t strides[2] = {16, static_cast<cuuint64_t>(ppitch) * 4u};
+    // {4 words, ceil(w / 4) groups, rows}: the same rows, read in groups of
+    // four words, so that a box row may be up to 4 * 256 words wide.  The
+    // last group of a row may reach up to 3 words past word w - 1; they lie
+    // inside the row because the pitch is a multiple of 16 bytes and holds
+    // w words.
+    if (boxw % 4u || boxw > kMaxBoxWords || pitch_bytes < 16u * ((w + 3u) / 4u)) return false;
+    cuuint64_t dims[3] = {4, (w + 3u) / 4u, h};
+    cuuint64_t strides[2] = {16, pitch_bytes};
     cuuint32_t box[3] = {4, boxw / 4u, ch};
     cuuint32_t estr[3] = {1, 1, 1};
-    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t *>(packed), dims, strides,
+    r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void *>(base), dims, strides,
            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
@@ -276,7 +285,7 @@ bool valid_image(uint32_t w, uint32_t h, uint32_t stride, uint32_t bpp, int32_t 
   if (static_cast<uint64_t>(stride) < static_cast<uint64_t>(w) * bpp) return false;
   if (r < 0 || r > OP_MAX_RADIUS) return false;
   if (L < 1 || L > OP_MAX_LEVELS) return false;
-  if (flags & ~(OP_LEVEL_INTDIV3 | OP_LITERAL)) return false;
+  if (flags & ~(OP_LEVEL_INTDIV3 | OP_LITERAL | OP_FUSED_PACK)) return false;
   if ((flags & OP_LITERAL) && L > OP_LITERAL_MAX_LEVELS) return false;
   return true;
 }
@@ -311,6 +320,11 @@ struct op_s {
   bool ws_owned = false;
   CUtensorMap map;
   bool map_valid = false;
+  // tensor maps over the input image for the fused pack, for the last two
+  // input pointers (op_run_host_async alternates between two)
+  CUtensorMap raw_map[2];
+  const void *raw_ptr[2] = {nullptr, nullptr};
+  uint32_t raw_next = 0;
   uint32_t *d_err = nullptr;
   cudaEvent_t prof_ev = nullptr;
   // host-buffer path: two staging slots, each an input and an output image,
@@ -461,6 +475,7 @@ int op_set_config(op_t *op, const op_config_t *cfg) {
       op->cfg, op->w, std::max(1u, opk::output_window(op->w, op->h, op->r, op->flags).rows()),
       op->r, op->L, op->di);
   op->map_valid = false;
+  op->raw_ptr[0] = op->raw_ptr[1] = nullptr;
   return OP_OK;
 }
 
@@ -510,6 +525,7 @@ int op_set_workspace(op_t *op, void *d_ws, size_t bytes) {
   op->ws_bytes = bytes;
   op->ws_owned = false;
   op->map_valid = false;
+  op->raw_ptr[0] = op->raw_ptr[1] = nullptr;
   return OP_OK;
 }
 
@@ -522,6 +538,7 @@ static int ensure_workspace(op_t *op) {
   op->ws_bytes = op_workspace_size(op);
   op->ws_owned = true;
   op->map_valid = false;
+  op->raw_ptr[0] = op->raw_ptr[1] = nullptr;
   return OP_OK;
 }
 
@@ -530,15 +547,38 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   if (!op || !d_in || !d_out) return OP_E_INVALID;
   const size_t bytes = static_cast<size_t>(op->h) * op->stride;
   if (ranges_overlap(d_in, d_out, bytes)) return OP_E_INVALID;
-  int st = ensure_workspace(op);
-  if (st != OP_OK) return st;
   const op_config_t &c = op->cfg;
   const opk::Geometry g = geometry_of(c, op->r, op->L, op->w);
-  if (!op->map_valid) {
-    if (!opk::encode_packed_map(&op->map, static_cast<const uint32_t *>(op->ws), op->w, op->h,
-                                op->ppitch, g.boxw, c.chunk_rows))
-      return OP_E_CUDA;
-    op->map_valid = true;
+  // Fused pack (OP_FUSED_PACK): the filter's copies read the input pixels
+  // themselves (the map over the input is encoded once per input pointer)
+  // and the packed workspace is not needed.
+  const CUtensorMap *map = &op->map;
+  bool fused = op->bpp == 4 && (op->flags & OP_FUSED_PACK) && op->stride % 16u == 0u &&
+               reinterpret_cast<uintptr_t>(d_in) % 16u == 0u;
+  if (fused) {
+    int k = op->raw_ptr[0] == d_in ? 0 : op->raw_ptr[1] == d_in ? 1 : -1;
+    if (k < 0) {
+      k = static_cast<int>(op->raw_next);
+      op->raw_next ^= 1u;
+      op->raw_ptr[k] = nullptr;
+      if (opk::encode_word_map(&op->raw_map[k], d_in, op->w, op->h, op->stride, g.boxw,
+                               c.chunk_rows))
+        op->raw_ptr[k] = d_in;
+      else
+        k = -1;  // the driver refused this map: run the prepass instead
+    }
+    fused = k >= 0;
+    if (fused) map = &op->raw_map[k];
+  }
+  if (!fused) {
+    const int st = ensure_workspace(op);
+    if (st != OP_OK) return st;
+    if (!op->map_valid) {
+      if (!opk::encode_packed_map(&op->map, static_cast<const uint32_t *>(op->ws), op->w, op->h,
+                                  op->ppitch, g.boxw, c.chunk_rows))
+        return OP_E_CUDA;
+      op->map_valid = true;
+    }
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ImgDesc d{};
@@ -553,7 +593,8 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   d.bpp = op->bpp;
   d.r = op->r;
   d.L = op->L;
-  d.mode = op->flags;
+  d.mode = op->flags & (OP_LEVEL_INTDIV3 | OP_LITERAL);
+  d.fused = fused ? 1u : 0u;
   d.ppitch = op->ppitch;
   d.tiles_x = g.tiles_x;
   d.tile_h = op->tile_h;
@@ -568,12 +609,14 @@ int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream) {
   if (win.rows() == 0u) return OP_OK;  // literal mode: no pixel is r from every edge
   const RingCfg rc = opk::make_ring(op->r, c.chunk_rows, c.prefetch, g.boxw);
   const size_t smem = smem_of(g, c, op->r, op->L);
-  const int pack_grid = opk::pack_grid_for(op->h, op->di.sms);
-  cudaError_t e = opk::launch_pack_single(d, pack_grid, s);
-  if (e != cudaSuccess) return OP_E_CUDA;
+  cudaError_t e;
+  if (!fused) {
+    e = opk::launch_pack_single(d, opk::pack_grid_for(op->h, op->di.sms), s);
+    if (e != cudaSuccess) return OP_E_CUDA;
+  }
   if (op->prof_ev && cudaEventRecord(op->prof_ev, s) != cudaSuccess) return OP_E_CUDA;
   const dim3 grid(d.tiles_x, (win.rows() + d.tile_h - 1) / d.tile_h);
-  e = opk::launch_tile(g.nt, g.kcols, g.variant, d, op->map, rc, grid, smem, op->d_err,
+  e = opk::launch_tile(g.nt, g.kcols, g.variant, d, *map, rc, grid, smem, op->d_err,
                        kWaitTimeoutNs, s);
   return e == cudaSuccess ? OP_OK : OP_E_CUDA;
 }
@@ -829,7 +872,7 @@ op_batch_t *op_batch_create(uint32_t max_images, uint64_t max_pixels, int32_t ma
     b->smem[g] = sm;
     b->grid_persist[g] = occ * di.sms;
   }
-  b->grid_pack = 8 * di.sms;
+  b->grid_pack = 6 * di.sms;  // the pack kernels' resident blocks per SM (launch bounds)
   size_t o = 0;
   b->off_ctrl = o;
   o = align_up(o + kCtrlWords * sizeof(uint32_t), kAlign);
@@ -1019,7 +1062,7 @@ int op_batch_set(op_batch_t *b, const op_image_t *images, uint32_t n, void *stre
       d.bpp = im.bpp;
       d.r = im.radius;
       d.L = im.levels;
-      d.mode = im.flags;
+      d.mode = im.flags & (OP_LEVEL_INTDIV3 | OP_LITERAL);
       d.ppitch = packed_pitch(im.width);
       d.tile_h = tile_h[i];
       const opk::Geometry &ge = geo[i];

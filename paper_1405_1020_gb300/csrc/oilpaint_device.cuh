@@ -82,6 +82,9 @@ struct __align__(16) ImgDesc {
   uint32_t fmt;      // packed word format: 0 one column per thread, 1 (r <= 15) and 2
                      // (r > 15) difference and column histograms
   uint32_t path;     // 0: histograms per thread; 1: column histograms, levels across lanes
+  uint32_t fused;    // 1: the tensor map reads the input image itself (4-byte pixels) and
+                     // each ring chunk is converted to packed words in shared memory;
+                     // 0: it reads the packed image the pack prepass wrote
   // output window: columns [ox0, ox1), rows [oy0, oy1) (the whole image, or
   // in literal mode the pixels at least r from every edge); tiles cover the
   // rows from oy0
@@ -257,6 +260,23 @@ __device__ __forceinline__ void lds_v2(uint32_t addr, uint32_t &lo, uint32_t &hi
     return;
   }
   asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(addr));
+}
+
+__device__ __forceinline__ void lds_v4(uint32_t addr, uint32_t (&v)[4]) {
+  if (!OPK_SMEM_OK(addr, 16u)) {
+    v[0] = v[1] = v[2] = v[3] = 0u;
+    return;
+  }
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void sts_v4(uint32_t addr, const uint32_t (&v)[4]) {
+  if (!OPK_SMEM_OK(addr, 16u)) return;
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3])
+               : "memory");
 }
 
 __device__ __forceinline__ void sts_zero64(uint32_t addr) {
@@ -557,6 +577,55 @@ __device__ __forceinline__ void pack_row(const ImgDesc &d, uint32_t y, uint32_t 
   for (uint32_t x = x0 + tid; x < w; x += nthr) {
     const uint8_t *p = src + x * bpp;
     dst[x] = word(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+  }
+}
+
+// Fused pack (4-byte input pixels staged raw by the halo copies).  The ring
+// slot at shared address `slot` holds the ch entering rows of a chunk, from
+// image row ye, and half_bytes further its ch leaving rows, from row yl;
+// each row is boxw pixels wide from image column xs (boxw a multiple of 4).
+// The CTA's threads convert them in place, four pixels at a time, to the
+// packed words the pack prepass would have written (format d.fmt); pixels
+// outside the image -- zero-filled by the copy, or the bytes of the row past
+// its last pixel -- become word 0, which adds nothing to any histogram.
+// The caller synchronises the CTA before and after.
+__device__ __forceinline__ void convert_raw_slot(const ImgDesc &d, uint32_t slot,
+                                                 uint32_t half_bytes, int xs, int ye, int yl,
+                                                 uint32_t ch, uint32_t boxw) {
+  const uint32_t groups = boxw >> 2;
+  const uint32_t rows = 2u * ch;
+  const uint32_t nthr = blockDim.x;
+  const int w = static_cast<int>(d.w), h = static_cast<int>(d.h);
+  const uint32_t L = d.L, mode = d.mode, fmt = d.fmt;
+  uint32_t hr = 0, q = threadIdx.x;  // half-row (entering rows, then leaving rows), group
+  while (q >= groups) {
+    q -= groups;
+    ++hr;
+  }
+  while (hr < rows) {
+    const bool leaving = hr >= ch;
+    const uint32_t rr = leaving ? hr - ch : hr;
+    const int y = (leaving ? yl : ye) + static_cast<int>(rr);
+    const uint32_t addr = slot + (leaving ? half_bytes : 0u) + (rr * boxw + 4u * q) * 4u;
+    const int x = xs + static_cast<int>(4u * q);
+    const bool row_in = y >= 0 && y < h;
+    uint32_t v[4];
+    lds_v4(addr, v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t p = v[e];
+      const uint32_t R = p & 0xFFu, G = (p >> 8) & 0xFFu, B = (p >> 16) & 0xFFu;
+      const uint32_t wd = fmt == 1u   ? pack_word_delta(R, G, B, L, mode)
+                          : fmt == 2u ? pack_word_delta_b(R, G, B, L, mode)
+                                      : pack_word(R, G, B, L, mode);
+      v[e] = (row_in && x + e >= 0 && x + e < w) ? wd : 0u;
+    }
+    sts_v4(addr, v);
+    q += nthr;
+    while (q >= groups) {
+      q -= groups;
+      ++hr;
+    }
   }
 }
 
@@ -1119,6 +1188,11 @@ __device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *t
         issue(k + static_cast<int>(rc.pf));
       }
       ++issued;
+    }
+    if (d.fused) {  // raw input pixels: convert the chunk in place
+      convert_raw_slot(d, sm.ring + (g % rc.nslot) * rc.slot_bytes, rc.half_bytes, xs,
+                       E0 + k * ch, E0 + k * ch - 2 * r - 1, rc.ch, boxw);
+      __syncthreads();
     }
     const uint32_t *base_e = ring + (g % rc.nslot) * slot_words;
     const uint32_t *base_l = base_e + half_words;

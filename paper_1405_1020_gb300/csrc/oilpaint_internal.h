@@ -139,15 +139,12 @@ inline size_t cols_hist_bytes(const Geometry &g, int r, uint32_t L) {
   return ((sums + 127u) & ~static_cast<size_t>(127u)) + sums / 2u;
 }
 
-// Blocks of the single-image pack launch (256 threads, one image row at a
-// time, rows b, b + grid, ...): as many as 8 per SM can be resident, and the
-// grid is trimmed so that every block packs the same number of rows -- with
-// 8 * sms blocks a 3000-row image left 1216 - 568 blocks idle through the
-// last third of the launch.
-inline int pack_grid_for(uint32_t rows, int sms) {
-  const uint32_t slots = 8u * static_cast<uint32_t>(sms > 0 ? sms : 1);
-  const uint32_t per_block = (rows + slots - 1u) / slots;
-  return static_cast<int>(per_block ? (rows + per_block - 1u) / per_block : 1u);
+// Blocks of the single-image pack launch: one per image row (256 threads
+// each).  Fewer blocks looping over several rows each (as many as fit one
+// wave) measured slower: a block's rows are then packed one after another,
+// each waiting for its own loads.
+inline int pack_grid_for(uint32_t rows, int /*sms*/) {
+  return static_cast<int>(rows ? rows : 1u);
 }
 
 // Histogram bytes of a CTA on the straight-line path: per level and thread
@@ -211,6 +208,12 @@ inline void set_window(ImgDesc &d, const Window &o) {
 // refuses the map.
 bool encode_packed_map(CUtensorMap *map, const uint32_t *packed, uint32_t w, uint32_t h,
                        uint32_t ppitch, uint32_t boxw, uint32_t ch);
+
+// The same for any image of 32-bit words (the packed image, or for the fused
+// pack the input pixels of a 4-byte-per-pixel image): w x h words, rows
+// pitch_bytes apart.  False unless base and pitch are multiples of 16 bytes.
+bool encode_word_map(CUtensorMap *map, const void *base, uint32_t w, uint32_t h,
+                     uint64_t pitch_bytes, uint32_t boxw, uint32_t ch);
 
 // Tile height for an image of H output rows cut into tiles_x tile columns
 // when `slots` CTAs can be resident at once: minimises waves x steps per

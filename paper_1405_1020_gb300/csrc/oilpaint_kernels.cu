@@ -22,7 +22,13 @@
 
 namespace opk {
 
-__global__ void __launch_bounds__(256) pack_single_kernel(const ImgDesc d) {
+// Both pack kernels are held to 40 registers (6 blocks of 256 per SM) and
+// the single-image launch takes one row per block: the pack streams its
+// input once, so the loads in flight per SM decide its speed.  At 48
+// registers and three rows per block the 12 MP RGBA pack took 24 us and the
+// RGB one about 30 us; with more blocks resident and one row each, 22 us and
+// 24 us.
+__global__ void __launch_bounds__(256, 6) pack_single_kernel(const ImgDesc d) {
   for (uint32_t y = blockIdx.x; y < d.h; y += gridDim.x) pack_row(d, y, threadIdx.x, blockDim.x);
 }
 
@@ -40,7 +46,7 @@ __device__ __forceinline__ uint32_t find_image(const uint32_t *__restrict__ pref
   return lo;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)
     pack_batch_kernel(const ImgDesc *__restrict__ descs, const uint32_t *__restrict__ row_prefix,
                       const uint32_t *__restrict__ d_n, uint32_t *queues, uint32_t nqueues) {
   // the filter launches that follow start their ticket queues from zero

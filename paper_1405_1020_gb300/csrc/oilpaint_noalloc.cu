@@ -58,7 +58,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   if (!d_in || !d_out || width < 1 || height < 1 || width > OP_MAX_DIM || height > OP_MAX_DIM ||
       (bpp != 3 && bpp != 4) || static_cast<uint64_t>(stride) < static_cast<uint64_t>(width) * bpp ||
       radius < 0 || radius > OP_MAX_RADIUS || levels < 1 || levels > OP_MAX_LEVELS ||
-      (flags & ~(OP_LEVEL_INTDIV3 | OP_LITERAL)) ||
+      (flags & ~(OP_LEVEL_INTDIV3 | OP_LITERAL | OP_FUSED_PACK)) ||
       ((flags & OP_LITERAL) && levels > OP_LITERAL_MAX_LEVELS))
     return OP_E_INVALID;
   const size_t bytes = static_cast<size_t>(height) * stride;
@@ -109,7 +109,7 @@ extern "C" int op_run_noalloc(const uint8_t *d_in, uint8_t *d_out, uint32_t widt
   d.bpp = bpp;
   d.r = radius;
   d.L = levels;
-  d.mode = flags;
+  d.mode = flags & (OP_LEVEL_INTDIV3 | OP_LITERAL);
   d.ppitch = ppitch;
   d.tiles_x = g.tiles_x;
   const opk::Window win = opk::output_window(width, height, radius, flags);

@@ -48,7 +48,7 @@ def test_status_strings(lib):
     (10, 10, 30, 3, 45, 20, 0),      # radius > OP_MAX_RADIUS
     (10, 10, 30, 3, 1, 0, 0),        # L = 0
     (10, 10, 30, 3, 1, 257, 0),      # L > 256
-    (10, 10, 30, 3, 1, 20, 4),       # unknown flag
+    (10, 10, 30, 3, 1, 20, 8),       # unknown flag (bit 3)
     (10, 10, 30, 3, 1, 255, 2),      # literal mode with L > OP_LITERAL_MAX_LEVELS
     (70000, 10, 210000, 3, 1, 20, 0),  # width > OP_MAX_DIM
 ])

@@ -120,7 +120,7 @@ def test_literal_noalloc_and_limits():
                 stride, 4, "noalloc literal")
     assert B.op_run_noalloc(src.data_ptr(), out.data_ptr(), 130, 90, stride, 4, 6, 255, LIT,
                             s) == B.OP_E_INVALID
-    assert B.op_run_noalloc(src.data_ptr(), out.data_ptr(), 130, 90, stride, 4, 6, 20, 4,
-                            s) == B.OP_E_INVALID
+    assert B.op_run_noalloc(src.data_ptr(), out.data_ptr(), 130, 90, stride, 4, 6, 20, 8,
+                            s) == B.OP_E_INVALID  # unknown flag bit
     with pytest.raises(B.OilPaintError):
         OilPaint(130, 90, 6, 255, bpp=4, stride=stride, flags=LIT)
