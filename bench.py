@@ -310,7 +310,8 @@ def run_ours(args):
                 "kernel": kernel, "kernel_ms": round(f_ms, 4),
                 "pack_ms": round(statistics.mean(pack_ms), 4),
                 "ops_per_pixel": ops_per_pixel(RADIUS, LEVELS),
-                "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz",
+                "peak_source": f"{sms} SMs x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz "
+                               "(lanes measured: profiles/alu_peak_probe.md)",
                 "bounding_pipe": pipe}
 
     # end to end through the host-buffer entry points: every step copies its

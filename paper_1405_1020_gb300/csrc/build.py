@@ -147,6 +147,22 @@ def build_jpeg(force: bool = False, verbose: bool = False):
     return JPEG_LIB
 
 
+ALU_PROBE = os.path.join(PKG, "alu_probe")
+
+
+def build_alu_probe(force: bool = False) -> str:
+    """Build the integer-ALU throughput probe (alu_probe.cu), a standalone
+    program that measures the roofline denominator of the filter kernels."""
+    src = os.path.join(CSRC, "alu_probe.cu")
+    if (not force and os.path.exists(ALU_PROBE)
+            and os.path.getmtime(ALU_PROBE) >= os.path.getmtime(src)):
+        return ALU_PROBE
+    tmp = ALU_PROBE + f".tmp{os.getpid()}"
+    subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", tmp], check=True)
+    os.replace(tmp, ALU_PROBE)
+    return ALU_PROBE
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 checked="--checked" in sys.argv))

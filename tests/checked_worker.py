@@ -25,10 +25,10 @@ def want(buf, w, h, stride, bpp, r, L, mode):
     return oracle.oilpaint(buf, w, h, stride, bpp, r, L, mode=mode, out=out)
 
 
-def image(w, h, bpp, seed):
+def image(w, h, bpp, seed, stride=None):
     img = synth.camera_like(h, w, seed=seed, npoly=15, rad_range=(2, 60))
     img[np.random.default_rng(seed).random((h, w)) < 0.1] = 255
-    return synth.to_strided(img, bpp=bpp, stride=w * bpp + 4)
+    return synth.to_strided(img, bpp=bpp, stride=stride or w * bpp + 4)
 
 
 def main() -> int:
@@ -69,6 +69,20 @@ def main() -> int:
             assert np.array_equal(dst.cpu().numpy(), want(buf, 233, 150, stride, bpp, r, L, mode)), \
                 (r, L, mode, bpp, cfg)
             n += 1
+    # the fused pack (4-byte pixels on 16-byte rows; every path and word format)
+    for k, (r, L, mode, cfg) in enumerate(cases):
+        buf, stride = image(233, 150, 4, seed=200 + k, stride=944)
+        src = torch.from_numpy(buf).cuda()
+        dst = torch.full_like(src, FILL)
+        op = OilPaint(233, 150, r, L, bpp=4, stride=stride, flags=mode | B.OP_FUSED_PACK,
+                      config=cfg)
+        op.run(src, dst)
+        st = op.sync_status()
+        assert st == B.OP_OK, (r, L, cfg, "fused", B.status_string(st))
+        op.close()
+        assert np.array_equal(dst.cpu().numpy(), want(buf, 233, 150, stride, 4, r, L, mode)), \
+            (r, L, mode, "fused", cfg)
+        n += 1
     # batch: all four groups (r above 15 or not x L above 20 or not), literal
     # and default images
     images = []
