@@ -200,7 +200,8 @@ def tune_batch(images: list[dict], max_radius: int, max_levels: int, reps: int =
                     raise
                 # a candidate that does not fit the group falls back: skip it
                 gcfg = got[keys.index(k)]["config"]
-                if any(gcfg[f] != cfg[f] for f in ("tile_w", "chunk_rows", "cols_per_thread")):
+                if any(gcfg[f] != cfg[f] for f in ("tile_w", "chunk_rows", "cols_per_thread",
+                                                    "path")):
                     continue
                 if not all(torch.equal(a, c) for a, c in zip(ref, outs)):
                     raise B.OilPaintError(f"batch config {cfg} for group {k} changed the output")

@@ -121,3 +121,54 @@ def run(steps: int = 10, warmup: int = 3, n: int = 64, config=None) -> dict:
                    for g in groups],
     }
 
+
+
+def tune(table_path: str | None = None, n: int = 64, reps: int = 7, verbose: bool = True) -> dict:
+    """Tunes the batch groups' configurations on this workload
+    (autotune.tune_batch, coordinate descent over the groups) and writes
+    them as the batch entries of the tuning table (the single-image entries
+    are kept)."""
+    import json
+
+    from . import autotune
+    from .filter import load_tuning
+
+    path = table_path or autotune.TABLE_PATH
+    load_tuning(path)
+    images = make_batch(synth.batch_specs(n=n), make_pool())
+    for im in images:
+        im["bpp"] = 3
+    max_r = max(im["r"] for im in images)
+    max_L = max(im["L"] for im in images)
+    res = autotune.tune_batch(images, max_r, max_L, reps=reps, verbose=verbose)
+    with open(path) as f:
+        table = json.load(f)
+    workload = "64-image mixed batch, r in {2,4,8,12,20}, L in {16,20,32}"
+    table["batch_entries"] = {k: {"batch_ms": round(res["ms"], 4), "config": v["config"],
+                                  "workload": workload}
+                              for k, v in res["groups"].items()}
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+        f.write("\n")
+    return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    import sys
+
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--tune", action="store_true", help="tune the batch groups and save the table")
+    p.add_argument("--steps", type=int, default=10)
+    a = p.parse_args()
+    import __graft_entry__
+    __graft_entry__.build()
+    from .filter import load_tuning
+    if a.tune:
+        r = tune()
+        print(json.dumps({"untuned_ms": r["ms_untuned"], "tuned_ms": r["ms"],
+                          "groups": r["groups"]}))
+    load_tuning()
+    print(json.dumps(run(steps=a.steps)))
+    sys.exit(0)
