@@ -43,12 +43,19 @@ class _Bits:
         return bytes(self.out)
 
 
-def flat_gray_jpeg(blocks: np.ndarray) -> bytes:
+def flat_gray_jpeg(blocks: np.ndarray, width: int | None = None,
+                   height: int | None = None) -> bytes:
     """Baseline grayscale JPEG of a (by, bx) array of block values (uint8):
-    the image is (8 by) x (8 bx) pixels, block (i, j) filled with blocks[i, j]."""
+    the image is (8 by) x (8 bx) pixels, block (i, j) filled with blocks[i, j],
+    or its top-left width x height pixels (the frame header then gives the
+    smaller size, and a decoder drops the edge blocks' pixels beyond it,
+    T.81 A.1.1); width > 8 (bx - 1) and height > 8 (by - 1)."""
     blocks = np.asarray(blocks, dtype=np.int64)
     by, bx = blocks.shape
-    h, w = 8 * by, 8 * bx
+    h = 8 * by if height is None else height
+    w = 8 * bx if width is None else width
+    if not (8 * (by - 1) < h <= 8 * by and 8 * (bx - 1) < w <= 8 * bx):
+        raise ValueError("size does not match the block grid")
     out = bytearray(b"\xff\xd8")                                            # SOI
     out += _segment(0xFFDB, bytes([0x00]) + bytes([1] * 64))                # DQT: table 0, all 1
     out += _segment(0xFFC0, struct.pack(">BHHB", 8, h, w, 1) + bytes([1, 0x11, 0]))  # SOF0
@@ -73,9 +80,11 @@ def flat_gray_jpeg(blocks: np.ndarray) -> bytes:
     return bytes(out)
 
 
-def flat_gray_image(blocks: np.ndarray) -> np.ndarray:
-    """The (8 by) x (8 bx) grayscale image flat_gray_jpeg(blocks) encodes."""
-    return np.kron(np.asarray(blocks, dtype=np.uint8), np.ones((8, 8), dtype=np.uint8))
+def flat_gray_image(blocks: np.ndarray, width: int | None = None,
+                    height: int | None = None) -> np.ndarray:
+    """The grayscale image flat_gray_jpeg(blocks, width, height) encodes."""
+    img = np.kron(np.asarray(blocks, dtype=np.uint8), np.ones((8, 8), dtype=np.uint8))
+    return img[:height, :width]
 
 
 def frame_header(data: bytes) -> dict:

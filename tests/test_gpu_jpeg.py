@@ -78,6 +78,24 @@ def test_flat_block_jpeg_decodes_exactly(pipe):
         assert np.array_equal(got[..., c], want)
 
 
+@pytest.mark.parametrize("w,h", [(133, 70), (129, 65), (57, 9)])
+def test_flat_block_jpeg_ragged_size_decodes_exactly(pipe, w, h):
+    """Sizes that are not multiples of the 8x8 block: the decoder keeps the
+    edge blocks' pixels inside the frame only."""
+    bx, by = (w + 7) // 8, (h + 7) // 8
+    blocks = _blocks(by, bx, seed=w + h)
+    data = flat_gray_jpeg(blocks, w, h)
+    assert pipe.info(data) == (w, h, 1)
+    got = pipe.decode(data).cpu().numpy().reshape(h, w, 3)
+    want = flat_gray_image(blocks, w, h)
+    for c in range(3):
+        assert np.array_equal(got[..., c], want)
+    out, rgb = pipe.filter(data, 3, 20, quality=95, sampling=J.OP_JPEG_CSS_444, keep_rgb=True)
+    img = np.repeat(want[..., None], 3, axis=2)
+    assert np.array_equal(rgb.cpu().numpy().reshape(h, w, 3), _oracle_rgb(img, 3, 20))
+    assert frame_header(out)["width"] == w and frame_header(out)["height"] == h
+
+
 @pytest.mark.parametrize("radius,levels", [(2, 20), (5, 64), (1, 256), (15, 20)])
 def test_pipeline_on_flat_blocks_equals_oracle(pipe, radius, levels):
     blocks = _blocks(24, 40, seed=radius * 7 + levels)

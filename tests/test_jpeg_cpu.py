@@ -82,3 +82,17 @@ def test_flat_gray_writer():
         assert scan[i + 1] == 0x00
     img = flat_gray_image(blocks)
     assert img.shape == (40, 56) and img[8 * 4 + 3, 8 * 6 + 5] == blocks[4, 6]
+
+
+def test_flat_gray_writer_ragged_size():
+    blocks = np.arange(12, dtype=np.uint8).reshape(3, 4) * 20
+    data = flat_gray_jpeg(blocks, 29, 17)
+    hdr = frame_header(data)
+    assert (hdr["width"], hdr["height"]) == (29, 17)
+    img = flat_gray_image(blocks, 29, 17)
+    assert img.shape == (17, 29) and img[16, 28] == blocks[2, 3]
+    # the entropy-coded data is that of the whole block grid either way
+    full = flat_gray_jpeg(blocks)
+    assert data[data.index(b"\xff\xda"):] == full[full.index(b"\xff\xda"):]
+    with pytest.raises(ValueError):
+        flat_gray_jpeg(blocks, 24, 17)
