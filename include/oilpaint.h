@@ -196,13 +196,15 @@ size_t op_workspace_size(const op_t *op);
 
 /* Give `op` caller-owned device workspace of `bytes` >= op_workspace_size,
  * 16-byte aligned; it must stay valid while runs that use it are in flight.
- * Without it op_run allocates its own on first use (freed by op_destroy). */
+ * Without it op_run allocates its own on first use (freed by op_destroy);
+ * runs that take the fused pack (OP_FUSED_PACK) use none. */
 int op_set_workspace(op_t *op, void *d_ws, size_t bytes);
 
 /*
  * op_run -- filter one image, asynchronously on `stream`.  d_in, d_out:
  * device pointers to height*stride bytes each, non-overlapping.  Launches the
- * pack prepass and the tiled filter kernel.  OP_E_CUDA if a launch fails.
+ * pack prepass and the tiled filter kernel (the filter alone under
+ * OP_FUSED_PACK, where it applies).  OP_E_CUDA if a launch fails.
  */
 int op_run(op_t *op, const uint8_t *d_in, uint8_t *d_out, void *stream);
 
@@ -234,8 +236,9 @@ int op_run_host_async(op_t *op, const uint8_t *h_in, uint8_t *h_out, void *strea
 /* Profiling hook: when `event` (a cudaEvent_t passed as void*) is not NULL,
  * every later op_run records it on the run's stream between the pack prepass
  * and the filter kernel, so that events recorded by the caller before and
- * after op_run time the two kernels separately.  NULL turns it off.  The
- * event stays owned by the caller. */
+ * after op_run time the two kernels separately (with OP_FUSED_PACK there is
+ * one launch, and the event is recorded just before it).  NULL turns it off.
+ * The event stays owned by the caller. */
 int op_set_profile_event(op_t *op, void *event);
 
 /* Synchronise `stream`, then report and clear the sticky device error word
