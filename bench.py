@@ -364,13 +364,16 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s_timed_region": round(t_wall, 4),
     }
-    if not args.skip_batch:
+    # The batch, JPEG and served measurements describe one GPU: they run in
+    # the single-GPU job only, so that a multi-GPU run holds its GPUs for the
+    # headline steps alone.
+    if not args.skip_batch and world == 1:
         from paper_1405_1020_gb300 import batchbench
         line["batched"] = batchbench.run(steps=max(3, args.steps // 2), warmup=2)
-    if not args.skip_jpeg and rank == 0:
+    if not args.skip_jpeg and world == 1:
         from paper_1405_1020_gb300 import jpegbench
         line["jpeg_pipeline"] = jpegbench.run()
-    if args.serve_seconds > 0:
+    if args.serve_seconds > 0 and world == 1:
         from paper_1405_1020_gb300 import serve
         line["served"] = serve.bench_loads(seconds=args.serve_seconds,
                                            overload_seconds=args.overload_seconds)
