@@ -248,3 +248,37 @@ class JpegPipeline:
         t = op_jpeg_timing_t()
         check(op_jpeg_last_timing(self._h, t), "op_jpeg_last_timing")
         return {"decode_ms": t.decode_ms, "filter_ms": t.filter_ms, "encode_ms": t.encode_ms}
+
+
+def main(argv=None) -> int:
+    """python -m paper_1405_1020_gb300.jpeg IN.jpg OUT.jpg [--radius R] [--levels L] ...
+
+    Filters a JPEG file into another (section 3.2's ApplyOilPaintOnFile) and
+    prints the decode, filter and encode times, as the paper's driver logs
+    them."""
+    import argparse
+    import json
+
+    p = argparse.ArgumentParser(description="oil-paint filter of a JPEG file, on the GPU")
+    p.add_argument("input")
+    p.add_argument("output")
+    p.add_argument("--radius", type=int, default=5)
+    p.add_argument("--levels", type=int, default=20)
+    p.add_argument("--quality", type=int, default=90)
+    p.add_argument("--sampling", choices=["444", "422", "420"], default="420")
+    p.add_argument("--intdiv3", action="store_true", help="level from floor((R+G+B)/3)")
+    p.add_argument("--literal", action="store_true", help="section 4's listing as printed")
+    a = p.parse_args(argv)
+    flags = (binding.OP_LEVEL_INTDIV3 if a.intdiv3 else 0) | (binding.OP_LITERAL if a.literal else 0)
+    sampling = {"444": OP_JPEG_CSS_444, "422": OP_JPEG_CSS_422, "420": OP_JPEG_CSS_420}[a.sampling]
+    with JpegPipeline() as jp:
+        jp.filter_file(a.input, a.output, a.radius, a.levels, flags, a.quality, sampling)
+        w, h, _ = jp.info(open(a.output, "rb").read())
+        print(json.dumps({"width": w, "height": h, **jp.last_timing()}))
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+
+    sys.exit(main())

@@ -168,6 +168,18 @@ def test_filter_file(pipe, tmp_path):
     assert e.value.status == OP_E_INVALID
 
 
+def test_command_line(pipe, tmp_path, capsys):
+    w, h = 300, 200
+    src = synth.camera_like(h, w, seed=12, npoly=20, rad_range=(5, 80))
+    t = torch.from_numpy(np.ascontiguousarray(src).reshape(h, 3 * w)).cuda()
+    data = pipe.encode(t, w, h, quality=90)
+    fin, fout = tmp_path / "a.jpg", tmp_path / "b.jpg"
+    fin.write_bytes(data)
+    assert J.main([str(fin), str(fout), "--radius", "4", "--levels", "16"]) == 0
+    assert fout.read_bytes() == pipe.filter(data, 4, 16, quality=90)
+    assert '"width": 300' in capsys.readouterr().out
+
+
 def test_errors(pipe):
     w, h = 64, 48
     src = synth.camera_like(h, w, seed=3, npoly=5, rad_range=(5, 30))
