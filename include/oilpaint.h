@@ -129,7 +129,13 @@ typedef struct op_s op_t;
  *                   the window histogram in one part (path 2) or split by
  *                   column parity into two (path 3); 32 or 64 threads;
  *                   needs levels <= 32 and K/2 <= radius <= 15 (radius >= 4
- *                   for 8 columns), else OP_E_UNSUPPORTED.  Not for batches.
+ *                   for 8 columns), else OP_E_UNSUPPORTED.  Not for batches;
+ *                   4: direct, no histogram (radius 1 or 2, any levels, one
+ *                   column per thread, 32..128 threads): each thread keeps
+ *                   its window's (2r+1)^2 packed pixels in registers and
+ *                   counts their 8-bit levels by pairwise comparison, so the
+ *                   work per pixel does not depend on L; other radii are
+ *                   refused (OP_E_UNSUPPORTED).  Not for batches.
  * The halo copy of a tile is at most 1024 columns wide (copies wider than
  * 256 columns read the packed image as groups of 4 words): tile_w + 2r + up
  * to 3 columns for one column per thread and for path 1, K * (threads - 1 +

@@ -161,7 +161,8 @@ uint32_t threads_of(const op_config_t &c) {
 
 // Range checks that need no device.
 bool config_in_range(const op_config_t &c) {
-  if (c.path > 3u) return false;
+  if (c.path > 4u) return false;
+  if (c.path == 4u && cols_per_thread(c) != 1) return false;  // direct: one column per thread
   if (c.cols_per_thread != 0 && c.cols_per_thread != 1 && c.cols_per_thread != 2 &&
       c.cols_per_thread != 4 && c.cols_per_thread != 8)
     return false;
@@ -172,7 +173,7 @@ bool config_in_range(const op_config_t &c) {
   // the straight-line paths (2, 3): 4 or 8 columns of 32 or 64 threads, or 2
   // columns on path 2; eight columns exist only there (path 0 with 8 columns
   // means path 3)
-  if ((c.path >= 2u || cpt == 8u) && (nt > 64 || (cpt != 4u && cpt != 8u))) {
+  if ((c.path == 2u || c.path == 3u || cpt == 8u) && (nt > 64 || (cpt != 4u && cpt != 8u))) {
     // two columns: path 2 only (the window histogram in one part)
     if (!(c.path == 2u && cpt == 2u && nt <= 64)) return false;
   }
@@ -239,13 +240,22 @@ int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
   return OP_OK;
 }
 
-// Built-in default: the first of a preference list that runs and whose shared
+// Built-in default: the direct path at radius 1 and 2 with many levels, else
+// the first of a preference list that runs and whose shared
 // memory leaves room for >= 2 CTAs per SM, one halo chunk in flight: the
 // straight-line difference histograms (64 threads x 4 columns, the window
 // histogram in one part, 2-row chunks) where they apply (2 <= r <= 15,
 // L <= 32), then difference histograms over 4 or 2 columns per thread
 // (r <= 44, L <= 32), then one column per thread (8-row chunks).
 op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
+  // The direct path where its cost, independent of L, beats the L-level
+  // argmax of the histogram paths (12 MP at r = 1: 0.21 ms against 0.125 ms
+  // at L = 20 and 0.34 ms at L = 64; at r = 2: 0.86 ms against 0.40 ms at
+  // L = 64 and 1.50 ms at L = 256).
+  if ((r == 1 && L > 40u) || (r == 2 && L > 144u)) {
+    const op_config_t c = {128, 0, 4, 1, 1, 4};
+    if (check_config(c, r, L, di) == OP_OK) return c;
+  }
   // threads, columns per thread, path, halo chunk rows
   static const uint32_t prefs[][4] = {{64, 4, 2, 2}, {32, 4, 0, 8}, {64, 2, 0, 8}, {128, 1, 0, 8},
                                       {96, 1, 0, 8},  {64, 1, 0, 8}, {32, 1, 0, 8}};

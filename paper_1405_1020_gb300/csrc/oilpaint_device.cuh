@@ -101,6 +101,9 @@ constexpr uint32_t kModeLiteral = 2u;
 // (5-bit level field next to the valid bit).
 constexpr int kDeltaMaxRadius = 44;
 constexpr uint32_t kDeltaMaxLevels = 32;
+// The direct path (run_tile_direct, path 4): radius 1 or 2, any L <= 256.
+constexpr uint32_t kPathDirect = 4;
+constexpr int kDirectMaxRadius = 2;
 // The straight-line difference-histogram path (run_tile_deltak): variant-A
 // bins, K/2 <= r <= 15 for K = 2, 4 or 8 columns per thread (r >= 4 for
 // K = 8), L <= 32 (L <= 64 for K = 2).
@@ -593,7 +596,8 @@ __device__ __forceinline__ void convert_raw_slot(const ImgDesc &d, uint32_t slot
                                                  uint32_t half_bytes, int xs, int ye, int yl,
                                                  uint32_t ch, uint32_t boxw) {
   const uint32_t groups = boxw >> 2;
-  const uint32_t rows = 2u * ch;
+  // the direct path's copies bring entering rows only
+  const uint32_t rows = (d.path == kPathDirect ? 1u : 2u) * ch;
   const uint32_t nthr = blockDim.x;
   const int w = static_cast<int>(d.w), h = static_cast<int>(d.h);
   const uint32_t L = d.L, mode = d.mode, fmt = d.fmt;
@@ -1128,13 +1132,15 @@ __device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *t
       return;  // nothing armed: the wait for this chunk runs out and reports a timeout
     }
 #endif
-    mbar_arrive_expect_tx(bar, 2u * box_bytes);
+    // the direct path (4) keeps its windows in registers: entering rows only
+    const bool leaving = d.path != kPathDirect;
+    mbar_arrive_expect_tx(bar, (leaving ? 2u : 1u) * box_bytes);
     if (boxw > kMaxBox2dWords) {  // xs is a multiple of 4: a whole group
       tma_load_3d(dst, tmap, xs >> 2, E0 + k * ch, bar);
-      tma_load_3d(dst + rc.half_bytes, tmap, xs >> 2, E0 + k * ch - 2 * r - 1, bar);
+      if (leaving) tma_load_3d(dst + rc.half_bytes, tmap, xs >> 2, E0 + k * ch - 2 * r - 1, bar);
     } else {
       tma_load_2d(dst, tmap, xs, E0 + k * ch, bar);
-      tma_load_2d(dst + rc.half_bytes, tmap, xs, E0 + k * ch - 2 * r - 1, bar);
+      if (leaving) tma_load_2d(dst + rc.half_bytes, tmap, xs, E0 + k * ch - 2 * r - 1, bar);
     }
   };
 
@@ -1204,6 +1210,99 @@ __device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *t
   }
   chunk_ctr += static_cast<uint32_t>(nchunks);
   return true;
+}
+
+// Direct path (path 4), radius R = 1 or 2, any L <= 256: no histogram.  A
+// window holds at most (2R+1)^2 = 25 pixels, so its most frequent level is
+// found by comparing the pixels' 8-bit levels pairwise (section 4's count per
+// level, restricted to the levels present), at a cost independent of L.
+// Thread t owns column xa = x0 + t and keeps its window's packed words
+// (format 0) in registers, oldest row first, sliding down the tile: each
+// step shifts the rows up and appends the entering row from the ring; the
+// leaving row is simply dropped (the ring carries entering rows only).  A
+// cell outside the image, or in literal mode a white pixel (level L), gets
+// the level 256 + k: it matches no other cell, its count stays 0, and it
+// cannot win.  Keys (count << 9) | (511 - level) give the largest count and,
+// on ties, the lowest level; the winning level's channel sums are summed
+// over the matching cells and divided exactly (counts <= 25).
+template <int NT, int R>
+__device__ bool run_tile_direct(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0,
+                                int y1, const RingCfg &rc, const SmemMap &sm,
+                                uint32_t &chunk_ctr, uint32_t *err, uint64_t timeout_ns) {
+  static_assert(R >= 1 && R <= kDirectMaxRadius, "direct path radius");
+  constexpr int N = 2 * R + 1;
+  constexpr int K = N * N;
+  const int t = threadIdx.x;
+  const int W = static_cast<int>(d.w), H = static_cast<int>(d.h);
+  const uint32_t L = d.L;
+  const int xa = x0 + t;
+  const int xs = (x0 - R) & ~3;  // box start, rounded down to 16 bytes
+  const int jl = xa - R - xs;    // ring index of column xa - R
+  const int E0 = y0 - R;
+  const int nsteps = (y1 - y0) + 2 * R;
+  const bool col_out = xa >= d.ox0 && xa < d.ox1;
+  uint32_t colmask = 0;  // bit c: column xa - R + c lies in the image
+#pragma unroll
+  for (int c = 0; c < N; ++c)
+    if (xa - R + c >= 0 && xa - R + c < W) colmask |= 1u << c;
+  uint32_t win[K];
+  uint32_t rowmask = 0;  // bit i: window row i lies in the image
+#pragma unroll
+  for (int k = 0; k < K; ++k) win[k] = 0u;
+
+  return ring_pass(
+      d, tmap, xs, E0, nsteps, rc, sm, chunk_ctr, err, timeout_ns, nullptr, false, x0, y0, y1,
+      [&](int s, const uint32_t *rowe, const uint32_t *) {
+        const int e = E0 + s;  // entering row
+#pragma unroll
+        for (int k = 0; k < K - N; ++k) win[k] = win[k + N];
+        const uint32_t *pe = rowe + jl;
+#pragma unroll
+        for (int c = 0; c < N; ++c) win[K - N + c] = pe[c];
+        rowmask = (rowmask >> 1) | ((e >= 0 && e < H) ? (1u << (N - 1)) : 0u);
+        if (s < 2 * R || !col_out) return;
+        const int y = e - R;  // the output row, complete now
+        const uint32_t alpha = d.bpp == 4 ? load_alpha(d, xa, y) : 0u;
+        uint32_t lv[K];
+        uint32_t inmask = 0;  // bit k: cell k takes part
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const uint32_t l = win[k] >> 24;
+          const bool in = ((rowmask >> (k / N)) & (colmask >> (k % N)) & 1u) && l < L;
+          lv[k] = in ? l : 256u + static_cast<uint32_t>(k);
+          inmask |= in ? 1u << k : 0u;
+        }
+        // every pair compared once, both counts updated (one candidate at a
+        // time against every cell, with one count live, measured 5% slower
+        // at r = 2)
+        uint32_t cnt[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) cnt[k] = (inmask >> k) & 1u;
+#pragma unroll
+        for (int a = 0; a < K; ++a)
+#pragma unroll
+          for (int b = a + 1; b < K; ++b) {
+            const uint32_t eq = lv[a] == lv[b] ? 1u : 0u;
+            cnt[a] += eq;
+            cnt[b] += eq;
+          }
+        uint32_t best = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) best = max(best, (cnt[k] << 9) | (511u - lv[k]));
+        if (best < 512u) return;  // no level below L in the window (literal mode only)
+        const uint32_t m = 511u - (best & 511u), n = best >> 9;
+        uint32_t Rs = 0, Gs = 0, Bs = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if (lv[k] == m) {
+            Rs += (win[k] >> 16) & 0xFFu;
+            Gs += (win[k] >> 8) & 0xFFu;
+            Bs += win[k] & 0xFFu;
+          }
+        const uint32_t mul = rcp_of(n);
+        store_pixel(d, xa, y, div_mean<kVarA>(Rs, n, mul), div_mean<kVarA>(Gs, n, mul),
+                    div_mean<kVarA>(Bs, n, mul), alpha);
+      });
 }
 
 // One output column per thread: tile [x0, x0 + NT) x [y0, y1), thread t owns

@@ -74,6 +74,7 @@ inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
 // the packed word format.
 struct Geometry {
   int path;
+  int r;
   uint32_t nt;
   int kcols;
   uint32_t tile_w;
@@ -88,7 +89,23 @@ inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, u
                                uint32_t w) {
   Geometry g;
   g.nt = nt;
+  g.r = r;
   g.variant = variant_for_radius(r);
+  // the direct path: radius 1 or 2, any L, one column per thread
+  if (path == static_cast<int>(kPathDirect)) {
+    if (r >= 1 && r <= kDirectMaxRadius && kcols_wanted == 1) {
+      g.path = path;
+      g.kcols = 1;
+      g.tile_w = nt;
+      g.xshift = 0;
+      g.boxw = box_width(nt, r);
+      g.fmt = 0u;
+      g.variant = kVarA;
+      g.tiles_x = (w + nt - 1u) / nt;
+      return g;
+    }
+    path = 0;
+  }
   // eight columns per thread exist only on the straight-line path (in two parts)
   if (path == 0 && kcols_wanted == 8) path = 3;
   if (path == 2 || path == 3) {
@@ -270,13 +287,17 @@ cudaError_t set_tile_smem_limit(size_t bytes);
 int tile_occupancy(uint32_t nt, bool persistent, int kcols, int variant, size_t smem);
 // ... of the column-histogram kernel: nt = 32 * warps, twk = outputs per warp / 32.
 int tile_occupancy_cols(uint32_t nt, int twk, int variant, size_t smem);
+// ... of the direct kernel (path 4) of nt threads at radius r.
+int direct_occupancy(uint32_t nt, int r, size_t smem);
 
 // Histogram bytes and resident CTAs of an image's single-image kernel.
 inline size_t geometry_hist_bytes(const Geometry &g, int r, uint32_t L) {
+  if (g.path == static_cast<int>(kPathDirect)) return 0;  // windows in registers
   if (g.path == 2 || g.path == 3) return deltak_hist_bytes(g.nt, g.kcols, g.path - 1, L);
   return g.path == 1 ? cols_hist_bytes(g, r, L) : hist_bytes(g.nt, g.kcols, L, g.variant);
 }
 inline int geometry_occupancy(const Geometry &g, size_t smem) {
+  if (g.path == static_cast<int>(kPathDirect)) return direct_occupancy(g.nt, g.r, smem);
   if (g.path == 2 || g.path == 3) return deltak_occupancy(g.nt, g.kcols, g.path - 1, smem);
   return g.path == 1 ? tile_occupancy_cols(g.nt, g.kcols, g.variant, smem)
                      : tile_occupancy(g.nt, false, g.kcols, g.variant, smem);

@@ -95,6 +95,22 @@ __global__ void __launch_bounds__(NT, 1)
   run_tile_delta<NT, K, VAR>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
 }
 
+// Radius 2's window and counts fit 128 registers per thread (then 4 CTAs of
+// 128 threads per SM); unbounded, the unrolled comparisons take all 255.
+template <int NT, int R>
+__global__ void __launch_bounds__(NT, R == 1 ? 1 : 65536 / (NT * 128))
+    tile_direct_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d,
+                       const RingCfg rc, uint32_t *err, uint64_t timeout_ns) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const SmemMap sm = carve_smem(smem, rc, 0u);
+  init_cta(sm, rc);
+  uint32_t ctr = 0;
+  const int x0 = static_cast<int>(blockIdx.x) * NT;
+  const int y0 = d.oy0 + static_cast<int>(blockIdx.y * d.tile_h);
+  const int y1 = min(y0 + static_cast<int>(d.tile_h), d.oy1);
+  run_tile_direct<NT, R>(d, &tmap, x0, y0, y1, rc, sm, ctr, err, timeout_ns);
+}
+
 template <int NW, int TWK, int VAR>
 __global__ void __launch_bounds__(32 * NW, 1)
     tile_cols_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d, const RingCfg rc,
@@ -245,9 +261,38 @@ static void cols_n(int twk, int variant, const ImgDesc &d, const CUtensorMap &ma
   }
 }
 
+// The direct kernel of nt threads and radius r (nullptr outside the table).
+using DirectFn = void (*)(const CUtensorMap, const ImgDesc, const RingCfg, uint32_t *, uint64_t);
+static DirectFn direct_fn(uint32_t nt, int r) {
+  static constexpr DirectFn fns[4][kDirectMaxRadius] = {
+      {tile_direct_kernel<32, 1>, tile_direct_kernel<32, 2>},
+      {tile_direct_kernel<64, 1>, tile_direct_kernel<64, 2>},
+      {tile_direct_kernel<96, 1>, tile_direct_kernel<96, 2>},
+      {tile_direct_kernel<128, 1>, tile_direct_kernel<128, 2>}};
+  const int i = nt == 32 ? 0 : nt == 64 ? 1 : nt == 96 ? 2 : nt == 128 ? 3 : -1;
+  if (i < 0 || r < 1 || r > kDirectMaxRadius) return nullptr;
+  return fns[i][r - 1];
+}
+
+int direct_occupancy(uint32_t nt, int r, size_t smem) {
+  const DirectFn f = direct_fn(nt, r);
+  if (!f) return 0;
+  int n = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, static_cast<int>(nt), smem) ==
+                 cudaSuccess
+             ? n
+             : 0;
+}
+
 cudaError_t launch_tile(uint32_t nt, int kcols, int variant, const ImgDesc &d,
                         const CUtensorMap &map, const RingCfg &rc, dim3 grid, size_t smem,
                         uint32_t *err, uint64_t timeout_ns, cudaStream_t s) {
+  if (d.path == kPathDirect) {
+    const DirectFn f = direct_fn(nt, d.r);
+    if (!f || kcols != 1 || d.fmt != 0u) return cudaErrorInvalidValue;
+    f<<<grid, nt, smem, s>>>(map, d, rc, err, timeout_ns);
+    return cudaGetLastError();
+  }
   if (d.path == 1u) {
     if (kcols != 1 && kcols != 2) return cudaErrorInvalidValue;
     switch (nt) {
@@ -376,6 +421,11 @@ cudaError_t set_tile_smem_limit(size_t bytes) {
   const int b = static_cast<int>(bytes);
   cudaError_t e;
   if ((e = set_deltak_smem_limit(bytes)) != cudaSuccess) return e;
+  for (uint32_t nt : {32u, 64u, 96u, 128u})
+    for (int r = 1; r <= kDirectMaxRadius; ++r)
+      if ((e = cudaFuncSetAttribute(direct_fn(nt, r), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    b)) != cudaSuccess)
+        return e;
   if ((e = set_limit_cols<1>(b)) != cudaSuccess) return e;
   if ((e = set_limit_cols<2>(b)) != cudaSuccess) return e;
   if ((e = set_limit_cols<4>(b)) != cudaSuccess) return e;

@@ -54,6 +54,9 @@ def main() -> int:
         (25, 32, 0, {"tile_w": 128, "cols_per_thread": 2, "path": 1}),
         (6, 20, B.OP_LITERAL, {"tile_w": 128, "cols_per_thread": 4}),
         (17, 254, B.OP_LITERAL, {"tile_w": 32, "cols_per_thread": 1}),
+        (1, 256, 0, {"tile_w": 128, "chunk_rows": 4, "path": 4}),
+        (2, 64, B.OP_LITERAL, {"tile_w": 64, "chunk_rows": 3, "path": 4}),
+        (2, 20, 1, {"tile_w": 96, "chunk_rows": 1, "prefetch": 2, "path": 4}),
     ]
     n = 0
     for k, (r, L, mode, cfg) in enumerate(cases):

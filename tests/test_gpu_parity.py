@@ -266,6 +266,69 @@ def test_straight_line_refused_outside_its_range(K, path, r, L, status):
     op.close()
 
 
+def _direct_cases(n=96, seed=23):
+    """The direct path (path 4: radius 1 or 2, windows in registers, levels
+    compared pairwise): every level count class up to 256, widths around the
+    tile widths and narrower than a tile, one-row and short images, both
+    level modes and literal mode, thread counts, tile heights, halo chunk
+    heights and prefetch depths."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for k in range(n):
+        r = 1 + k % 2
+        mode = int(rng.choice([0, 1, B.OP_LITERAL, B.OP_LITERAL | 1]))
+        Ls = [1, 2, 3, 7, 16, 20, 32, 33, 64, 100, 255, 256]
+        L = int(rng.choice([x for x in Ls if not (mode & B.OP_LITERAL) or x <= 254]))
+        w = int(rng.choice([1, 2, 3, 5, 31, 32, 33, 63, 64, 65, 95, 96, 97, 128, 129, 300]))
+        h = int(rng.choice([1, 2, 3, 4, 5, 17, 64, 129]))
+        bpp = int(rng.choice([3, 4]))
+        pad = int(rng.choice([0, 1, 4, 13]))
+        nt = int(rng.choice([32, 64, 96, 128]))
+        cfg = {"tile_w": nt, "tile_h": int(rng.choice([0, 1, 2, 5, 16, 64])),
+               "chunk_rows": int(rng.choice([1, 2, 3, 8])), "prefetch": int(rng.integers(1, 3)),
+               "cols_per_thread": 1, "path": 4}
+        cases.append((k, w, h, r, L, bpp, pad, mode, cfg))
+    return cases
+
+
+@pytest.mark.parametrize("k,w,h,r,L,bpp,pad,mode,cfg", _direct_cases())
+def test_fuzz_direct_path(k, w, h, r, L, bpp, pad, mode, cfg):
+    if k % 3 == 0:  # few colours: many equal levels and ties
+        img = synth.camera_like(h, w, seed=2300 + k, npoly=6, rad_range=(1, 20), noise=0.0)
+    elif k % 3 == 1:
+        img = synth.uniform_rgb(h, w, seed=2300 + k)
+    else:
+        img = synth.camera_like(h, w, seed=2300 + k, npoly=12, rad_range=(1, 60))
+    if k % 4 == 0:  # runs of white (level L - 1, or level L in literal mode)
+        img[np.random.default_rng(k).random((h, w)) < 0.25] = 255
+    check_case(img, r, L, bpp, pad, mode, cfg)
+
+
+@pytest.mark.parametrize("r,L,cfg,status", [
+    (0, 20, {"tile_w": 128, "path": 4}, B.OP_E_UNSUPPORTED),
+    (3, 20, {"tile_w": 128, "path": 4}, B.OP_E_UNSUPPORTED),
+    (15, 256, {"tile_w": 64, "path": 4}, B.OP_E_UNSUPPORTED),
+    (1, 20, {"tile_w": 128, "cols_per_thread": 2, "path": 4}, B.OP_E_INVALID),
+    (1, 20, {"tile_w": 48, "path": 4}, B.OP_E_INVALID),
+])
+def test_direct_path_refused_outside_its_range(r, L, cfg, status):
+    with pytest.raises(B.OilPaintError) as e:
+        OilPaint(100, 50, r, L, bpp=3, stride=300, config=cfg)
+    assert e.value.status == status
+
+
+@pytest.mark.parametrize("r,L", [(1, 20), (2, 256), (1, 256)])
+def test_direct_path_whole_12mp_image(camera_12mp, r, L):
+    """The 12 MP RGBA camera-like image through the direct path, every byte
+    against the oracle."""
+    buf, stride = camera_12mp
+    w, h = 4000, 3000
+    cfg = {"tile_w": 128, "chunk_rows": 4, "prefetch": 1, "path": 4}
+    got = gpu_filter(buf, w, h, stride, 4, r, L, config=cfg)
+    want = cpu_filter(buf, w, h, stride, 4, r, L)
+    assert_same(got, want, w, h, stride, 4, f"12 MP direct r={r} L={L}")
+
+
 def _column_path_cases(n=48, seed=13):
     """The column-histogram path (path 1, L <= 32): 1, 2 or 4 warps sweeping
     32 or 64 columns each, both bin variants (r <= 15 and above), every
