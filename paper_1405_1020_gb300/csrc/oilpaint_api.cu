@@ -249,10 +249,10 @@ int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
 // (r <= 44, L <= 32), then one column per thread (8-row chunks).
 op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
   // The direct path where its cost, independent of L, beats the L-level
-  // argmax of the histogram paths (12 MP at r = 1: 0.21 ms against 0.125 ms
-  // at L = 20 and 0.34 ms at L = 64; at r = 2: 0.86 ms against 0.40 ms at
-  // L = 64 and 1.50 ms at L = 256).
-  if ((r == 1 && L > 40u) || (r == 2 && L > 144u)) {
+  // argmax of the histogram paths (12 MP at r = 1: 0.19 ms against 0.125 ms
+  // at L = 20, 0.17 ms at L = 32 and 0.34 ms at L = 64; at r = 2: 0.80 ms
+  // against 0.67 ms at L = 128 and 1.50 ms at L = 256).
+  if ((r == 1 && L > 40u) || (r == 2 && L > 150u)) {
     const op_config_t c = {128, 0, 4, 1, 1, 4};
     if (check_config(c, r, L, di) == OP_OK) return c;
   }

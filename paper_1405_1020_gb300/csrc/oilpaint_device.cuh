@@ -1264,13 +1264,21 @@ __device__ bool run_tile_direct(const ImgDesc &d, const CUtensorMap *tmap, int x
         const int y = e - R;  // the output row, complete now
         const uint32_t alpha = d.bpp == 4 ? load_alpha(d, xa, y) : 0u;
         uint32_t lv[K];
-        uint32_t inmask = 0;  // bit k: cell k takes part
+        uint32_t inmask = (1u << K) - 1u;  // bit k: cell k takes part
+        constexpr uint32_t kAll = (1u << N) - 1u;
+        if (rowmask == kAll && colmask == kAll && !(d.mode & kModeLiteral)) {
+          // inside the image, every level below L: every cell takes part
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const uint32_t l = win[k] >> 24;
-          const bool in = ((rowmask >> (k / N)) & (colmask >> (k % N)) & 1u) && l < L;
-          lv[k] = in ? l : 256u + static_cast<uint32_t>(k);
-          inmask |= in ? 1u << k : 0u;
+          for (int k = 0; k < K; ++k) lv[k] = win[k] >> 24;
+        } else {
+          inmask = 0u;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const uint32_t l = win[k] >> 24;
+            const bool in = ((rowmask >> (k / N)) & (colmask >> (k % N)) & 1u) && l < L;
+            lv[k] = in ? l : 256u + static_cast<uint32_t>(k);
+            inmask |= in ? 1u << k : 0u;
+          }
         }
         // every pair compared once, both counts updated (one candidate at a
         // time against every cell, with one count live, measured 5% slower
