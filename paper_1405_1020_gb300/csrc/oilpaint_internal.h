@@ -66,7 +66,8 @@ inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
 }
 
 // Launch geometry of one image: path (0 histograms per thread, 1 column
-// histograms, 2 and 3 the straight-line difference histograms with the
+// histograms, 4 the direct path of radius 1 and 2, 2 and 3 the straight-line
+// difference histograms with the
 // window histogram in one or two parts), threads per CTA, columns per thread
 // (path 0: 2 or 4 only where the difference-histogram path applies; path 1:
 // outputs per warp / 32; paths 2 and 3: 4 or 8), tile width, the x of the
