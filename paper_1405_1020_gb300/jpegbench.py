@@ -23,7 +23,11 @@ def run(width: int = 4000, height: int = 3000, radius: int = 15, levels: int = 2
     from . import synth
     from .csrc import build as cbuild
 
-    if cbuild.build_jpeg() is None or not J.available():
+    try:
+        built = cbuild.build_jpeg()
+    except Exception as e:  # noqa: BLE001 -- the benchmark line reports it
+        return {"unavailable": f"liboilpaint_jpeg.so did not build: {e}"}
+    if built is None or not J.available():
         return {"unavailable": "nvJPEG is not in this CUDA toolkit"}
     src = synth.camera_like(height, width, seed=seed)
     rgb = torch.from_numpy(np.ascontiguousarray(src).reshape(height, 3 * width)).cuda()
