@@ -130,7 +130,7 @@ typedef struct op_s op_t;
  *                   column parity into two (path 3); 32 or 64 threads;
  *                   needs levels <= 32 and K/2 <= radius <= 15 (radius >= 4
  *                   for 8 columns), else OP_E_UNSUPPORTED.  Not for batches;
- *                   4: direct, no histogram (radius 1 or 2, any levels, one
+ *                   4: direct, no histogram (radius 0, 1 or 2, any levels, one
  *                   column per thread, 32..128 threads): each thread keeps
  *                   its window's (2r+1)^2 packed pixels in registers and
  *                   counts their 8-bit levels by pairwise comparison, so the

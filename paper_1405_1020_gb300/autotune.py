@@ -45,7 +45,7 @@ def candidates(radius: int, levels: int, tile_hs=(0,)) -> list[dict]:
         for nt, ch, pf, th in itertools.product((32, 64), (1, 2, 4), (1, 2), tile_hs):
             out.append({"tile_w": nt * 2, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
                         "cols_per_thread": 2, "path": 2})
-    if 1 <= radius <= 2:  # direct: windows in registers, levels compared pairwise
+    if 0 <= radius <= 2:  # direct: windows in registers, levels compared pairwise
         for nt, ch, pf, th in itertools.product((64, 128), (2, 4, 8), (1, 2), tile_hs):
             out.append({"tile_w": nt, "tile_h": th, "chunk_rows": ch, "prefetch": pf,
                         "cols_per_thread": 1, "path": 4})

@@ -248,12 +248,13 @@ int check_config(const op_config_t &c, int r, uint32_t L, const DevInfo &di) {
 // L <= 32), then difference histograms over 4 or 2 columns per thread
 // (r <= 44, L <= 32), then one column per thread (8-row chunks).
 op_config_t builtin_config(int r, uint32_t L, const DevInfo &di) {
-  // The direct path where its cost, independent of L, beats the L-level
+  // The direct path at r = 0 (the pixel itself: 12 MP 0.049 ms against
+  // 0.109 ms) and where its cost, independent of L, beats the L-level
   // argmax of the histogram paths (12 MP at r = 1: 0.19 ms against 0.125 ms
   // at L = 20, 0.17 ms at L = 32 and 0.34 ms at L = 64; at r = 2: 0.80 ms
   // against 0.67 ms at L = 128 and 1.50 ms at L = 256).
-  if ((r == 1 && L > 40u) || (r == 2 && L > 150u)) {
-    const op_config_t c = {128, 0, 4, 1, 1, 4};
+  if (r == 0 || (r == 1 && L > 40u) || (r == 2 && L > 150u)) {
+    const op_config_t c = {64, 0, 8, 1, 1, 4};  // 64 threads, 8-row chunks, 1 in flight
     if (check_config(c, r, L, di) == OP_OK) return c;
   }
   // threads, columns per thread, path, halo chunk rows

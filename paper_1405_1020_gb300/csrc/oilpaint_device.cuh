@@ -101,7 +101,7 @@ constexpr uint32_t kModeLiteral = 2u;
 // (5-bit level field next to the valid bit).
 constexpr int kDeltaMaxRadius = 44;
 constexpr uint32_t kDeltaMaxLevels = 32;
-// The direct path (run_tile_direct, path 4): radius 1 or 2, any L <= 256.
+// The direct path (run_tile_direct, path 4): radius 0, 1 or 2, any L <= 256.
 constexpr uint32_t kPathDirect = 4;
 constexpr int kDirectMaxRadius = 2;
 // The straight-line difference-histogram path (run_tile_deltak): variant-A
@@ -1212,7 +1212,7 @@ __device__ __forceinline__ bool ring_pass(const ImgDesc &d, const CUtensorMap *t
   return true;
 }
 
-// Direct path (path 4), radius R = 1 or 2, any L <= 256: no histogram.  A
+// Direct path (path 4), radius R = 0, 1 or 2, any L <= 256: no histogram.  A
 // window holds at most (2R+1)^2 = 25 pixels, so its most frequent level is
 // found by comparing the pixels' 8-bit levels pairwise (section 4's count per
 // level, restricted to the levels present), at a cost independent of L.
@@ -1229,7 +1229,7 @@ template <int NT, int R>
 __device__ bool run_tile_direct(const ImgDesc &d, const CUtensorMap *tmap, int x0, int y0,
                                 int y1, const RingCfg &rc, const SmemMap &sm,
                                 uint32_t &chunk_ctr, uint32_t *err, uint64_t timeout_ns) {
-  static_assert(R >= 1 && R <= kDirectMaxRadius, "direct path radius");
+  static_assert(R >= 0 && R <= kDirectMaxRadius, "direct path radius");
   constexpr int N = 2 * R + 1;
   constexpr int K = N * N;
   const int t = threadIdx.x;

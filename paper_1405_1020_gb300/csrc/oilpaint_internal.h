@@ -66,7 +66,7 @@ inline uint32_t delta_box_width(uint32_t nt, int k, int r) {
 }
 
 // Launch geometry of one image: path (0 histograms per thread, 1 column
-// histograms, 4 the direct path of radius 1 and 2, 2 and 3 the straight-line
+// histograms, 4 the direct path of radius 0 to 2, 2 and 3 the straight-line
 // difference histograms with the
 // window histogram in one or two parts), threads per CTA, columns per thread
 // (path 0: 2 or 4 only where the difference-histogram path applies; path 1:
@@ -92,9 +92,9 @@ inline Geometry image_geometry(int path, uint32_t nt, int kcols_wanted, int r, u
   g.nt = nt;
   g.r = r;
   g.variant = variant_for_radius(r);
-  // the direct path: radius 1 or 2, any L, one column per thread
+  // the direct path: radius 0, 1 or 2, any L, one column per thread
   if (path == static_cast<int>(kPathDirect)) {
-    if (r >= 1 && r <= kDirectMaxRadius && kcols_wanted == 1) {
+    if (r >= 0 && r <= kDirectMaxRadius && kcols_wanted == 1) {
       g.path = path;
       g.kcols = 1;
       g.tile_w = nt;

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT, 1)
 // Radius 2's window and counts fit 128 registers per thread (then 4 CTAs of
 // 128 threads per SM); unbounded, the unrolled comparisons take all 255.
 template <int NT, int R>
-__global__ void __launch_bounds__(NT, R == 1 ? 1 : 65536 / (NT * 128))
+__global__ void __launch_bounds__(NT, R < 2 ? 1 : 65536 / (NT * 128))
     tile_direct_kernel(const __grid_constant__ CUtensorMap tmap, const ImgDesc d,
                        const RingCfg rc, uint32_t *err, uint64_t timeout_ns) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -264,14 +264,14 @@ static void cols_n(int twk, int variant, const ImgDesc &d, const CUtensorMap &ma
 // The direct kernel of nt threads and radius r (nullptr outside the table).
 using DirectFn = void (*)(const CUtensorMap, const ImgDesc, const RingCfg, uint32_t *, uint64_t);
 static DirectFn direct_fn(uint32_t nt, int r) {
-  static constexpr DirectFn fns[4][kDirectMaxRadius] = {
-      {tile_direct_kernel<32, 1>, tile_direct_kernel<32, 2>},
-      {tile_direct_kernel<64, 1>, tile_direct_kernel<64, 2>},
-      {tile_direct_kernel<96, 1>, tile_direct_kernel<96, 2>},
-      {tile_direct_kernel<128, 1>, tile_direct_kernel<128, 2>}};
+  static constexpr DirectFn fns[4][kDirectMaxRadius + 1] = {
+      {tile_direct_kernel<32, 0>, tile_direct_kernel<32, 1>, tile_direct_kernel<32, 2>},
+      {tile_direct_kernel<64, 0>, tile_direct_kernel<64, 1>, tile_direct_kernel<64, 2>},
+      {tile_direct_kernel<96, 0>, tile_direct_kernel<96, 1>, tile_direct_kernel<96, 2>},
+      {tile_direct_kernel<128, 0>, tile_direct_kernel<128, 1>, tile_direct_kernel<128, 2>}};
   const int i = nt == 32 ? 0 : nt == 64 ? 1 : nt == 96 ? 2 : nt == 128 ? 3 : -1;
-  if (i < 0 || r < 1 || r > kDirectMaxRadius) return nullptr;
-  return fns[i][r - 1];
+  if (i < 0 || r < 0 || r > kDirectMaxRadius) return nullptr;
+  return fns[i][r];
 }
 
 int direct_occupancy(uint32_t nt, int r, size_t smem) {
@@ -422,7 +422,7 @@ cudaError_t set_tile_smem_limit(size_t bytes) {
   cudaError_t e;
   if ((e = set_deltak_smem_limit(bytes)) != cudaSuccess) return e;
   for (uint32_t nt : {32u, 64u, 96u, 128u})
-    for (int r = 1; r <= kDirectMaxRadius; ++r)
+    for (int r = 0; r <= kDirectMaxRadius; ++r)
       if ((e = cudaFuncSetAttribute(direct_fn(nt, r), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     b)) != cudaSuccess)
         return e;

@@ -266,8 +266,8 @@ def test_straight_line_refused_outside_its_range(K, path, r, L, status):
     op.close()
 
 
-def _direct_cases(n=96, seed=23):
-    """The direct path (path 4: radius 1 or 2, windows in registers, levels
+def _direct_cases(n=108, seed=23):
+    """The direct path (path 4: radius 0, 1 or 2, windows in registers, levels
     compared pairwise): every level count class up to 256, widths around the
     tile widths and narrower than a tile, one-row and short images, both
     level modes and literal mode, thread counts, tile heights, halo chunk
@@ -275,7 +275,7 @@ def _direct_cases(n=96, seed=23):
     rng = np.random.default_rng(seed)
     cases = []
     for k in range(n):
-        r = 1 + k % 2
+        r = (1, 2, 0)[k % 3]
         mode = int(rng.choice([0, 1, B.OP_LITERAL, B.OP_LITERAL | 1]))
         Ls = [1, 2, 3, 7, 16, 20, 32, 33, 64, 100, 255, 256]
         L = int(rng.choice([x for x in Ls if not (mode & B.OP_LITERAL) or x <= 254]))
@@ -305,7 +305,6 @@ def test_fuzz_direct_path(k, w, h, r, L, bpp, pad, mode, cfg):
 
 
 @pytest.mark.parametrize("r,L,cfg,status", [
-    (0, 20, {"tile_w": 128, "path": 4}, B.OP_E_UNSUPPORTED),
     (3, 20, {"tile_w": 128, "path": 4}, B.OP_E_UNSUPPORTED),
     (15, 256, {"tile_w": 64, "path": 4}, B.OP_E_UNSUPPORTED),
     (1, 20, {"tile_w": 128, "cols_per_thread": 2, "path": 4}, B.OP_E_INVALID),
