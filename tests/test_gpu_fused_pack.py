@@ -62,6 +62,9 @@ CASES = [
     (300, 60, 4, 20, B.OP_LITERAL, None),
     (300, 60, 4, 254, B.OP_LITERAL | B.OP_LEVEL_INTDIV3, None),
     (257, 33, 12, 32, 0, {"tile_w": 256, "cols_per_thread": 4, "path": 2}),
+    (333, 77, 1, 64, 0, {"tile_w": 128, "chunk_rows": 8, "path": 4}),     # direct path:
+    (301, 50, 2, 256, 0, {"tile_w": 64, "chunk_rows": 3, "path": 4}),     # entering rows only
+    (203, 41, 0, 20, B.OP_LITERAL, {"tile_w": 64, "chunk_rows": 8, "path": 4}),
 ]
 
 
