@@ -1,6 +1,6 @@
 """Randomized parity campaign, run by hand on a GPU (not collected by pytest):
 
-    python tests/fuzz_campaign.py SEED SECONDS
+    python tests/fuzz_campaign.py SEED SECONDS [image|batch]
 
 Draws configurations from seven families -- the default choice at any
 radius and level count, one column per thread, difference histograms with
@@ -10,7 +10,8 @@ direct path, and the tuned table's entries -- with random image sizes
 literal mode, the fused pack, tile heights, halo chunk heights and prefetch
 depths, camera-like images with runs of white; filters each through op_run
 and compares every byte with the oracle.  A configuration the library
-refuses must be refused with OP_E_UNSUPPORTED.  Exits 1 on any difference.
+refuses must be refused with OP_E_UNSUPPORTED.  `batch` runs random image
+sets through the batch API instead.  Exits 1 on any difference.
 """
 import json
 import os
@@ -29,6 +30,66 @@ load_tuning()
 FILL = 0x5A
 rng = np.random.default_rng(int(sys.argv[1]) if len(sys.argv) > 1 else 1234)
 budget = float(sys.argv[2]) if len(sys.argv) > 2 else 480.0
+MODE = sys.argv[3] if len(sys.argv) > 3 else "image"
+
+
+def batch_campaign():
+    """Random batches (1..40 images of mixed size, radius, levels, bytes per
+    pixel and mode) through op_batch_set, run eagerly and replayed from the
+    captured graph, every image against the oracle."""
+    from paper_1405_1020_gb300.filter import Batch
+    t0 = time.time(); nb = ni = 0; fails = []
+    stream = torch.cuda.Stream()
+    while time.time() - t0 < budget:
+        n = int(rng.integers(1, 41))
+        ims = []
+        for _ in range(n):
+            w = int(rng.integers(1, 700)); h = int(rng.integers(1, 300))
+            bpp = int(rng.choice([3, 4])); mode = int(rng.choice([0, 1, B.OP_LITERAL]))
+            r = int(rng.choice([0, 1, 2, 3, 5, 8, 12, 15, 16, 20, 31, 44]))
+            L = int(rng.choice([1, 2, 7, 16, 20, 21, 32, 33, 64, 200, 254]))
+            img = synth.camera_like(h, w, seed=int(rng.integers(1 << 30)), npoly=8,
+                                    rad_range=(1, max(2, w // 3)))
+            if rng.random() < 0.3:
+                img[rng.random((h, w)) < 0.2] = 255
+            buf, stride = synth.to_strided(img, bpp=bpp, stride=w * bpp + int(rng.integers(0, 9)))
+            src = torch.from_numpy(buf).cuda()
+            ims.append(dict(buf=buf, src=src, dst=torch.full_like(src, FILL), w=w, h=h,
+                            stride=stride, bpp=bpp, r=r, L=L, mode=mode))
+        torch.cuda.synchronize()
+        pix = Batch.padded_pixels([(im["w"], im["h"]) for im in ims])
+        b = Batch(n, pix + 4096, max(im["r"] for im in ims), max(im["L"] for im in ims))
+        descs = [(im["src"], im["dst"], im["w"], im["h"], im["stride"], im["bpp"], im["r"],
+                  im["L"], im["mode"]) for im in ims]
+        for how in ("eager", "graph"):
+            for im in ims:
+                im["dst"].fill_(FILL)
+            torch.cuda.synchronize()
+            b.set(descs, stream)
+            if how == "eager":
+                b.run(stream)
+            else:
+                b.capture(stream)
+                b.launch_graph(stream)
+            st = b.sync_status(stream)
+            for k, im in enumerate(ims):
+                want = oracle.oilpaint(im["buf"], im["w"], im["h"], im["stride"], im["bpp"],
+                                       im["r"], im["L"], mode=im["mode"],
+                                       out=np.full(im["buf"].size, FILL, np.uint8))
+                if st != B.OP_OK or not np.array_equal(im["dst"].cpu().numpy(), want):
+                    fails.append(dict(how=how, k=k, n=n, w=im["w"], h=im["h"], r=im["r"],
+                                      L=im["L"], bpp=im["bpp"], mode=im["mode"], status=st))
+                    print("FAIL", fails[-1], flush=True)
+                ni += 1
+        b.close()
+        nb += 1
+    print(json.dumps({"batches": nb, "images": ni, "failures": len(fails),
+                      "seconds": round(time.time() - t0, 1)}))
+    sys.exit(1 if fails else 0)
+
+
+if MODE == "batch":
+    batch_campaign()
 t0 = time.time(); n = 0; refused = 0; fails = []
 while time.time() - t0 < budget:
     fam = int(rng.integers(0, 7))
