@@ -250,6 +250,68 @@ class JpegPipeline:
         return {"decode_ms": t.decode_ms, "filter_ms": t.filter_ms, "encode_ms": t.encode_ms}
 
 
+
+class JpegPool:
+    """`workers` host threads, each with its own codec context (JpegPipeline)
+    on its own CUDA stream, kept across calls.  One image's Huffman decoding
+    on the host (nvJPEG's simple decode call, which holds a host core for
+    most of an image's time) then overlaps other images' decoding and their
+    filtering and encoding on the GPU; ctypes releases the interpreter lock
+    during the library calls."""
+
+    def __init__(self, workers: int = 4):
+        import threading
+        from concurrent.futures import ThreadPoolExecutor
+
+        import torch
+
+        load()  # once, before the threads
+        self._local = threading.local()
+        self._contexts = []
+        self._lock = threading.Lock()
+        self._device = torch.cuda.current_device()
+        self._pool = ThreadPoolExecutor(max_workers=max(1, workers))
+
+    def _context(self):
+        import torch
+
+        if not hasattr(self._local, "jp"):
+            torch.cuda.set_device(self._device)
+            self._local.stream = torch.cuda.Stream()
+            self._local.jp = JpegPipeline(self._local.stream)
+            with self._lock:
+                self._contexts.append(self._local.jp)
+        return self._local.jp, self._local.stream
+
+    def filter_many(self, datas, radius: int, levels: int, flags: int = 0, quality: int = 90,
+                    sampling: int = OP_JPEG_CSS_420) -> list:
+        """JpegPipeline.filter over every JPEG byte string of `datas`;
+        the encoded outputs in input order."""
+        def one(data):
+            jp, stream = self._context()
+            return jp.filter(data, radius, levels, flags, quality, sampling, stream=stream)
+
+        return list(self._pool.map(one, datas))
+
+    def close(self):
+        self._pool.shutdown(wait=True)
+        for jp in self._contexts:
+            jp.close()
+        self._contexts = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def filter_many(datas, radius: int, levels: int, flags: int = 0, quality: int = 90,
+                sampling: int = OP_JPEG_CSS_420, workers: int = 4) -> list:
+    """JpegPool(workers).filter_many(...) for a one-off list of images."""
+    with JpegPool(workers) as pool:
+        return pool.filter_many(datas, radius, levels, flags, quality, sampling)
+
 def main(argv=None) -> int:
     """python -m paper_1405_1020_gb300.jpeg IN.jpg OUT.jpg [--radius R] [--levels L] ...
 

@@ -168,6 +168,17 @@ def test_filter_file(pipe, tmp_path):
     assert e.value.status == OP_E_INVALID
 
 
+def test_filter_many_equals_one_at_a_time(pipe):
+    datas = []
+    for k, (w, h) in enumerate(((320, 240), (101, 77), (640, 480), (64, 64), (333, 251))):
+        src = synth.camera_like(h, w, seed=40 + k, npoly=15, rad_range=(5, 80))
+        t = torch.from_numpy(np.ascontiguousarray(src).reshape(h, 3 * w)).cuda()
+        datas.append(pipe.encode(t, w, h, quality=90))
+    datas = datas * 3
+    got = J.filter_many(datas, 4, 20, quality=90, workers=4)
+    assert got == [pipe.filter(d, 4, 20, quality=90) for d in datas]
+
+
 def test_command_line(pipe, tmp_path, capsys):
     w, h = 300, 200
     src = synth.camera_like(h, w, seed=12, npoly=20, rad_range=(5, 80))
