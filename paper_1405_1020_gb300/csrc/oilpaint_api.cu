@@ -83,9 +83,11 @@ uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
   double best = 1e300;
   uint32_t best_h = H;
   if (slots < 1) slots = 1;
-  for (uint32_t t = 1; t <= H; ++t) {
+  // Only the distinct heights ceil(H / t) matter, each with the smallest t
+  // giving it, in increasing t (O(sqrt H) of them; ties keep the smaller t):
+  // after height th the next is reached at t = ceil(H / (th - 1)).
+  for (uint32_t t = 1; t <= H;) {
     const uint32_t th = (H + t - 1) / t;
-    if (t > 1 && (H + th - 1) / th != t) continue;  // same tiling as a smaller t
     const uint64_t tiles = static_cast<uint64_t>(tiles_x) * t;
     const uint64_t waves = (tiles + slots - 1) / slots;
     const double cost = static_cast<double>(waves) * (th + 2.0 * r);
@@ -93,6 +95,8 @@ uint32_t auto_tile_h(uint32_t H, uint32_t tiles_x, int r, uint64_t slots) {
       best = cost;
       best_h = th;
     }
+    if (th == 1) break;
+    t = (H + th - 2) / (th - 1);
   }
   return best_h;
 }
