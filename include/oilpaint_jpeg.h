@@ -57,8 +57,8 @@ extern "C" {
 
 typedef struct op_jpeg op_jpeg_t;
 
-/* Per-phase device times of the last op_jpeg_filter / op_jpeg_filter_file
- * call, in milliseconds, from CUDA events recorded on its stream around each
+/* Per-phase device times of the last op_jpeg_filter / op_jpeg_filter_file /
+ * op_jpeg_filter_batch call, in milliseconds, from CUDA events recorded on its stream around each
  * phase (the counterpart of the paper's decode / process / encode tick counts
  * in ApplyOilPaintOnFile).  decode_ms includes the host-side parse nvJPEG does
  * inside the decode call, because the events bracket the call. */
@@ -127,8 +127,43 @@ int op_jpeg_filter_file(op_jpeg_t *jp, const char *in_path, const char *out_path
                         int32_t radius, uint32_t levels, uint32_t flags, int quality,
                         int sampling, void *stream);
 
-/* Phase times of the last successful op_jpeg_filter / op_jpeg_filter_file;
- * OP_E_INVALID before the first. */
+/* Most images one op_jpeg_filter_batch call takes. */
+#define OP_JPEG_MAX_BATCH 64
+
+/* The pipeline over n JPEG streams (section 3.2's ApplyOilPaintOnFile over a
+ * set of files): the streams are decoded together, then each image is
+ * filtered (radius, levels, flags as op_create_ex) and encoded at quality /
+ * sampling in turn.  in[i] (in_len[i] bytes, host) is image i; its encoded
+ * result goes to out[i][0..cap[i]) (host) with its length in out_bytes[i],
+ * and its status in status[i] (OP_OK, or the first failing step's status as
+ * op_jpeg_filter gives it; on OP_E_NOSPACE out_bytes[i] is the size needed).
+ *
+ * Decoding: the streams nvJPEG's hardware decoder takes (baseline, one scan,
+ * not 4:1:0 or 4:1:1 sampling; checked per stream with
+ * nvjpegDecodeBatchedSupported) are decoded in one nvjpegDecodeBatched call on
+ * the GPU's JPEG decoder engines, the others with the decode of
+ * op_jpeg_decode; where the engine is absent, or the batched call fails, every
+ * stream takes that decode.  The engine's output was byte-identical to the
+ * other decoder's on the streams tested (see the tests).  The hardware
+ * context is created by the first call that needs it and kept.
+ *
+ * Device memory: the decoded images of a call are held together (the sum of
+ * height x pitch over the images, pitch = 3 * width rounded up to 16 bytes),
+ * in a buffer of the context that is kept and grown across calls.
+ *
+ * Returns OP_OK when every image succeeded, otherwise the status of the first
+ * image that failed (status[] says which; the others are still processed).
+ * OP_E_INVALID, with nothing processed and status[] untouched, for a NULL
+ * context or array, n = 0 or n > OP_JPEG_MAX_BATCH.  Synchronises `stream`;
+ * op_jpeg_last_timing then gives the batch's decode time and the sums of
+ * the images' filter and encode times. */
+int op_jpeg_filter_batch(op_jpeg_t *jp, uint32_t n, const uint8_t *const *in,
+                         const size_t *in_len, int32_t radius, uint32_t levels, uint32_t flags,
+                         int quality, int sampling, uint8_t *const *out, const size_t *cap,
+                         size_t *out_bytes, int *status, void *stream);
+
+/* Phase times of the last successful op_jpeg_filter / op_jpeg_filter_file /
+ * op_jpeg_filter_batch; OP_E_INVALID before the first. */
 int op_jpeg_last_timing(const op_jpeg_t *jp, op_jpeg_timing_t *t);
 
 /* Release the context, its device buffers and its filter handle (after

@@ -148,19 +148,31 @@ def build_jpeg(force: bool = False, verbose: bool = False):
 
 
 ALU_PROBE = os.path.join(PKG, "alu_probe")
+SMEM_UPDATE_PROBE = os.path.join(PKG, "smem_update_probe")
+
+
+def _build_probe(name: str, exe: str, force: bool) -> str:
+    src = os.path.join(CSRC, name + ".cu")
+    if (not force and os.path.exists(exe)
+            and os.path.getmtime(exe) >= os.path.getmtime(src)):
+        return exe
+    tmp = exe + f".tmp{os.getpid()}"
+    subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", tmp], check=True)
+    os.replace(tmp, exe)
+    return exe
 
 
 def build_alu_probe(force: bool = False) -> str:
     """Build the integer-ALU throughput probe (alu_probe.cu), a standalone
     program that measures the roofline denominator of the filter kernels."""
-    src = os.path.join(CSRC, "alu_probe.cu")
-    if (not force and os.path.exists(ALU_PROBE)
-            and os.path.getmtime(ALU_PROBE) >= os.path.getmtime(src)):
-        return ALU_PROBE
-    tmp = ALU_PROBE + f".tmp{os.getpid()}"
-    subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", tmp], check=True)
-    os.replace(tmp, ALU_PROBE)
-    return ALU_PROBE
+    return _build_probe("alu_probe", ALU_PROBE, force)
+
+
+def build_smem_update_probe(force: bool = False) -> str:
+    """Build the shared-memory bin-update probe (smem_update_probe.cu), a
+    standalone program that times a histogram bin update as load-add-store
+    and as shared-memory reductions."""
+    return _build_probe("smem_update_probe", SMEM_UPDATE_PROBE, force)
 
 
 if __name__ == "__main__":

@@ -31,6 +31,17 @@ struct op_jpeg {
     op_t *op = nullptr;
     uint32_t op_w = 0, op_h = 0, op_pitch = 0, op_levels = 0, op_flags = 0;
     int32_t op_radius = 0;
+    // Hardware (JPEG engine) decoder of op_jpeg_filter_batch: its own handle,
+    // batched state and stream parser, created on first use; hw_ok is 0
+    // before that, 1 when created, -1 when the engine is absent.
+    nvjpegHandle_t hw = nullptr;
+    nvjpegJpegState_t hw_dec = nullptr;
+    nvjpegJpegStream_t hw_parse = nullptr;
+    int hw_ok = 0;
+    int hw_batch = 0;  // batch size the state was initialised for
+    // Decoded images of op_jpeg_filter_batch, held together.
+    uint8_t *d_batch = nullptr;
+    size_t batch_cap = 0;
     // Events bracketing the three phases.
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     op_jpeg_timing_t timing{};
@@ -130,6 +141,79 @@ int encode_from(op_jpeg_t *jp, const uint8_t *d_rgb, uint32_t w, uint32_t h, uin
     return from_cuda(cudaStreamSynchronize(s));
 }
 
+// The hardware decoder, created on first use; false (and remembered) when
+// the GPU has no JPEG engine or nvJPEG cannot drive it.
+bool hw_ready(op_jpeg_t *jp) {
+    if (jp->hw_ok == 0) {
+        bool ok = nvjpegCreateEx(NVJPEG_BACKEND_HARDWARE, nullptr, nullptr, 0, &jp->hw) ==
+                  NVJPEG_STATUS_SUCCESS;
+        ok = ok && nvjpegJpegStateCreate(jp->hw, &jp->hw_dec) == NVJPEG_STATUS_SUCCESS;
+        ok = ok && nvjpegJpegStreamCreate(jp->hw, &jp->hw_parse) == NVJPEG_STATUS_SUCCESS;
+        if (!ok) {
+            if (jp->hw_parse) nvjpegJpegStreamDestroy(jp->hw_parse);
+            if (jp->hw_dec) nvjpegJpegStateDestroy(jp->hw_dec);
+            if (jp->hw) nvjpegDestroy(jp->hw);
+            jp->hw_parse = nullptr;
+            jp->hw_dec = nullptr;
+            jp->hw = nullptr;
+        }
+        cudaGetLastError();
+        jp->hw_ok = ok ? 1 : -1;
+    }
+    return jp->hw_ok == 1;
+}
+
+// Whether the hardware decoder takes this stream (nvJPEG reports 0 for yes).
+bool hw_takes(op_jpeg_t *jp, const uint8_t *data, size_t len) {
+    int unsupported = 1;
+    return nvjpegJpegStreamParse(jp->hw, data, len, 0, 0, jp->hw_parse) ==
+               NVJPEG_STATUS_SUCCESS &&
+           nvjpegDecodeBatchedSupported(jp->hw, jp->hw_parse, &unsupported) ==
+               NVJPEG_STATUS_SUCCESS &&
+           unsupported == 0;
+}
+
+// m streams in one batched call on the hardware decoder.
+int hw_decode(op_jpeg_t *jp, int m, const unsigned char *const *data, const size_t *lens,
+              nvjpegImage_t *dst, cudaStream_t s) {
+    if (jp->hw_batch != m) {
+        jp->hw_batch = 0;
+        int st = from_nvjpeg(
+            nvjpegDecodeBatchedInitialize(jp->hw, jp->hw_dec, m, 1, NVJPEG_OUTPUT_RGBI));
+        if (st != OP_OK) return st;
+        jp->hw_batch = m;
+    }
+    return from_nvjpeg(nvjpegDecodeBatched(jp->hw, jp->hw_dec, data, lens, dst, s));
+}
+
+// The context's filter handle for these arguments, made anew when the image
+// size or the parameters changed.
+int ensure_op(op_jpeg_t *jp, uint32_t w, uint32_t h, uint32_t pitch, int32_t radius,
+              uint32_t levels, uint32_t flags) {
+    if (jp->op && jp->op_w == w && jp->op_h == h && jp->op_pitch == pitch &&
+        jp->op_radius == radius && jp->op_levels == levels && jp->op_flags == flags)
+        return OP_OK;
+    if (jp->op) op_destroy(jp->op);
+    jp->op = op_create_ex(w, h, pitch, 3, radius, levels, flags);
+    if (!jp->op) return op_last_error();
+    jp->op_w = w;
+    jp->op_h = h;
+    jp->op_pitch = pitch;
+    jp->op_radius = radius;
+    jp->op_levels = levels;
+    jp->op_flags = flags;
+    return OP_OK;
+}
+
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
 }  // namespace
 
 extern "C" {
@@ -148,6 +232,10 @@ int op_jpeg_destroy(op_jpeg_t *jp) {
     if (jp->enc) nvjpegEncoderStateDestroy(jp->enc);
     if (jp->dec) nvjpegJpegStateDestroy(jp->dec);
     if (jp->handle) nvjpegDestroy(jp->handle);
+    if (jp->hw_parse) nvjpegJpegStreamDestroy(jp->hw_parse);
+    if (jp->hw_dec) nvjpegJpegStateDestroy(jp->hw_dec);
+    if (jp->hw) nvjpegDestroy(jp->hw);
+    if (jp->d_batch) cudaFree(jp->d_batch);
     cudaGetLastError();
     delete jp;
     return OP_OK;
@@ -242,18 +330,8 @@ int op_jpeg_filter(op_jpeg_t *jp, const uint8_t *in, size_t in_len, int32_t radi
         if (st != OP_OK) return st;
         dst = jp->d_out;
     }
-    if (!jp->op || jp->op_w != w || jp->op_h != h || jp->op_pitch != pitch ||
-        jp->op_radius != radius || jp->op_levels != levels || jp->op_flags != flags) {
-        if (jp->op) op_destroy(jp->op);
-        jp->op = op_create_ex(w, h, pitch, 3, radius, levels, flags);
-        if (!jp->op) return op_last_error();
-        jp->op_w = w;
-        jp->op_h = h;
-        jp->op_pitch = pitch;
-        jp->op_radius = radius;
-        jp->op_levels = levels;
-        jp->op_flags = flags;
-    }
+    st = ensure_op(jp, w, h, pitch, radius, levels, flags);
+    if (st != OP_OK) return st;
     jp->have_timing = false;
     st = from_cuda(cudaEventRecord(jp->ev[0], s));
     if (st == OP_OK) st = decode_into(jp, in, in_len, jp->d_in, pitch, s);
@@ -305,6 +383,102 @@ int op_jpeg_filter_file(op_jpeg_t *jp, const char *in_path, const char *out_path
     if (!f) return OP_E_INVALID;
     const bool ok = std::fwrite(out.data(), 1, n, f) == n;
     return (std::fclose(f) == 0 && ok) ? OP_OK : OP_E_INVALID;
+}
+
+int op_jpeg_filter_batch(op_jpeg_t *jp, uint32_t n, const uint8_t *const *in,
+                         const size_t *in_len, int32_t radius, uint32_t levels, uint32_t flags,
+                         int quality, int sampling, uint8_t *const *out, const size_t *cap,
+                         size_t *out_bytes, int *status, void *stream) {
+    if (!jp || !in || !in_len || !out || !cap || !out_bytes || !status || n == 0 ||
+        n > OP_JPEG_MAX_BATCH || quality < 1 || quality > 100 || !valid_sampling(sampling))
+        return OP_E_INVALID;
+    cudaStream_t s = as_stream(stream);
+    jp->have_timing = false;
+    uint32_t w[OP_JPEG_MAX_BATCH], h[OP_JPEG_MAX_BATCH], pitch[OP_JPEG_MAX_BATCH];
+    size_t off[OP_JPEG_MAX_BATCH];
+    size_t total = 0, most = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        out_bytes[i] = 0;
+        status[i] = (!in[i] || (!out[i] && cap[i] > 0))
+                        ? OP_E_INVALID
+                        : read_info(jp, in[i], in_len[i], &w[i], &h[i], nullptr);
+        if (status[i] != OP_OK) continue;
+        pitch[i] = (3u * w[i] + 15u) & ~15u;
+        off[i] = total;
+        const size_t bytes = static_cast<size_t>(pitch[i]) * h[i];
+        total += bytes;
+        if (bytes > most) most = bytes;
+    }
+    // Steps that every remaining image needs: on failure each takes the status.
+    auto fail_rest = [&](int st) {
+        for (uint32_t i = 0; i < n; ++i)
+            if (status[i] == OP_OK) status[i] = st;
+    };
+    int st = OP_OK;
+    if (total > 0) {
+        st = set_params(jp, quality, sampling, s);
+        if (st == OP_OK) st = grow(&jp->d_batch, &jp->batch_cap, total);
+        if (st == OP_OK) st = grow(&jp->d_out, &jp->out_cap, most);
+        if (st == OP_OK) st = from_cuda(cudaEventRecord(jp->ev[0], s));
+        if (st != OP_OK) fail_rest(st);
+    }
+    op_jpeg_timing_t t{};
+    if (total > 0 && st == OP_OK) {
+        // The hardware decoder's share in one call, then the rest one by one.
+        bool on_hw[OP_JPEG_MAX_BATCH] = {};
+        const unsigned char *hw_in[OP_JPEG_MAX_BATCH];
+        size_t hw_len[OP_JPEG_MAX_BATCH];
+        nvjpegImage_t hw_dst[OP_JPEG_MAX_BATCH];
+        int m = 0;
+        if (hw_ready(jp)) {
+            for (uint32_t i = 0; i < n; ++i) {
+                if (status[i] != OP_OK || !hw_takes(jp, in[i], in_len[i])) continue;
+                on_hw[i] = true;
+                hw_in[m] = in[i];
+                hw_len[m] = in_len[i];
+                std::memset(&hw_dst[m], 0, sizeof(hw_dst[m]));
+                hw_dst[m].channel[0] = jp->d_batch + off[i];
+                hw_dst[m].pitch[0] = pitch[i];
+                ++m;
+            }
+            if (m > 0 && hw_decode(jp, m, hw_in, hw_len, hw_dst, s) != OP_OK) {
+                cudaGetLastError();
+                for (uint32_t i = 0; i < n; ++i) on_hw[i] = false;  // all take the other decode
+            }
+        }
+        for (uint32_t i = 0; i < n; ++i)
+            if (status[i] == OP_OK && !on_hw[i])
+                status[i] = decode_into(jp, in[i], in_len[i], jp->d_batch + off[i], pitch[i], s);
+        st = from_cuda(cudaEventRecord(jp->ev[1], s));
+        if (st == OP_OK) st = from_cuda(cudaEventSynchronize(jp->ev[1]));
+        if (st != OP_OK) fail_rest(st);
+        t.decode_ms = elapsed_ms(jp->ev[0], jp->ev[1]);
+        // Filter and encode image by image (the encoder synchronises `s`).
+        for (uint32_t i = 0; i < n; ++i) {
+            if (status[i] != OP_OK) continue;
+            uint8_t *src = jp->d_batch + off[i];
+            int si = ensure_op(jp, w[i], h[i], pitch[i], radius, levels, flags);
+            if (si == OP_OK) si = from_cuda(cudaEventRecord(jp->ev[2], s));
+            if (si == OP_OK) si = op_run(jp->op, src, jp->d_out, s);
+            if (si == OP_OK) si = from_cuda(cudaEventRecord(jp->ev[3], s));
+            if (si == OP_OK) si = op_sync_status(jp->op, s);
+            if (si == OP_OK)
+                si = encode_from(jp, jp->d_out, w[i], h[i], pitch[i], out[i], cap[i],
+                                 &out_bytes[i], s);
+            if (si == OP_OK) si = from_cuda(cudaEventRecord(jp->ev[0], s));
+            if (si == OP_OK) si = from_cuda(cudaEventSynchronize(jp->ev[0]));
+            if (si == OP_OK) {
+                t.filter_ms += elapsed_ms(jp->ev[2], jp->ev[3]);
+                t.encode_ms += elapsed_ms(jp->ev[3], jp->ev[0]);
+            }
+            status[i] = si;
+        }
+    }
+    for (uint32_t i = 0; i < n; ++i)
+        if (status[i] != OP_OK) return status[i];
+    jp->timing = t;
+    jp->have_timing = true;
+    return OP_OK;
 }
 
 int op_jpeg_last_timing(const op_jpeg_t *jp, op_jpeg_timing_t *t) {

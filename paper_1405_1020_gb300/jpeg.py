@@ -32,8 +32,10 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liboilpaint
 EXPORTS = (
     "op_jpeg_create", "op_jpeg_last_error", "op_jpeg_info", "op_jpeg_decode",
     "op_jpeg_encode_bound", "op_jpeg_encode", "op_jpeg_filter", "op_jpeg_filter_file",
-    "op_jpeg_last_timing", "op_jpeg_destroy",
+    "op_jpeg_filter_batch", "op_jpeg_last_timing", "op_jpeg_destroy",
 )
+
+OP_JPEG_MAX_BATCH = 64
 
 
 class op_jpeg_timing_t(ctypes.Structure):
@@ -69,6 +71,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "op_jpeg_encode": (ci, [vp, vp, u32, u32, u32, ci, ci, vp, sz, psz, vp]),
         "op_jpeg_filter": (ci, [vp, cp, sz, i32, u32, u32, ci, ci, vp, sz, psz, vp, u32, vp]),
         "op_jpeg_filter_file": (ci, [vp, cp, cp, i32, u32, u32, ci, ci, vp]),
+        "op_jpeg_filter_batch": (ci, [vp, u32, ctypes.POINTER(vp), psz, i32, u32, u32, ci, ci,
+                                      ctypes.POINTER(vp), psz, psz, ctypes.POINTER(ci), vp]),
         "op_jpeg_last_timing": (ci, [vp, ctypes.POINTER(op_jpeg_timing_t)]),
         "op_jpeg_destroy": (ci, [vp]),
     }
@@ -135,6 +139,20 @@ def op_jpeg_filter_file(jp, in_path: str, out_path: str, radius, levels, flags, 
                         sampling, stream=None):
     return load().op_jpeg_filter_file(jp, os.fsencode(in_path), os.fsencode(out_path), radius,
                                       levels, flags, quality, sampling, stream)
+
+
+def op_jpeg_filter_batch(jp, datas, radius, levels, flags, quality, sampling, outs, caps,
+                         out_bytes, status, stream=None):
+    """datas: a sequence of JPEG byte strings (kept alive by the caller);
+    outs: a ctypes array of output addresses (c_void_p); caps, out_bytes:
+    ctypes arrays of c_size_t; status: a ctypes array of c_int; one entry per
+    image."""
+    n = len(datas)
+    ins = (ctypes.c_void_p * max(n, 1))(
+        *[ctypes.cast(ctypes.c_char_p(d), ctypes.c_void_p) for d in datas])
+    lens = (ctypes.c_size_t * max(n, 1))(*[len(d) for d in datas])
+    return load().op_jpeg_filter_batch(jp, n, ins, lens, radius, levels, flags, quality,
+                                       sampling, outs, caps, out_bytes, status, stream)
 
 
 def op_jpeg_last_timing(jp, t: op_jpeg_timing_t):
@@ -239,6 +257,39 @@ class JpegPipeline:
         out = self._out[:n.value].tobytes()
         return (out, rgb) if keep_rgb else out
 
+    def filter_batch(self, datas, radius: int, levels: int, flags: int = 0, quality: int = 90,
+                     sampling: int = OP_JPEG_CSS_420, stream=None) -> list:
+        """filter() over a list of JPEG byte strings in one op_jpeg_filter_batch
+        call (one batched decode on the GPU's JPEG engines where the streams
+        allow it); the encoded outputs in input order.  Raises OilPaintError
+        for the first image that failed."""
+        import numpy as np
+        datas = [bytes(d) for d in datas]
+        n = len(datas)
+        if n == 0:
+            return []
+        caps = []
+        for d in datas:
+            try:
+                w, h, _ = self.info(d)
+                caps.append(self.encode_bound(w, h, quality, sampling))
+            except OilPaintError:
+                caps.append(0)        # the call reports this image's status
+        buf = np.empty(max(1, sum(caps)), dtype=np.uint8)
+        offs = np.concatenate(([0], np.cumsum(caps)[:-1])).astype(np.int64)
+        base = buf.ctypes.data
+        outs = (ctypes.c_void_p * n)(*[base + int(o) for o in offs])
+        capa = (ctypes.c_size_t * n)(*caps)
+        got = (ctypes.c_size_t * n)()
+        status = (ctypes.c_int * n)()
+        st = op_jpeg_filter_batch(self._h, datas, radius, levels, flags, quality, sampling, outs,
+                                  capa, got, status, _stream_handle(stream))
+        if st != OP_OK:
+            bad = next((i for i in range(n) if status[i] != OP_OK), None)
+            what = "op_jpeg_filter_batch" if bad is None else f"op_jpeg_filter_batch (image {bad})"
+            check(st, what)
+        return [buf[int(o):int(o) + got[i]].tobytes() for i, o in enumerate(offs)]
+
     def filter_file(self, in_path: str, out_path: str, radius: int, levels: int, flags: int = 0,
                     quality: int = 90, sampling: int = OP_JPEG_CSS_420, stream=None):
         check(op_jpeg_filter_file(self._h, in_path, out_path, radius, levels, flags, quality,
@@ -253,13 +304,19 @@ class JpegPipeline:
 
 class JpegPool:
     """`workers` host threads, each with its own codec context (JpegPipeline)
-    on its own CUDA stream, kept across calls.  One image's Huffman decoding
-    on the host (nvJPEG's simple decode call, which holds a host core for
-    most of an image's time) then overlaps other images' decoding and their
-    filtering and encoding on the GPU; ctypes releases the interpreter lock
-    during the library calls."""
+    on its own CUDA stream, kept across calls.  With batch = 1 each thread
+    takes one image at a time (JpegPipeline.filter): one image's Huffman
+    decoding on the host (nvJPEG's simple decode call, which holds a host core
+    for most of an image's time) then overlaps other images' decoding and
+    their filtering and encoding on the GPU.  With batch > 1 each thread
+    takes `batch` images at a time (JpegPipeline.filter_batch), decoded
+    together on the GPU's JPEG engines where the streams allow it.  ctypes
+    releases the interpreter lock during the library calls."""
 
-    def __init__(self, workers: int = 4):
+    def __init__(self, workers: int = 4, batch: int = 8):
+        if not 1 <= batch <= OP_JPEG_MAX_BATCH:
+            raise ValueError(f"batch must be 1..{OP_JPEG_MAX_BATCH}")
+        self._batch = batch
         import threading
         from concurrent.futures import ThreadPoolExecutor
 
@@ -291,7 +348,15 @@ class JpegPool:
             jp, stream = self._context()
             return jp.filter(data, radius, levels, flags, quality, sampling, stream=stream)
 
-        return list(self._pool.map(one, datas))
+        def some(chunk):
+            jp, stream = self._context()
+            return jp.filter_batch(chunk, radius, levels, flags, quality, sampling, stream=stream)
+
+        if self._batch == 1:
+            return list(self._pool.map(one, datas))
+        datas = list(datas)
+        chunks = [datas[i:i + self._batch] for i in range(0, len(datas), self._batch)]
+        return [out for part in self._pool.map(some, chunks) for out in part]
 
     def close(self):
         self._pool.shutdown(wait=True)
@@ -307,9 +372,9 @@ class JpegPool:
 
 
 def filter_many(datas, radius: int, levels: int, flags: int = 0, quality: int = 90,
-                sampling: int = OP_JPEG_CSS_420, workers: int = 4) -> list:
-    """JpegPool(workers).filter_many(...) for a one-off list of images."""
-    with JpegPool(workers) as pool:
+                sampling: int = OP_JPEG_CSS_420, workers: int = 4, batch: int = 8) -> list:
+    """JpegPool(workers, batch).filter_many(...) for a one-off list of images."""
+    with JpegPool(workers, batch) as pool:
         return pool.filter_many(datas, radius, levels, flags, quality, sampling)
 
 def main(argv=None) -> int:

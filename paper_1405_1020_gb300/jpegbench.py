@@ -7,7 +7,9 @@ Reported: wall time per call (host clock around op_jpeg_filter, which returns
 after the encoded bytes are on the host) and the three phase times from the
 library's CUDA events, medians over the timed calls; and the throughput of a
 JpegPool of `workers` host threads (a codec context and stream each, created
-before the timed region) over 4 x workers copies of the image.
+before the timed region) over `images` copies of the image, each thread
+taking `batch` images per op_jpeg_filter_batch call (one batched decode on
+the GPU's JPEG engines), best of two passes.
 """
 from __future__ import annotations
 
@@ -19,7 +21,7 @@ import numpy as np
 
 def run(width: int = 4000, height: int = 3000, radius: int = 15, levels: int = 20,
         quality: int = 90, calls: int = 10, warmup: int = 2, seed: int = 2,
-        workers: int = 8) -> dict:
+        workers: int = 4, batch: int = 8, images: int = 64) -> dict:
     import torch
 
     from . import jpeg as J
@@ -44,18 +46,20 @@ def run(width: int = 4000, height: int = 3000, radius: int = 15, levels: int = 2
             out = p.filter(data, radius, levels, quality=quality)
             walls.append(time.perf_counter() - t)
             phases.append(p.last_timing())
-        many = [data] * (4 * workers)
-        with J.JpegPool(workers) as pool:
-            pool.filter_many(many[:workers], radius, levels, quality=quality)  # contexts
-            t = time.perf_counter()
-            outs = pool.filter_many(many, radius, levels, quality=quality)
-            many_s = time.perf_counter() - t
-        if any(o != out for o in outs):
-            raise RuntimeError("filter_many output differs from filter")
+        many = [data] * images
+        with J.JpegPool(workers, batch) as pool:
+            pool.filter_many(many[:workers * batch], radius, levels, quality=quality)  # contexts
+            many_s = float("inf")
+            for _ in range(2):
+                t = time.perf_counter()
+                outs = pool.filter_many(many, radius, levels, quality=quality)
+                many_s = min(many_s, time.perf_counter() - t)
+                if any(o != out for o in outs):
+                    raise RuntimeError("filter_many output differs from filter")
     wall = statistics.median(walls)
     med = {k: round(statistics.median(ph[k] for ph in phases), 4) for k in phases[0]}
     return {
-        "threads": {"workers": workers, "images": len(many),
+        "threads": {"workers": workers, "batch": batch, "images": len(many),
                     "ms_per_image": round(many_s / len(many) * 1e3, 3),
                     "mpix_s": round(len(many) * width * height / many_s / 1e6, 1)},
         "workload": f"{width}x{height} camera-like RGB, JPEG q{quality} 4:2:0 in and out, "
@@ -63,5 +67,6 @@ def run(width: int = 4000, height: int = 3000, radius: int = 15, levels: int = 2
         "calls": calls, "ms_per_image": round(wall * 1e3, 3),
         "mpix_s": round(width * height / wall / 1e6, 1),
         "phase_ms": med, "jpeg_in_bytes": len(data), "jpeg_out_bytes": len(out),
-        "codec": "nvJPEG (Huffman decoding on the host, the rest on the GPU)",
+        "codec": "nvJPEG: one call's decode with Huffman decoding on the host, the rest on "
+                 "the GPU; batched decode on the GPU's JPEG engines",
     }

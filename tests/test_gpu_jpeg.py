@@ -175,7 +175,7 @@ def test_filter_many_equals_one_at_a_time(pipe):
         t = torch.from_numpy(np.ascontiguousarray(src).reshape(h, 3 * w)).cuda()
         datas.append(pipe.encode(t, w, h, quality=90))
     datas = datas * 3
-    got = J.filter_many(datas, 4, 20, quality=90, workers=4)
+    got = J.filter_many(datas, 4, 20, quality=90, workers=4, batch=1)
     assert got == [pipe.filter(d, 4, 20, quality=90) for d in datas]
 
 
@@ -224,3 +224,82 @@ def test_errors(pipe):
     with J.JpegPipeline() as fresh:
         with pytest.raises(OilPaintError):
             fresh.last_timing()
+
+
+def _photo_jpegs(pipe, sizes, seed0, sampling=J.OP_JPEG_CSS_420, quality=90):
+    out = []
+    for k, (w, h) in enumerate(sizes):
+        src = synth.camera_like(h, w, seed=seed0 + k, npoly=15, rad_range=(5, 80))
+        t = torch.from_numpy(np.ascontiguousarray(src).reshape(h, 3 * w)).cuda()
+        out.append(pipe.encode(t, w, h, quality=quality, sampling=sampling))
+    return out
+
+
+@pytest.mark.parametrize("sampling", [J.OP_JPEG_CSS_444, J.OP_JPEG_CSS_422, J.OP_JPEG_CSS_420])
+def test_filter_batch_equals_filter(pipe, sampling):
+    # ragged sizes, a grayscale stream among the colour ones; each output must
+    # equal the one-image pipeline's (whose filter is checked against the
+    # oracle above), whichever decoder the batch gave the stream to
+    datas = _photo_jpegs(pipe, ((320, 240), (101, 77), (64, 64), (333, 251), (17, 9)), 60,
+                         sampling=sampling)
+    datas.insert(2, flat_gray_jpeg(_blocks(9, 13, 7), 99, 70))
+    got = pipe.filter_batch(datas, 5, 20, quality=88, sampling=sampling)
+    assert got == [pipe.filter(d, 5, 20, quality=88, sampling=sampling) for d in datas]
+    t = pipe.last_timing()
+    assert t["decode_ms"] > 0 and t["filter_ms"] > 0 and t["encode_ms"] > 0
+
+
+def test_filter_batch_12mp(pipe):
+    # the benchmark's image size, eight streams in one batched decode
+    w, h = 4000, 3000
+    src = synth.camera_like(h, w, seed=2)
+    t = torch.from_numpy(np.ascontiguousarray(src).reshape(h, 3 * w)).cuda()
+    data = pipe.encode(t, w, h, quality=90)
+    one = pipe.filter(data, 15, 20, quality=90)
+    assert pipe.filter_batch([data] * 8, 15, 20, quality=90) == [one] * 8
+
+
+def test_filter_batch_statuses(pipe):
+    datas = _photo_jpegs(pipe, ((96, 80), (50, 41)), 70)
+    junk = b"\x00" * 64
+    batch = [datas[0], junk, datas[1]]
+    with pytest.raises(OilPaintError) as e:
+        pipe.filter_batch(batch, 3, 16)
+    assert e.value.status == J.OP_E_CODEC and "image 1" in str(e.value)
+    # through the C call: per-image statuses; the good images still come out,
+    # and an output buffer that is too small reports the size needed
+    want = [pipe.filter(d, 3, 16) for d in datas]
+    n = 3
+    caps = [len(want[0]) + 100, 16, 16]
+    bufs = [ctypes.create_string_buffer(c) for c in caps]
+    outs = (ctypes.c_void_p * n)(*[ctypes.addressof(b) for b in bufs])
+    capa = (ctypes.c_size_t * n)(*caps)
+    got = (ctypes.c_size_t * n)()
+    status = (ctypes.c_int * n)()
+    st = J.op_jpeg_filter_batch(pipe._h, batch, 3, 16, 0, 90, J.OP_JPEG_CSS_420, outs, capa, got,
+                                status, None)
+    assert st == J.OP_E_CODEC
+    assert list(status) == [0, J.OP_E_CODEC, J.OP_E_NOSPACE]
+    assert bufs[0].raw[:got[0]] == want[0]
+    assert got[2] == len(want[1])
+    # arguments checked before anything runs: status[] untouched
+    status[0] = 12345
+    for bad_n, q in ((0, 90), (J.OP_JPEG_MAX_BATCH + 1, 90), (1, 0), (1, 101)):
+        many = [datas[0]] * bad_n
+        arr = lambda t: (t * max(bad_n, 1))()  # noqa: E731
+        assert J.op_jpeg_filter_batch(pipe._h, many, 3, 16, 0, q, 0, arr(ctypes.c_void_p),
+                                      arr(ctypes.c_size_t), arr(ctypes.c_size_t), status,
+                                      None) == OP_E_INVALID
+    assert status[0] == 12345
+
+
+def test_filter_many_batched_equals_one_at_a_time(pipe):
+    datas = _photo_jpegs(pipe, ((320, 240), (101, 77), (640, 480), (64, 64), (333, 251)), 80)
+    datas = datas * 3
+    want = [pipe.filter(d, 4, 20, quality=90) for d in datas]
+    assert J.filter_many(datas, 4, 20, quality=90, workers=2, batch=4) == want
+    with J.JpegPool(3, batch=8) as pool:
+        assert pool.filter_many(datas, 4, 20, quality=90) == want
+        assert pool.filter_many(datas[:1], 4, 20, quality=90) == want[:1]
+    with pytest.raises(ValueError):
+        J.JpegPool(1, batch=0)

@@ -40,7 +40,7 @@ def test_header_and_binding_agree():
     assert sorted(J.EXPORTS) == declared()
     consts = header_constants()
     for name in ("OP_E_CODEC", "OP_E_NOSPACE", "OP_JPEG_CSS_444", "OP_JPEG_CSS_422",
-                 "OP_JPEG_CSS_420"):
+                 "OP_JPEG_CSS_420", "OP_JPEG_MAX_BATCH"):
         assert consts[name] == getattr(J, name), name
 
 
@@ -59,6 +59,10 @@ def test_null_handles(lib):
     assert J.op_jpeg_encode(None, 1 << 20, 10, 10, 30, 90, 0, None, 0, n) == OP_E_INVALID
     assert J.op_jpeg_filter(None, b"\xff\xd8", 2, 20, 0, 90, 0, None, 0, n) == OP_E_INVALID
     assert J.op_jpeg_filter_file(None, "a.jpg", "b.jpg", 2, 20, 0, 90, 0) == OP_E_INVALID
+    arr = lambda t: (t * 1)()  # noqa: E731
+    assert J.op_jpeg_filter_batch(None, [b"\xff\xd8"], 2, 20, 0, 90, 0, arr(ctypes.c_void_p),
+                                  arr(ctypes.c_size_t), arr(ctypes.c_size_t),
+                                  arr(ctypes.c_int)) == OP_E_INVALID
     assert J.op_jpeg_last_timing(None, J.op_jpeg_timing_t()) == OP_E_INVALID
     assert J.op_jpeg_destroy(None) == OP_OK
 
