@@ -154,7 +154,9 @@ int op_jpeg_filter_file(op_jpeg_t *jp, const char *in_path, const char *out_path
  * Returns OP_OK when every image succeeded, otherwise the status of the first
  * image that failed (status[] says which; the others are still processed).
  * OP_E_INVALID, with nothing processed and status[] untouched, for a NULL
- * context or array, n = 0 or n > OP_JPEG_MAX_BATCH.  Synchronises `stream`;
+ * context or array, n = 0, n > OP_JPEG_MAX_BATCH, a quality outside 1..100
+ * or an unknown sampling; a NULL in[i] (or a NULL out[i] with cap[i] > 0)
+ * fails image i alone, with OP_E_INVALID.  Synchronises `stream`;
  * op_jpeg_last_timing then gives the batch's decode time and the sums of
  * the images' filter and encode times. */
 int op_jpeg_filter_batch(op_jpeg_t *jp, uint32_t n, const uint8_t *const *in,
