@@ -29,7 +29,11 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls that return encoded bytes or a timing synchronise that
  *     stream before they return; op_jpeg_decode does not (its device work is
- *     queued on `stream`, the host-side parse is done when it returns).
+ *     queued on `stream`, the host-side parse is done when it returns), but
+ *     a decode first waits for the device work of the context's previous
+ *     decode, whose staging buffers it reuses.  Every decode in this library
+ *     follows that rule, op_jpeg_filter's and op_jpeg_filter_batch's
+ *     included.
  *   - one op_jpeg_t serves one host thread at a time.
  */
 #ifndef OILPAINT_JPEG_H

@@ -20,6 +20,11 @@
 struct op_jpeg {
     nvjpegHandle_t handle = nullptr;
     nvjpegJpegState_t dec = nullptr;
+    // Recorded after each decode with `dec`: the next decode waits for it,
+    // because the state's staging buffers are in use until the device work
+    // of the decode that filled them has run.
+    cudaEvent_t dec_done = nullptr;
+    bool dec_pending = false;
     nvjpegEncoderState_t enc = nullptr;
     nvjpegEncoderParams_t params = nullptr;
     // Device RGB buffers of op_jpeg_filter, grown on demand.
@@ -107,13 +112,24 @@ int set_params(op_jpeg_t *jp, int quality, int sampling, cudaStream_t s) {
         jp->params, static_cast<nvjpegChromaSubsampling_t>(sampling), s));
 }
 
+// One image through nvJPEG's simple decode.  The decode state is reused
+// only after the previous decode's device work has run (it may have been
+// queued on another stream, or behind other work on this one).
 int decode_into(op_jpeg_t *jp, const uint8_t *data, size_t len, uint8_t *d_rgb, uint32_t pitch,
                 cudaStream_t s) {
+    if (jp->dec_pending) {
+        int st = from_cuda(cudaEventSynchronize(jp->dec_done));
+        if (st != OP_OK) return st;
+        jp->dec_pending = false;
+    }
     nvjpegImage_t dst;
     std::memset(&dst, 0, sizeof(dst));
     dst.channel[0] = d_rgb;
     dst.pitch[0] = pitch;
-    return from_nvjpeg(nvjpegDecode(jp->handle, jp->dec, data, len, NVJPEG_OUTPUT_RGBI, &dst, s));
+    int st = from_nvjpeg(nvjpegDecode(jp->handle, jp->dec, data, len, NVJPEG_OUTPUT_RGBI, &dst, s));
+    const int rec = from_cuda(cudaEventRecord(jp->dec_done, s));
+    if (rec == OP_OK) jp->dec_pending = true;
+    return st != OP_OK ? st : rec;
 }
 
 // Encode and copy the bitstream out.  The first retrieval only reports the
@@ -228,6 +244,7 @@ int op_jpeg_destroy(op_jpeg_t *jp) {
     if (jp->d_out) cudaFree(jp->d_out);
     for (cudaEvent_t e : jp->ev)
         if (e) cudaEventDestroy(e);
+    if (jp->dec_done) cudaEventDestroy(jp->dec_done);
     if (jp->params) nvjpegEncoderParamsDestroy(jp->params);
     if (jp->enc) nvjpegEncoderStateDestroy(jp->enc);
     if (jp->dec) nvjpegJpegStateDestroy(jp->dec);
@@ -254,6 +271,8 @@ op_jpeg_t *op_jpeg_create(void *stream) {
     if (st == OP_OK) st = from_nvjpeg(nvjpegEncoderParamsCreate(jp->handle, &jp->params, s));
     if (st == OP_OK) st = set_params(jp, 90, OP_JPEG_CSS_420, s);
     for (int i = 0; i < 4 && st == OP_OK; ++i) st = from_cuda(cudaEventCreate(&jp->ev[i]));
+    if (st == OP_OK)
+        st = from_cuda(cudaEventCreateWithFlags(&jp->dec_done, cudaEventDisableTiming));
     if (st != OP_OK) {
         op_jpeg_destroy(jp);
         g_last_error = st;

@@ -80,6 +80,51 @@ def flat_gray_jpeg(blocks: np.ndarray, width: int | None = None,
     return bytes(out)
 
 
+def flat_gray_jpeg_progressive(blocks: np.ndarray, width: int | None = None,
+                               height: int | None = None) -> bytes:
+    """The image of flat_gray_jpeg(blocks, width, height) as a progressive
+    JPEG (T.81 Annex G, SOF2): a DC first scan (Ss = Se = 0, no successive
+    approximation) coding the same DC differences as the baseline stream,
+    then one AC scan (Ss = 1, Se = 63) in which every block is a lone
+    end-of-band (EOB0: an end-of-band run of one block).  Its decoded pixels
+    are the same known image."""
+    blocks = np.asarray(blocks, dtype=np.int64)
+    by, bx = blocks.shape
+    h = 8 * by if height is None else height
+    w = 8 * bx if width is None else width
+    if not (8 * (by - 1) < h <= 8 * by and 8 * (bx - 1) < w <= 8 * bx):
+        raise ValueError("size does not match the block grid")
+    out = bytearray(b"\xff\xd8")                                            # SOI
+    out += _segment(0xFFDB, bytes([0x00]) + bytes([1] * 64))                # DQT: table 0, all 1
+    out += _segment(0xFFC2, struct.pack(">BHHB", 8, h, w, 1) + bytes([1, 0x11, 0]))  # SOF2
+    dc_bits = [0, 0, 0, 12] + [0] * 12
+    out += _segment(0xFFC4, bytes([0x00] + dc_bits + list(range(12))))      # DHT: DC table 0
+    ac_bits = [1] + [0] * 15
+    out += _segment(0xFFC4, bytes([0x10] + ac_bits + [0x00]))               # DHT: AC table 0 (EOB0)
+    # DC first scan: component 1, DC table 0; Ss = 0, Se = 0, Ah = Al = 0
+    out += _segment(0xFFDA, bytes([1, 1, 0x00, 0, 0, 0]))
+    bits = _Bits()
+    pred = 0
+    for v in blocks.reshape(-1):
+        dc = 8 * (int(v) - 128)
+        diff = dc - pred
+        pred = dc
+        size = 0 if diff == 0 else abs(diff).bit_length()
+        bits.put(size, 4)
+        if size:
+            bits.put(diff if diff > 0 else diff + (1 << size) - 1, size)
+    out += bits.flush()
+    # AC scan: component 1, AC table 0; Ss = 1, Se = 63, Ah = Al = 0; a
+    # one-component scan covers the component's ceil(w/8) x ceil(h/8) blocks
+    out += _segment(0xFFDA, bytes([1, 1, 0x00, 1, 63, 0]))
+    bits = _Bits()
+    for _ in range(((w + 7) // 8) * ((h + 7) // 8)):
+        bits.put(0, 1)                                                      # EOB0
+    out += bits.flush()
+    out += b"\xff\xd9"                                                      # EOI
+    return bytes(out)
+
+
 def flat_gray_image(blocks: np.ndarray, width: int | None = None,
                     height: int | None = None) -> np.ndarray:
     """The grayscale image flat_gray_jpeg(blocks, width, height) encodes."""

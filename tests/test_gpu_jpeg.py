@@ -18,7 +18,8 @@ from paper_1405_1020_gb300 import jpeg as J
 from paper_1405_1020_gb300 import synth
 from paper_1405_1020_gb300.binding import OP_E_INVALID, OilPaintError
 
-from tests.jpeg_fixture import flat_gray_image, flat_gray_jpeg, frame_header
+from tests.jpeg_fixture import (flat_gray_image, flat_gray_jpeg, flat_gray_jpeg_progressive,
+                                frame_header)
 
 pytestmark = pytest.mark.gpu
 
@@ -303,3 +304,58 @@ def test_filter_many_batched_equals_one_at_a_time(pipe):
         assert pool.filter_many(datas[:1], 4, 20, quality=90) == want[:1]
     with pytest.raises(ValueError):
         J.JpegPool(1, batch=0)
+
+
+def test_progressive_flat_block_jpeg_decodes_exactly(pipe):
+    blocks = _blocks(8, 11, 21)
+    w, h = 83, 61
+    data = flat_gray_jpeg_progressive(blocks, w, h)
+    assert frame_header(data)["sof"] == 0xC2
+    want = flat_gray_image(blocks, w, h)
+    got = pipe.decode(data).cpu().numpy().reshape(h, w, 3)
+    for c in range(3):
+        np.testing.assert_array_equal(got[..., c], want)
+
+
+def test_filter_batch_mixes_decoders(pipe):
+    # progressive streams are not for the JPEG engines (baseline only): in a
+    # batch they take the other decoder, behind the engines' share queued on
+    # the same stream; every output equals the one-image pipeline's, and the
+    # progressive images' filtered pixels equal the oracle's on the known image
+    photos = _photo_jpegs(pipe, ((160, 120), (77, 50)), 90)
+    b1, b2 = _blocks(7, 10, 31), _blocks(4, 5, 32)
+    p1 = flat_gray_jpeg_progressive(b1, 75, 53)
+    p2 = flat_gray_jpeg_progressive(b2, 40, 32)
+    batch = [photos[0], p1, flat_gray_jpeg(b1, 75, 53), p2, photos[1]]
+    for _ in range(3):
+        got = pipe.filter_batch(batch, 3, 20, quality=95, sampling=J.OP_JPEG_CSS_444)
+        assert got == [pipe.filter(d, 3, 20, quality=95, sampling=J.OP_JPEG_CSS_444)
+                       for d in batch]
+    for data, blocks, (w, h) in ((p1, b1, (75, 53)), (p2, b2, (40, 32))):
+        _, rgb = pipe.filter(data, 3, 20, quality=95, sampling=J.OP_JPEG_CSS_444, keep_rgb=True)
+        img = np.repeat(flat_gray_image(blocks, w, h)[..., None], 3, axis=2)
+        np.testing.assert_array_equal(rgb.cpu().numpy().reshape(h, w, 3), _oracle_rgb(img, 3, 20))
+
+
+def test_back_to_back_decodes_on_a_busy_stream(pipe):
+    # decodes queued behind tens of milliseconds of other work on their
+    # stream, with no synchronisation between them: a decode may not reuse
+    # the decoder's state before the previous decode's device work has run
+    cases = []
+    for k, (by, bx, w, h) in enumerate(((7, 10, 75, 53), (6, 9, 70, 45), (3, 4, 30, 20))):
+        blocks = _blocks(by, bx, 50 + k)
+        writer = flat_gray_jpeg if k == 1 else flat_gray_jpeg_progressive
+        cases.append((writer(blocks, w, h), flat_gray_image(blocks, w, h), w, h))
+    stream = torch.cuda.Stream()
+    outs = [torch.zeros((h, 3 * w), dtype=torch.uint8, device="cuda") for _, _, w, h in cases]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(50_000_000)         # tens of milliseconds of one spinning thread
+        for (data, _, w, h), out in zip(cases, outs):
+            assert J.op_jpeg_decode(pipe._h, data, out.data_ptr(), 3 * w,
+                                    stream.cuda_stream) == 0
+    stream.synchronize()
+    for (_, want, w, h), out in zip(cases, outs):
+        got = out.cpu().numpy().reshape(h, w, 3)
+        for c in range(3):
+            np.testing.assert_array_equal(got[..., c], want)

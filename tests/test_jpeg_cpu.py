@@ -11,7 +11,8 @@ import pytest
 from paper_1405_1020_gb300 import jpeg as J
 from paper_1405_1020_gb300.binding import OP_E_INVALID, OP_OK
 from paper_1405_1020_gb300.csrc import build as cbuild
-from tests.jpeg_fixture import flat_gray_image, flat_gray_jpeg, frame_header
+from tests.jpeg_fixture import (flat_gray_image, flat_gray_jpeg, flat_gray_jpeg_progressive,
+                                frame_header)
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                       "oilpaint_jpeg.h")
@@ -100,3 +101,36 @@ def test_flat_gray_writer_ragged_size():
     assert data[data.index(b"\xff\xda"):] == full[full.index(b"\xff\xda"):]
     with pytest.raises(ValueError):
         flat_gray_jpeg(blocks, 24, 17)
+
+
+def _segments(data: bytes):
+    """(marker, payload) of every marker segment before EOI, entropy-coded
+    data skipped (T.81 B.1.1.2: 0xFF00 is a stuffed byte, not a marker)."""
+    out, i = [], 2
+    while i < len(data) - 2:
+        assert data[i] == 0xFF
+        marker = data[i + 1]
+        n = int.from_bytes(data[i + 2:i + 4], "big")
+        out.append((marker, data[i + 4:i + 2 + n]))
+        i += 2 + n
+        if marker == 0xDA:                      # skip the scan's entropy-coded data
+            while not (data[i] == 0xFF and data[i + 1] != 0x00):
+                i += 1
+    return out
+
+
+def test_flat_gray_progressive_writer():
+    blocks = np.arange(35, dtype=np.uint8).reshape(5, 7) * 7
+    data = flat_gray_jpeg_progressive(blocks, 53, 37)
+    hdr = frame_header(data)
+    assert hdr["sof"] == 0xC2 and (hdr["width"], hdr["height"]) == (53, 37)
+    scans = [p for m, p in _segments(data) if m == 0xDA]
+    # a DC first scan, then one AC scan over bands 1..63, one component each
+    assert [tuple(p[-3:]) for p in scans] == [(0, 0, 0), (1, 63, 0)]
+    assert all(p[0] == 1 for p in scans)
+    # the AC scan codes one EOB0 (a single 0 bit) per block, padded with 1s
+    ac = data[data.rindex(b"\xff\xda") + 2 + 8:-2]
+    assert ac == b"\x00" * 4 + bytes([0b00011111])
+    assert data.count(b"\xff\xda") == 2       # two scans, no third
+    with pytest.raises(ValueError):
+        flat_gray_jpeg_progressive(blocks, 48, 37)
